@@ -1,0 +1,154 @@
+"""Pins of the oracle's smoother, V-cycle and Krylov solvers (Section 3)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.dg import SIPG
+from oracle.mesh import Mesh
+from oracle.multigrid import (CPHMultigrid, CoarseCholesky, cg, chebyshev, coarse_meshes,
+                              estimate_lambda, fcg, p_sequence)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_spd(n=30, seed=0):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(0.5, 40.0, n)) @ Q.T
+    A = 0.5 * (A + A.T) + np.diag(rng.uniform(1, 5, n))
+    return A
+
+
+def _cheb_T(s, t):
+    return np.cosh(s * np.arccosh(t)) if t >= 1 else np.cos(s * np.arccos(t))
+
+
+@pytest.mark.parametrize("ns", [1, 2, 3, 5, 6])
+def test_chebyshev_error_polynomial_closed_form(ns):
+    """e_s = T_s((theta - D^-1A)/delta) / T_s(theta/delta) e_0 (Algorithm 3)."""
+    A = _small_spd()
+    d = np.diag(A)
+    dinv = 1 / d
+    # eigen-decomposition of D^-1 A through the symmetric D^-1/2 A D^-1/2
+    S = A / np.sqrt(np.outer(d, d))
+    lam, W = np.linalg.eigh(S)
+    lmax = lam[-1]
+    rng = np.random.default_rng(ns)
+    xs = rng.standard_normal(len(d))
+    b = A @ xs
+    x0 = rng.standard_normal(len(d))
+    x = chebyshev(lambda v: A @ v, dinv, b, x0, lmax, ns)
+    l_hi, l_lo = 1.2 * lmax, 0.06 * lmax
+    th, de = (l_hi + l_lo) / 2, (l_hi - l_lo) / 2
+    poly = np.array([np.cos(ns * np.arccos(np.clip((th - l) / de, -1, 1))) for l in lam])
+    poly /= _cheb_T(ns, th / de)
+    Dh = np.sqrt(d)
+    e0 = Dh * (x0 - xs)                 # error in the symmetric frame
+    es = W @ (poly * (W.T @ e0))
+    assert np.max(np.abs(Dh * (x - xs) - es)) < 1e-12 * np.max(np.abs(e0))
+    # zero start uses no first apply and gives the same as an explicit zero
+    x_a = chebyshev(lambda v: A @ v, dinv, b, np.zeros_like(b), lmax, ns, x_is_zero=True)
+    x_b = chebyshev(lambda v: A @ v, dinv, b, np.zeros_like(b), lmax, ns)
+    assert np.max(np.abs(x_a - x_b)) < 1e-14 * np.max(np.abs(x_b))
+
+
+def test_lambda_estimate_converges_to_max_eigenvalue():
+    op = SIPG(Mesh(3), 2)
+    A = op.assemble()
+    d = A.diagonal()
+    S = (sp.diags(1 / np.sqrt(d)) @ A @ sp.diags(1 / np.sqrt(d))).toarray()
+    lmax = np.linalg.eigvalsh(S)[-1]
+    r0 = np.random.default_rng(0).uniform(-1, 1, op.n_dofs)
+    est = estimate_lambda(lambda v: A @ v, 1 / d, r0, 20)
+    assert est <= lmax * (1 + 1e-12)
+    assert est >= 0.97 * lmax
+    # more iterations only improve it
+    assert estimate_lambda(lambda v: A @ v, 1 / d, r0, 40) >= est - 1e-12
+
+
+def test_lambda_estimate_exact_when_cg_terminates():
+    A = np.diag([1.0, 2.0, 7.0])
+    est = estimate_lambda(lambda v: A @ v, np.ones(3), np.ones(3), 20)
+    assert abs(est - 7.0) < 1e-12
+
+
+def test_coarse_cholesky_residual():
+    A = _small_spd(60, 3)
+    b = np.random.default_rng(4).standard_normal(60)
+    x = CoarseCholesky(A).solve(b)
+    assert np.max(np.abs(A @ x - b)) <= 1e-14 * np.max(np.abs(A)) * np.max(np.abs(x)) * 60
+
+
+def test_level_hierarchy_cph():
+    assert p_sequence(8) == [8, 4, 2, 1]
+    assert p_sequence(6) == [6, 3, 1]
+    assert p_sequence(5) == [5, 2, 1]
+    assert p_sequence(1) == [1]
+    assert p_sequence(5, "minus1") == [5, 4, 3, 2, 1]
+    assert [m.m[0] for m in coarse_meshes(Mesh(32))] == [32, 16, 8, 4]
+    assert [m.m[0] for m in coarse_meshes(Mesh(24))] == [24, 12, 6, 3]
+    assert [m.m[0] for m in coarse_meshes(Mesh(18))] == [18, 9]
+    assert [m.m[0] for m in coarse_meshes(Mesh(4))] == [4]
+
+
+def _exact(x):
+    return np.sin(np.pi * x[..., 0]) * np.sin(np.pi * x[..., 1]) * np.sin(np.pi * x[..., 2])
+
+
+def _n10(hist, it):
+    rho = (hist[-1] / hist[0]) ** (1.0 / it)
+    return -10.0 / np.log10(rho)
+
+
+def test_fcg_equals_cg_with_fp64_vcycle_and_vcycle_is_symmetric():
+    mg = CPHMultigrid(Mesh(4), 3)
+    fine = mg.levels[-1]
+    b = fine.space.rhs(lambda x: 3 * np.pi ** 2 * _exact(x))
+    x1, it1, h1 = fcg(fine.apply, b, np.zeros_like(b), mg.vcycle)
+    x2, it2, h2 = cg(fine.apply, b, np.zeros_like(b), mg.vcycle)
+    assert it1 == it2
+    assert np.max(np.abs(x1 - x2)) <= 1e-12 * np.max(np.abs(x1))
+    assert h1[-1] <= 1e-10 * h1[0]
+    # the V-cycle with equal pre/post smoothing is a symmetric operator
+    rng = np.random.default_rng(0)
+    u, v = rng.standard_normal(fine.n), rng.standard_normal(fine.n)
+    a, bb = u @ mg.vcycle(v), v @ mg.vcycle(u)
+    assert abs(a - bb) <= 1e-11 * abs(a)
+    # the solve converged to the discrete solution
+    xd = np.linalg.solve(fine.A.toarray(), b)
+    assert np.max(np.abs(x1 - xd)) <= 1e-8 * np.max(np.abs(xd))
+
+
+def _golden_n10():
+    out = {}
+    with open(os.path.join(GOLDEN, "n10_cartesian_8cube_cph.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                out[int(k)] = float(v)
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_iteration_counts_near_paper_table(k):
+    """Loose pin: n10 within 1.5 of the paper's cph/floor(p/2) values at 8^3."""
+    mg = CPHMultigrid(Mesh(8), k)
+    fine = mg.levels[-1]
+    b = fine.space.rhs(lambda x: 3 * np.pi ** 2 * _exact(x))
+    _, it, hist = fcg(fine.apply, b, np.zeros_like(b), mg.vcycle)
+    assert abs(_n10(hist, it) - _golden_n10()[k]) < 1.5
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_cph_penalty_robustness(k):
+    """cph barely changes under tau x 1000 (paper Table PenaltyFactor, cph rows)."""
+    n10 = []
+    for pf in (1.0, 1000.0):
+        mg = CPHMultigrid(Mesh(8), k, penalty_factor=pf)
+        fine = mg.levels[-1]
+        b = fine.space.rhs(lambda x: 3 * np.pi ** 2 * _exact(x))
+        _, it, hist = fcg(fine.apply, b, np.zeros_like(b), mg.vcycle)
+        n10.append(_n10(hist, it))
+    assert abs(n10[1] - n10[0]) < 1.0, n10
