@@ -1,0 +1,191 @@
+/*
+ * libsipg -- matrix-free SIPG operator and cph hybrid multigrid on one GB300.
+ *
+ * C ABI of the hot path of Fehn, Munch, Wall, Kronbichler, "Hybrid multigrid
+ * methods for high-order discontinuous Galerkin discretizations"
+ * (arXiv:1910.01900).  Every call is plain C: opaque context, plain pointers
+ * and sizes, no C++ or framework types.
+ *
+ * Conventions that hold for every entry point
+ * -------------------------------------------
+ * - Return value: a sipg_status; SIPG_OK on success.  Nothing throws across
+ *   this boundary.  sipg_last_error(ctx) returns a text for the last failure of
+ *   that context (sipg_last_error(NULL): last failure of sipg_create).
+ * - Vectors named *_dev are DEVICE pointers owned by the caller, on the device
+ *   that was current when the context was created.  Vectors named *_host are
+ *   host pointers owned by the caller.  The library never frees or keeps caller
+ *   pointers after a call returns.
+ * - DoF order of a DG vector (level L, the finest): cell-major with cells
+ *   lexicographic (x fastest), then the (k+1)^3 nodes of the cell
+ *   lexicographic (x fastest).  FE vectors (levels below L): the global grid
+ *   of (m k'+1)^3 nodes, lexicographic, x fastest.
+ * - precision argument: 0 = double (FP64), 1 = float (FP32).  A void* vector
+ *   holds elements of that type.
+ * - All work is ordered on the context's stream (sipg_params.stream; NULL =
+ *   the legacy default stream).  Calls that return numbers to the host
+ *   (solve info, norms) synchronize that stream; all others are asynchronous.
+ * - The library owns every internal buffer (allocated in sipg_create, freed in
+ *   sipg_destroy).  Calls on one context must not overlap in time from
+ *   different host threads.
+ */
+#ifndef SIPG_H
+#define SIPG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sipg_ctx sipg_ctx;
+
+typedef enum {
+  SIPG_OK = 0,
+  SIPG_EINVAL = 1,      /* bad argument: size, degree, pointer, precision    */
+  SIPG_ECUDA = 2,       /* a CUDA runtime call failed                         */
+  SIPG_ENOMEM = 3,      /* device or host allocation failed                   */
+  SIPG_ENOTCONV = 4,    /* solver hit maxit before reaching the tolerance     */
+  SIPG_EBREAKDOWN = 5,  /* p^T A p <= 0 or a non-finite scalar in the solver  */
+  SIPG_ETIMEOUT = 6,    /* a bounded device-side wait ran out                 */
+  SIPG_ENAN = 7         /* non-finite input (right-hand side norm)           */
+} sipg_status;
+
+/* Structured hexahedral box mesh (Section 2: hexahedral cells, mapping x(xi)
+ * from the reference cell [0,1]^3; Section 5.3: deformed cube with degree-3
+ * element mappings).  m[i] cells in direction i over [lo_i, hi_i].
+ * deform = 0: affine (Cartesian) cells.  deform = 1: every cell is the
+ * tensor Lagrange interpolant of degree mapping_degree (must be 3) on its GL
+ * points of the map x_i <- x_i + amp * prod_j sin(pi (x_j-lo_j)/(hi_j-lo_j)).
+ * bc[s] for the box sides s = -x,+x,-y,+y,-z,+z: 0 = Dirichlet, 1 = Neumann
+ * (Eq. BoundaryConditions; only the homogeneous operator is applied). */
+typedef struct {
+  int m[3];
+  double lo[3], hi[3];
+  int deform;
+  double amp;
+  int mapping_degree;
+  int bc[6];
+} sipg_mesh;
+
+/* Method parameters (Sections 2 and 3).  Defaults from sipg_default_params. */
+typedef struct {
+  int degree;              /* k = p in the paper, 1..8                         */
+  double penalty_factor;   /* multiplies tau_e = (k+1)^2 A/V (Section 2); 1.0  */
+  int precision;           /* V-cycle precision: 0 FP64, 1 FP32 (Section 4,
+                              mixed-precision multigrid); the outer solver and
+                              the coarse solve are always FP64              */
+  int p_coarsen;           /* 0: p_{l-1} = floor(p_l/2) (Section 3.2), the only
+                              sequence built                                 */
+  int cheb_degree;         /* n_s smoothing steps pre and post, default 5      */
+  double cheb_lo, cheb_hi; /* smoothing range [lo, hi] * lambda_max: 0.06, 1.2 */
+  int eig_iters;           /* CG iterations of the lambda_max estimate, 20     */
+  double lambda_override;  /* > 0: use this lambda_max on every level (tests)  */
+  int smoother;            /* 0: Chebyshev-Jacobi (Algorithm 3)               */
+  int operator_only;       /* 1: build only the finest DG operator (for
+                              operator_apply); the solver calls then fail   */
+  void *stream;            /* cudaStream_t or NULL                             */
+} sipg_params;
+
+typedef struct {
+  int iterations;          /* outer iterations performed                       */
+  int converged;           /* 1 if ||r||/||r0|| <= rtol was reached            */
+  double r0_norm;          /* ||b - A x0||_2                                   */
+  double r_norm;           /* final ||r||_2                                    */
+  double rho;              /* average convergence rate (Section 5.1)           */
+  double n10;              /* -10 / log10(rho)                                 */
+  double seconds;          /* wall time of the solve on the stream             */
+  double res_history[256]; /* ||r_j||_2, j = 0..min(iterations,255)            */
+} sipg_solve_info;
+
+/* Fills the defaults listed above (degree 3, FP64). */
+void sipg_default_params(sipg_params *p);
+
+/* Setup (Section 3.1: setup cost not part of the solve): 1D rules, geometry
+ * and penalty per level, the cph level hierarchy (Section 3.2: DG_k -> FE_k ->
+ * FE_floor(k/2) -> ... -> FE_1 -> FE_1 on coarser meshes while every m is even
+ * and m/2 >= 3), transfer tables, inverse diagonals, lambda_max estimates by
+ * eig_iters Jacobi-CG iterations, the dense coarse factor.  Allocates all
+ * device memory of the context.  EINVAL for degree outside 1..8, m < 1,
+ * non-positive extents, mapping_degree != 3 with deform, a penalty factor
+ * <= 0, or no Dirichlet side when a solver will be used (the solver calls
+ * then return EINVAL). */
+sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_ctx **out);
+sipg_status sipg_destroy(sipg_ctx *ctx);
+const char *sipg_last_error(const sipg_ctx *ctx);
+
+/* Number of levels (L+1) and the size of level l (0 = coarsest, L = finest DG). */
+sipg_status sipg_num_levels(const sipg_ctx *ctx, int *nlevels);
+sipg_status sipg_num_dofs(const sipg_ctx *ctx, int level, int64_t *n);
+/* Level description: kind 0 = DG, 1 = FE; degree; cells per direction. */
+sipg_status sipg_level_info(const sipg_ctx *ctx, int level, int *kind, int *degree, int m[3]);
+/* lambda_max estimate of D^-1 A used by the smoother of level l (Section 3.1). */
+sipg_status sipg_lambda(const sipg_ctx *ctx, int level, double *lambda);
+
+/* Right-hand side of the manufactured solution (Section 5.3, cube): kind 0:
+ * u = prod_j sin(pi (x_j - lo_j)/(hi_j - lo_j)), f = -lap u, g = u on the
+ * Dirichlet sides (zero on the box), h = du/dn on Neumann sides.  Writes the
+ * FP64 DG vector b_dev (length = dofs of the finest level). */
+sipg_status sipg_rhs(sipg_ctx *ctx, int kind, double *b_dev);
+
+/* v = A u on the finest (DG) level: the homogeneous SIPG operator of
+ * Eq. WeakFormDG with fluxes InteriorPenaltyFlux1/2 and mirror boundary
+ * conditions, evaluated matrix-free by sum factorization (Section 4,
+ * Eq. MatrixFreeAbstractNotation).  u and v must not overlap. */
+sipg_status sipg_operator_apply(sipg_ctx *ctx, int precision, const void *u_dev, void *v_dev);
+
+/* v = A_l u on any level (FE levels: Eq. WeakFormFE with constrained rows set
+ * to the identity, Section 2), in either precision. */
+sipg_status sipg_level_apply(sipg_ctx *ctx, int level, int precision, const void *u_dev, void *v_dev);
+
+/* Inverse diagonal D^-1 of level l (Section 3.1), written in the level's
+ * precision (finest level: precision argument). */
+sipg_status sipg_inverse_diagonal(sipg_ctx *ctx, int level, int precision, void *d_dev);
+
+/* nsteps Chebyshev-Jacobi steps of Algorithm 3 on A_l x = b, starting from
+ * the given x (updated in place), in the level's V-cycle precision. */
+sipg_status sipg_smooth(sipg_ctx *ctx, int level, const void *b_dev, void *x_dev, int nsteps);
+
+/* Transfers between level l and l-1 (Section 3.2), V-cycle precision:
+ * restrict:   rc = R r = P^T r   (r on level l, rc on level l-1)
+ * prolongate: x += P xc          (xc on level l-1, x on level l)     */
+sipg_status sipg_restrict(sipg_ctx *ctx, int level, const void *r_dev, void *rc_dev);
+sipg_status sipg_prolongate_add(sipg_ctx *ctx, int level, const void *xc_dev, void *x_dev);
+
+/* Coarse solve on level 0: x = A_0^-1 b in FP64 (dense direct solver that
+ * replaces the paper's AMG, Section 3.3). */
+sipg_status sipg_coarse_solve(sipg_ctx *ctx, const double *b_dev, double *x_dev);
+
+/* One V-cycle of Algorithm 2 with x = 0 on entry: z = M^-1 r.  r and z are
+ * FP64 finest-level vectors; the cycle runs in params.precision. */
+sipg_status sipg_vcycle(sipg_ctx *ctx, const double *r_dev, double *z_dev);
+
+/* Solve A x = b (Algorithm 1 structure, flexible CG with one retained
+ * direction) preconditioned by one V-cycle, FP64 residual and inner
+ * products.  x_dev holds the start vector on entry.  Stops when
+ * ||r||/||r0|| <= rtol or after maxit iterations; fixed_iters > 0 runs exactly
+ * that many iterations instead.  info may be NULL.  ENOTCONV if maxit was
+ * hit, EBREAKDOWN on p^T A p <= 0 or non-finite scalars, ENAN for a
+ * non-finite right-hand side. */
+sipg_status sipg_solve(sipg_ctx *ctx, const double *b_dev, double *x_dev, double rtol,
+                       int maxit, int fixed_iters, sipg_solve_info *info);
+
+/* The same solve from and to HOST memory: copies b_host to the device, solves
+ * with x0 = 0, copies x back to x_host (both FP64, length = finest dofs). */
+sipg_status sipg_solve_host(sipg_ctx *ctx, const double *b_host, double *x_host, double rtol,
+                            int maxit, sipg_solve_info *info);
+
+/* Per-launch device time of the last sipg_operator_apply-style launches
+ * recorded with events on the context stream: the DG evaluation pass and the
+ * DG integration pass, in milliseconds (for roofline accounting). */
+sipg_status sipg_time_apply(sipg_ctx *ctx, int precision, const void *u_dev, void *v_dev,
+                            int repeats, float *ms_eval, float *ms_integrate);
+
+/* Peak arithmetic probe: runs an independent-FMA loop on every SM for the
+ * given precision (0 FP64 DFMA, 1 FP32 FFMA) and returns the measured rate in
+ * FLOP/s (2 per FMA).  Not part of the method: used for the roofline. */
+sipg_status sipg_fma_peak(int precision, void *stream, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

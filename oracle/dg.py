@@ -76,7 +76,22 @@ class SIPG:
                 self.fV[d, s], self.fG[d, s] = basis.tensor_basis(
                     self.nodes, _face_points(d, s == 1, self.xq))
         self.n_dofs = mesh.n_cells * n ** 3
-        self.tau = self._penalty()
+        self._tau = None
+
+    @property
+    def tau(self):
+        """tau_e of every cell (computed on first use)."""
+        if self._tau is None:
+            self._tau = self._penalty()
+        return self._tau
+
+    def tau_of(self, cells):
+        """tau_e of the given cells only (each cell's value depends on that cell alone)."""
+        cells = np.asarray(cells)
+        if self._tau is not None:
+            return self._tau[cells]
+        uniq, inv = np.unique(cells, return_inverse=True)
+        return self._penalty(uniq)[inv]
 
     # ---------------------------------------------------------------- geometry
     def cell_geometry(self, cells):
@@ -126,16 +141,19 @@ class SIPG:
                 c[s][sel] = np.einsum("fqba,fqa->fqb", Jinv, nrm[sel])
         return dA, nrm, c
 
-    def _penalty(self):
+    def _penalty(self, which=None):
         """tau_e per cell (penalty definition in Section 2) times the factor."""
-        mesh, E = self.mesh, self.mesh.n_cells
+        mesh = self.mesh
+        which = np.arange(mesh.n_cells) if which is None else np.asarray(which)
+        E = len(which)
         vol = np.zeros(E)
         a_int = np.zeros(E)
         a_bdry = np.zeros(E)
         for c0 in range(0, E, self.chunk):
-            cells = np.arange(c0, min(E, c0 + self.chunk))
+            loc = np.arange(c0, min(E, c0 + self.chunk))
+            cells = which[loc]
             jxw, _ = self.cell_geometry(cells)
-            vol[cells] = jxw.sum(axis=1)
+            vol[loc] = jxw.sum(axis=1)
             ijk = mesh.cell_ijk(cells)
             for d in range(3):
                 for s in (0, 1):  # s=0: face at xi_d=1 (upper side), s=1: xi_d=0
@@ -143,8 +161,8 @@ class SIPG:
                     area = (adet * np.linalg.norm(Jinv[:, :, d, :], axis=-1)
                             * self.wf[None, :]).sum(axis=1)
                     on_bdry = (ijk[:, d] == mesh.m[d] - 1) if s == 0 else (ijk[:, d] == 0)
-                    a_bdry[cells] += np.where(on_bdry, area, 0.0)
-                    a_int[cells] += np.where(on_bdry, 0.0, area)
+                    a_bdry[loc] += np.where(on_bdry, area, 0.0)
+                    a_int[loc] += np.where(on_bdry, 0.0, area)
         return self.penalty_factor * (self.k + 1) ** 2 * (0.5 * a_int + a_bdry) / vol
 
     # ------------------------------------------------------ local operators
@@ -239,12 +257,10 @@ class SIPG:
             flux = np.einsum("cqab,cqb->cqa", metric, grad)
             Vout[cs] += np.einsum("bqi,cqb->ci", self.G, flux)
         for d in range(3):
-            LU = mesh.faces(d)
-            touch = np.zeros(len(LU), bool)
-            for s in (0, 1):
-                ok = LU[:, s] >= 0
-                touch[ok] |= want[LU[ok, s]]
-            LU = LU[touch]
+            if cells is None:
+                LU = mesh.faces(d)
+            else:
+                LU = mesh.faces_of_cells(d, todo)
             if len(LU) == 0:
                 continue
             dA, c = self._face_blocks(d, LU)
@@ -262,7 +278,7 @@ class SIPG:
             if np.any(inner):
                 L, U_ = LU[inner, 0], LU[inner, 1]
                 w = dA[inner]
-                tau = np.maximum(self.tau[L], self.tau[U_])[:, None]
+                tau = np.maximum(self.tau_of(L), self.tau_of(U_))[:, None]
                 jump = vals[0][inner] - vals[1][inner]
                 avg = 0.5 * (dns[0][inner] + dns[1][inner])
                 val_coef = w * (-avg + tau * jump)    # multiplies [v]
@@ -282,7 +298,7 @@ class SIPG:
                 m = want[cell]
                 w = dA[sel][m]
                 uu, qq = vals[s][sel][m], dns[s][sel][m]
-                tau = self.tau[cell[m]][:, None]
+                tau = self.tau_of(cell[m])[:, None]
                 contrib = (w * (-qq + 2.0 * tau * uu)) @ self.fV[d, s]
                 contrib += np.einsum("fq,fqb,bqi->fi", w * (-uu), c[s][sel][m], self.fG[d, s])
                 np.add.at(Vout, cell[m], contrib)

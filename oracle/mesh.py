@@ -80,6 +80,25 @@ class Mesh:
         """The two tangential directions of a face normal to d, ascending."""
         return [t for t in range(3) if t != d]
 
+    def faces_of_cells(self, d, cells):
+        """(lower, upper) rows of the faces normal to d that touch the given cells."""
+        m = self.m
+        ijk = self.cell_ijk(np.asarray(cells))
+        rows = set()
+        for c, (i, j, k) in zip(np.asarray(cells), ijk):
+            for up in (0, 1):
+                a = [int(i), int(j), int(k)]
+                if up:
+                    lo_c = int(c)
+                    a[d] += 1
+                    up_c = self.cell_index(*a) if a[d] < m[d] else -1
+                else:
+                    up_c = int(c)
+                    a[d] -= 1
+                    lo_c = self.cell_index(*a) if a[d] >= 0 else -1
+                rows.add((lo_c, up_c))
+        return np.array(sorted(rows), dtype=np.int64).reshape(-1, 2)
+
     def faces(self, d):
         """All faces normal to direction d as (lower cell or -1, upper cell or -1).
 

@@ -1,0 +1,19 @@
+// FP32 instantiation of the DG passes (mixed-precision V-cycle, Section 4).
+#include "dg_launch.cuh"
+
+namespace sipg {
+
+template <>
+void upload_tables_dg<float>(const Tables<float> &t) { upload_tables_tu(t); }
+template <>
+cudaError_t launch_dg_eval<float>(int n, bool curved, const DGArgs<float> &a, cudaStream_t s, int cb) {
+  return dispatch_dg<float>(false, n, curved, a, s, cb);
+}
+template <>
+cudaError_t launch_dg_integrate<float>(int n, bool curved, const DGArgs<float> &a, cudaStream_t s, int cb) {
+  return dispatch_dg<float>(true, n, curved, a, s, cb);
+}
+template <>
+int dg_cells_per_block<float>(int n) { return default_cb(n); }
+
+}  // namespace sipg

@@ -1,0 +1,361 @@
+// Matrix-free SIPG operator on the DG level (Section 4, Eq.
+// MatrixFreeAbstractNotation; weak form Eq. WeakFormDG with the fluxes of
+// Eqs. InteriorPenaltyFlux1/2 and the mirror boundary conditions of
+// Eq. BoundaryConditions).
+//
+// Face integrals without atomics, in two passes over the cells:
+//
+//  eval pass      : u_e -> u at the Gauss points (3 interpolation sweeps) ->
+//                   reference gradient at the Gauss points (3 collocation
+//                   derivative sweeps), stored for the second pass; the value
+//                   and the outward normal derivative on all six faces are
+//                   extrapolated along the face normal and stored as the
+//                   cell's face traces.
+//  integrate pass : metric term on the stored gradient, then for every face
+//                   the SIPG flux from the cell's own trace and the
+//                   neighbour's trace, tested against the cell's own basis
+//                   only (the neighbour integrates its own side in its own
+//                   launch thread), then 3 transposed derivative sweeps and 3
+//                   transposed interpolation sweeps, and the fused epilogue.
+//
+// Each cell writes only its own outputs, so no two threads ever update the
+// same global value.  Per face point the own side computes, with [u] =
+// u_own - u_nb and q = outward normal derivative of each side,
+//   value coefficient   A = dA (tau_f [u] - (q_own - q_nb)/2)     (times v)
+//   normal-deriv coeff. B = -dA [u] / 2                           (times d_n v)
+// and on Dirichlet faces A = dA (2 tau_e u - q), B = -dA u; on Neumann faces
+// A = B = 0.  This is the per-side form of
+//   -{d_n v}[u] - [v]{d_n u} + tau [v][u]  and  -d_n v u - v d_n u + 2 tau v u.
+#pragma once
+#include "sumfac.cuh"
+
+namespace sipg {
+
+template <typename T, int N, bool CURVED, int CB>
+__global__ void __launch_bounds__(CB *N *N) dg_eval_kernel(const DGArgs<T> a) {
+  constexpr int N2 = N * N, N3 = N2 * N, NT = CB * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
+  const int cell0 = blockIdx.x * CB;
+  const int ncta = min(CB, a.ncells - cell0);
+  const bool act = cl < ncta;
+  T *su = sm + cl * 4 * N3;
+
+  const T *ug = a.u + (size_t)cell0 * N3;
+  for (int i = tid; i < ncta * N3; i += NT) {
+    const int c = i / N3;
+    sm[c * 4 * N3 + (i - c * N3)] = ug[i];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    if (act) sweep_inplace<T, N, MS>(su, d, l);
+    __syncthreads();
+  }
+  if (act) {
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      int base, stride;
+      line_of<N>(d, l, base, stride);
+      T x[N], y[N];
+      load_line<T, N>(su, base, stride, x);
+      apply_mat<T, N, MD>(x, y);
+      store_line<T, N>(su + (1 + d) * N3, base, stride, y);
+    }
+  }
+  __syncthreads();
+  T *gg = a.grad + (size_t)cell0 * 3 * N3;
+  for (int i = tid; i < ncta * 3 * N3; i += NT) {
+    const int c = i / (3 * N3);
+    gg[i] = sm[c * 4 * N3 + N3 + (i - c * 3 * N3)];
+  }
+  if (!act) return;
+  const int cell = cell0 + cl;
+  const int ijk[3] = {cell % a.m[0], (cell / a.m[0]) % a.m[1], cell / (a.m[0] * a.m[1])};
+  const Tables<T> &t = tab<T>();
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    int base, stride;
+    line_of<N>(d, l, base, stride);
+    T x[N];
+    load_line<T, N>(su, base, stride, x);
+    T v0 = t.l0[N][0] * x[0], v1 = t.l1[N][0] * x[0];
+#pragma unroll
+    for (int q = 1; q < N; ++q) {
+      v0 = fma(t.l0[N][q], x[q], v0);
+      v1 = fma(t.l1[N][q], x[q], v1);
+    }
+    T q0, q1;
+    if constexpr (!CURVED) {
+      T g[N];
+      load_line<T, N>(su + (1 + d) * N3, base, stride, g);
+      T g0 = t.l0[N][0] * g[0], g1 = t.l1[N][0] * g[0];
+#pragma unroll
+      for (int q = 1; q < N; ++q) {
+        g0 = fma(t.l0[N][q], g[q], g0);
+        g1 = fma(t.l1[N][q], g[q], g1);
+      }
+      q0 = -a.ih[d] * g0;
+      q1 = a.ih[d] * g1;
+    } else {
+      T gr0[3], gr1[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        T g[N];
+        load_line<T, N>(su + (1 + b) * N3, base, stride, g);
+        T g0 = t.l0[N][0] * g[0], g1 = t.l1[N][0] * g[0];
+#pragma unroll
+        for (int q = 1; q < N; ++q) {
+          g0 = fma(t.l0[N][q], g[q], g0);
+          g1 = fma(t.l1[N][q], g[q], g1);
+        }
+        gr0[b] = g0;
+        gr1[b] = g1;
+      }
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const size_t nfp = (size_t)a.m[t1] * a.m[t2];
+      const size_t f0 = (size_t)ijk[d] * nfp + ijk[t1] + (size_t)a.m[t1] * ijk[t2];
+      const size_t f1 = f0 + nfp;
+      const T *c0 = a.fc[d] + (f0 * 2 + 1) * 3 * N2 + l;   // this cell is the upper cell of plane i_d
+      const T *c1 = a.fc[d] + (f1 * 2 + 0) * 3 * N2 + l;   // and the lower cell of plane i_d+1
+      q0 = c0[0] * gr0[0] + c0[N2] * gr0[1] + c0[2 * N2] * gr0[2];
+      q1 = c1[0] * gr1[0] + c1[N2] * gr1[1] + c1[2 * N2] * gr1[2];
+    }
+    T *tr = a.trace + ((size_t)cell * 6 + 2 * d) * 2 * N2 + l;
+    tr[0] = v0;
+    tr[N2] = q0;
+    tr[2 * N2] = v1;
+    tr[3 * N2] = q1;
+  }
+}
+
+template <typename T, int N, bool CURVED, int CB>
+__global__ void __launch_bounds__(CB *N *N) dg_integrate_kernel(const DGArgs<T> a) {
+  constexpr int N2 = N * N, N3 = N2 * N, NT = CB * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
+  const int cell0 = blockIdx.x * CB;
+  const int ncta = min(CB, a.ncells - cell0);
+  const bool act = cl < ncta;
+  T *st = sm + cl * 4 * N3;   // value accumulator, then the integrated tile
+  T *sg = st + N3;            // three gradient components
+
+  const T *gg = a.grad + (size_t)cell0 * 3 * N3;
+  for (int i = tid; i < ncta * 3 * N3; i += NT) {
+    const int c = i / (3 * N3);
+    sm[c * 4 * N3 + N3 + (i - c * 3 * N3)] = gg[i];
+  }
+  __syncthreads();
+  for (int i = tid; i < ncta * N3; i += NT) {
+    const int c = i / N3, p = i - c * N3;
+    T *s = sm + c * 4 * N3 + N3;
+    const T g0 = s[p], g1 = s[N3 + p], g2 = s[2 * N3 + p];
+    if constexpr (!CURVED) {
+      s[p] = g0 * a.wcart[p];
+      s[N3 + p] = g1 * a.wcart[N3 + p];
+      s[2 * N3 + p] = g2 * a.wcart[2 * N3 + p];
+    } else {
+      const T *M = a.metric + (size_t)(cell0 + c) * 6 * N3 + p;
+      const T xx = M[0], yy = M[N3], zz = M[2 * N3], xy = M[3 * N3], xz = M[4 * N3], yz = M[5 * N3];
+      s[p] = xx * g0 + xy * g1 + xz * g2;
+      s[N3 + p] = xy * g0 + yy * g1 + yz * g2;
+      s[2 * N3 + p] = xz * g0 + yz * g1 + zz * g2;
+    }
+  }
+  __syncthreads();
+
+  const int cell = cell0 + cl;
+  int ijk[3] = {0, 0, 0};
+  if (act) {
+    ijk[0] = cell % a.m[0];
+    ijk[1] = (cell / a.m[0]) % a.m[1];
+    ijk[2] = cell / (a.m[0] * a.m[1]);
+  }
+  const Tables<T> &t = tab<T>();
+  const int cstride[3] = {1, a.m[0], a.m[0] * a.m[1]};
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    if (act) {
+      int base, stride;
+      line_of<N>(d, l, base, stride);
+      const T tau_e = a.tau[cell];
+      T A[2], B[2];
+      T cvec[2][3];
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const size_t nfp = (size_t)a.m[t1] * a.m[t2];
+      const size_t ftan = ijk[t1] + (size_t)a.m[t1] * ijk[t2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const T *tr = a.trace + ((size_t)cell * 6 + 2 * d + s) * 2 * N2 + l;
+        const T uo = tr[0], qo = tr[N2];
+        T dA;
+        const size_t face = (size_t)(ijk[d] + s) * nfp + ftan;
+        if constexpr (CURVED) {
+          dA = a.fdA[d][face * N2 + l];
+          const T *c = a.fc[d] + (face * 2 + (s ? 0 : 1)) * 3 * N2 + l;
+          cvec[s][0] = c[0];
+          cvec[s][1] = c[N2];
+          cvec[s][2] = c[2 * N2];
+        } else {
+          dA = a.fwcart[d * N2 + l];
+        }
+        const bool has_nb = s ? (ijk[d] < a.m[d] - 1) : (ijk[d] > 0);
+        if (has_nb) {
+          const int nb = cell + (s ? cstride[d] : -cstride[d]);
+          const T *tn = a.trace + ((size_t)nb * 6 + 2 * d + (1 - s)) * 2 * N2 + l;
+          const T un = tn[0], qn = tn[N2];
+          const T tau_f = max(tau_e, a.tau[nb]);
+          const T jump = uo - un;
+          A[s] = dA * (tau_f * jump - T(0.5) * (qo - qn));
+          B[s] = T(-0.5) * dA * jump;
+        } else if (a.bc[2 * d + s] == 0) {
+          A[s] = dA * (T(2) * tau_e * uo - qo);
+          B[s] = -dA * uo;
+        } else {
+          A[s] = T(0);
+          B[s] = T(0);
+        }
+      }
+      T y[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) y[q] = t.l0[N][q] * A[0] + t.l1[N][q] * A[1];
+      if (d == 0) {
+        store_line<T, N>(st, base, stride, y);
+      } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) st[base + q * stride] += y[q];
+      }
+      if constexpr (!CURVED) {
+        const T b0 = -a.ih[d] * B[0], b1 = a.ih[d] * B[1];
+        T *g = sg + d * N3;
+#pragma unroll
+        for (int q = 0; q < N; ++q) g[base + q * stride] += t.l0[N][q] * b0 + t.l1[N][q] * b1;
+      } else {
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+          const T b0 = cvec[0][bb] * B[0], b1 = cvec[1][bb] * B[1];
+          T *g = sg + bb * N3;
+#pragma unroll
+          for (int q = 0; q < N; ++q) g[base + q * stride] += t.l0[N][q] * b0 + t.l1[N][q] * b1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    if (act) {
+      int base, stride;
+      line_of<N>(d, l, base, stride);
+      T x[N], y[N];
+      load_line<T, N>(sg + d * N3, base, stride, x);
+      apply_mat<T, N, MDt>(x, y);
+#pragma unroll
+      for (int q = 0; q < N; ++q) st[base + q * stride] += y[q];
+    }
+    __syncthreads();
+  }
+#pragma unroll 1
+  for (int d = 0; d < 2; ++d) {
+    if (act) sweep_inplace<T, N, MSt>(st, d, l);
+    __syncthreads();
+  }
+  if (!act) return;
+  T x[N], y[N];
+  load_line<T, N>(st, l, N2, x);
+  apply_mat<T, N, MSt>(x, y);
+  const size_t g0 = (size_t)cell * N3 + l;
+  if (a.mode == 0) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.out[g0 + q * N2] = y[q];
+  } else if (a.mode == 2) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.out[g0 + q * N2] = a.b[g0 + q * N2] - y[q];
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      const size_t i = g0 + q * N2;
+      T v = a.c3 * a.dinv[i] * (a.b[i] - y[q]);
+      if (a.x) v = fma(a.c1, a.x[i], v);
+      if (a.xp) v = fma(a.c2, a.xp[i], v);
+      a.out[i] = v;
+    }
+  }
+}
+
+// Diagonal of the DG operator (setup, FP64), one thread per DoF: the cell
+// term sum_q grad N_i^T M_q grad N_i and the face self-coupling
+// dA (tau N_i^2 - N_i d_n N_i) on interior faces, dA (2 tau N_i^2 - 2 N_i d_n N_i)
+// on Dirichlet faces.
+struct DiagTabs {
+  double S[81], Sd[81], lp0[9], lp1[9];
+};
+
+template <int N, bool CURVED>
+__global__ void dg_diag_kernel(const DGArgs<double> a, const DiagTabs tb, double *diag) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)a.ncells * N3) return;
+  const int cell = (int)(idx / N3), i = (int)(idx - (long)cell * N3);
+  const int ii[3] = {i % N, (i / N) % N, i / N2};
+  const int ijk[3] = {cell % a.m[0], (cell / a.m[0]) % a.m[1], cell / (a.m[0] * a.m[1])};
+  double sum = 0;
+  for (int qz = 0; qz < N; ++qz)
+    for (int qy = 0; qy < N; ++qy)
+      for (int qx = 0; qx < N; ++qx) {
+        const int p = qx + N * qy + N2 * qz;
+        const double sx = tb.S[qx * N + ii[0]], sy = tb.S[qy * N + ii[1]], sz = tb.S[qz * N + ii[2]];
+        const double g0 = tb.Sd[qx * N + ii[0]] * sy * sz;
+        const double g1 = sx * tb.Sd[qy * N + ii[1]] * sz;
+        const double g2 = sx * sy * tb.Sd[qz * N + ii[2]];
+        if (!CURVED) {
+          sum += a.wcart[p] * g0 * g0 + a.wcart[N3 + p] * g1 * g1 + a.wcart[2 * N3 + p] * g2 * g2;
+        } else {
+          const double *M = a.metric + (size_t)cell * 6 * N3 + p;
+          sum += M[0] * g0 * g0 + M[N3] * g1 * g1 + M[2 * N3] * g2 * g2 +
+                 2.0 * (M[3 * N3] * g0 * g1 + M[4 * N3] * g0 * g2 + M[5 * N3] * g1 * g2);
+        }
+      }
+  const int cstride[3] = {1, a.m[0], a.m[0] * a.m[1]};
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    for (int s = 0; s < 2; ++s) {
+      if (ii[d] != (s ? N - 1 : 0)) continue;   // basis vanishes on this face
+      const bool has_nb = s ? (ijk[d] < a.m[d] - 1) : (ijk[d] > 0);
+      if (!has_nb && a.bc[2 * d + s] != 0) continue;   // Neumann: no term
+      const double tau_e = a.tau[cell];
+      const double tau_f = has_nb ? fmax(tau_e, a.tau[cell + (s ? cstride[d] : -cstride[d])]) : tau_e;
+      const double lp = s ? tb.lp1[ii[d]] : tb.lp0[ii[d]];
+      const size_t nfp = (size_t)a.m[t1] * a.m[t2];
+      const size_t face = (size_t)(ijk[d] + s) * nfp + ijk[t1] + (size_t)a.m[t1] * ijk[t2];
+      for (int q2 = 0; q2 < N; ++q2)
+        for (int q1 = 0; q1 < N; ++q1) {
+          const int lq = q1 + N * q2;
+          const double s1 = tb.S[q1 * N + ii[t1]], s2 = tb.S[q2 * N + ii[t2]];
+          const double nv = s1 * s2;
+          double dA, dn;
+          if (!CURVED) {
+            dA = a.fwcart[d * N2 + lq];
+            dn = (s ? a.ih[d] : -a.ih[d]) * lp * nv;
+          } else {
+            dA = a.fdA[d][face * N2 + lq];
+            const double *c = a.fc[d] + (face * 2 + (s ? 0 : 1)) * 3 * N2 + lq;
+            double gr[3];
+            gr[d] = lp * nv;
+            gr[t1] = tb.Sd[q1 * N + ii[t1]] * s2;
+            gr[t2] = s1 * tb.Sd[q2 * N + ii[t2]];
+            dn = c[0] * gr[0] + c[N2] * gr[1] + c[2 * N2] * gr[2];
+          }
+          if (has_nb)
+            sum += dA * (tau_f * nv * nv - nv * dn);
+          else
+            sum += dA * (2.0 * tau_e * nv * nv - 2.0 * nv * dn);
+        }
+    }
+  }
+  diag[idx] = sum;
+}
+
+}  // namespace sipg

@@ -1,0 +1,174 @@
+// Internal interfaces of libsipg: kernel argument blocks, level data and the
+// launchers each translation unit provides.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sipg.h"
+
+namespace sipg {
+
+constexpr int kMaxN = 9;   // points per direction, k = 1..8
+
+// Host copy of the 1D tables for one n (points per direction), in double.
+// Basis: Lagrange on the n Gauss-Lobatto nodes; quadrature: n-point Gauss.
+struct Rules1D {
+  int n = 0;
+  std::vector<double> gl;      // GL nodes on [0,1]
+  std::vector<double> xq, wq;  // Gauss points and weights on [0,1]
+  std::vector<double> S;       // S[q*n+i]  = l_i(x_q)                 (Gauss x GL)
+  std::vector<double> Sd;      // Sd[q*n+i] = l_i'(x_q)
+  std::vector<double> D;       // D[q*n+r]  = lG_r'(x_q), Lagrange on Gauss points
+  std::vector<double> l0, l1;  // lG_q(0), lG_q(1)
+  std::vector<double> lp0, lp1;// l_i'(0), l_i'(1)  (GL basis)
+};
+const Rules1D &rules(int n);
+std::vector<double> lagrange_values(const std::vector<double> &nodes, double x);
+std::vector<double> lagrange_derivs(const std::vector<double> &nodes, double x);
+
+// Device-side 1D tables for all n in one block, uploaded to constant memory of
+// every translation unit that launches sum-factorisation kernels.
+template <typename T>
+struct Tables {
+  // plain n x n matrices (used for n <= 4), stride n
+  T S[kMaxN + 1][16], St[kMaxN + 1][16], D[kMaxN + 1][16], Dt[kMaxN + 1][16];
+  // even-odd blocks (n >= 5): E[hc][hc] stride 5, O[hc][h] stride 4
+  T SE[kMaxN + 1][25], SO[kMaxN + 1][20], StE[kMaxN + 1][25], StO[kMaxN + 1][20];
+  T DE[kMaxN + 1][25], DO[kMaxN + 1][20], DtE[kMaxN + 1][25], DtO[kMaxN + 1][20];
+  T l0[kMaxN + 1][kMaxN], l1[kMaxN + 1][kMaxN];
+};
+template <typename T>
+void build_tables(Tables<T> &t);
+
+// Arguments of the DG evaluation / integration passes.
+template <typename T>
+struct DGArgs {
+  const T *u;          // input vector (cell-major, n^3 per cell)
+  T *out;              // output (mode dependent)
+  T *grad;             // scratch: reference gradient at Gauss points, [cell][3][n^3]
+  T *trace;            // scratch: face traces, [cell][6 faces][2 (value, d_n)][n^2]
+  const T *metric;     // curved: [cell][6][n^3] = w|detJ| J^-1 J^-T (xx,yy,zz,xy,xz,yz)
+  const T *wcart;      // Cartesian: [3][n^3] = w_q * prod(h)/h_d^2
+  const T *fdA[3];     // curved: [face][n^2] area element times weights
+  const T *fc[3];      // curved: [face][2 roles][3][n^2] = J^-1 n_outward (own side)
+  const T *fwcart;     // Cartesian: [3][n^2] = w_q1 w_q2 h_t1 h_t2
+  const T *tau;        // [cell] penalty tau_e
+  T ih[3];             // Cartesian 1/h_d
+  int m[3];
+  int ncells;
+  int bc[6];
+  // epilogue: mode 0 out = Au; 1 out = c1 x + c2 xp + c3 dinv (b - Au); 2 out = b - Au
+  int mode;
+  const T *x, *xp, *b, *dinv;
+  T c1, c2, c3;
+};
+
+// Arguments of the FE cell pass and the node gather pass.
+template <typename T>
+struct FEArgs {
+  const T *u;
+  T *ebuf;             // [cell][n^3]
+  T *out;
+  const T *metric;     // curved [cell][6][n^3]
+  const T *wcart;      // Cartesian [3][n^3]
+  int m[3];
+  int deg;             // polynomial degree p (n = p+1)
+  int grid[3];         // node grid = m*p+1
+  int ncells;
+  int bc[6];
+  int mode;            // gather: 0 apply, 1 chebyshev, 2 residual, 3 restrict (sum, constrained -> 0),
+                       //         4 diagonal (sum, constrained -> 1)
+  const T *x, *xp, *b, *dinv;
+  T c1, c2, c3;
+};
+
+// One multigrid level.
+struct Level {
+  int kind = 0;         // 0 DG, 1 FE
+  int deg = 1, n = 2;
+  int m[3] = {1, 1, 1};
+  int grid[3] = {1, 1, 1};
+  int64_t ncells = 0, ndofs = 0;
+  bool curved = false;
+  double h[3] = {1, 1, 1};
+  // geometry in both precisions ([0] double, [1] float)
+  void *metric[2] = {nullptr, nullptr};
+  void *wcart[2] = {nullptr, nullptr};
+  void *fdA[2][3] = {{nullptr}}, *fc[2][3] = {{nullptr}};
+  void *fwcart[2] = {nullptr, nullptr};
+  void *tau[2] = {nullptr, nullptr};
+  void *dinv[2] = {nullptr, nullptr};
+  double lambda = 0;
+  // transfer from level l-1 (coarser) to this level
+  int t_kind = -1;      // 0 c-transfer, 1 p-transfer, 2 h-transfer
+  void *P1[2] = {nullptr, nullptr};   // [2 children][nf][nc] interpolation tables
+  // V-cycle work vectors in the V-cycle precision (and FP64 for setup)
+  void *vb[2] = {nullptr, nullptr}, *vx[2] = {nullptr, nullptr}, *vr[2] = {nullptr, nullptr},
+       *vt[2] = {nullptr, nullptr};
+};
+
+// Launchers (one per precision; defined in the kernel translation units).
+template <typename T>
+void upload_tables_dg(const Tables<T> &t);
+template <typename T>
+void upload_tables_fe(const Tables<T> &t);
+
+template <typename T>
+cudaError_t launch_dg_eval(int n, bool curved, const DGArgs<T> &a, cudaStream_t s, int cb = 0);
+template <typename T>
+cudaError_t launch_dg_integrate(int n, bool curved, const DGArgs<T> &a, cudaStream_t s, int cb = 0);
+template <typename T>
+int dg_cells_per_block(int n);
+
+cudaError_t launch_dg_diag(int n, bool curved, const DGArgs<double> &a, double *diag, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_fe_cells(int n, bool curved, const FEArgs<T> &a, bool diag_only, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s);
+
+// Transfers.  For the c-transfer the coarse space is the FE space on the same
+// mesh with the same degree: prolongation injects, restriction sums duplicates.
+template <typename T>
+cudaError_t launch_c_prolongate_add(const FEArgs<T> &fe, const T *xc, T *xdg, cudaStream_t s);
+struct XferGeom {
+  int kind;             // 1 p, 2 h
+  int mf[3], mc[3];     // cells of fine and coarse mesh
+  int pf, pc;           // degrees
+  int gf[3], gc[3];     // node grids
+  int bc[6];
+};
+template <typename T>
+cudaError_t launch_fe_prolongate_add(const XferGeom &g, const T *P1, const T *xc, T *xf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf, T *ebuf_c, cudaStream_t s);
+
+// Vector kernels.
+template <typename T>
+cudaError_t launch_fill(T *x, T v, int64_t n, cudaStream_t s);
+template <typename Tout, typename Tin>
+cudaError_t launch_cast(Tout *y, const Tin *x, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_axpy(T *y, T a, const T *x, int64_t n, cudaStream_t s);   // y += a x
+cudaError_t launch_invert(double *d, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_xdb(T *x, T c, const T *dinv, const T *b, int64_t n, cudaStream_t s);   // x = c dinv b
+template <typename T>
+cudaError_t launch_xpby(T *p, const T *z, T beta, int64_t n, cudaStream_t s);              // p = z + beta p
+// deterministic dot products into device scalars: out[0] = x.y (and out[1] = z.w if z)
+cudaError_t launch_dot2(const double *x, const double *y, const double *z, const double *w, int64_t n,
+                        double *partials, unsigned *counter, double *out, cudaStream_t s);
+// FCG helpers (scalars in device memory, see solver.cu for the layout)
+cudaError_t launch_fcg_update_xr(double *x, double *r, const double *p, const double *v, int64_t n,
+                                 const double *sc, double *partials, unsigned *counter, double *out,
+                                 cudaStream_t s);
+cudaError_t launch_fcg_update_p(double *p, const double *z, const double *sc, int64_t n, cudaStream_t s);
+template <typename Tb, typename Tx>
+cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cudaStream_t s);
+
+cudaError_t fma_peak(int precision, cudaStream_t s, double *flops);
+
+}  // namespace sipg

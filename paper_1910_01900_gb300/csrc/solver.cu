@@ -1,0 +1,900 @@
+// Context, setup, V-cycle, Chebyshev smoother, flexible CG and the C ABI
+// (Section 3 of the paper: Algorithms 1-3, the cph level hierarchy, the
+// coarse solve; Section 4: mixed precision).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "geometry.h"
+#include "sipg_internal.h"
+
+using namespace sipg;
+
+struct sipg_ctx {
+  sipg_mesh mesh{};
+  sipg_params prm{};
+  MeshDesc md{};
+  cudaStream_t stream = nullptr;
+  bool solver = false;
+  std::vector<Level> lv;   // 0 = coarsest, L = finest DG
+  int L = 0;
+  void *dg_grad[2] = {nullptr, nullptr}, *dg_trace[2] = {nullptr, nullptr};
+  void *ebuf[2] = {nullptr, nullptr};
+  double *Ainv = nullptr;
+  int n0 = 0;
+  double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fv = nullptr, *fx = nullptr, *fb = nullptr;
+  double *scal = nullptr, *partials = nullptr;
+  unsigned *counter = nullptr;
+  std::vector<void *> allocs;
+  std::string err;
+};
+
+static std::string g_create_err;
+
+namespace {
+
+struct Fail {
+  sipg_status st;
+};
+
+#define CK(...)                                                                        \
+  do {                                                                                 \
+    cudaError_t e_ = (__VA_ARGS__);                                                         \
+    if (e_ != cudaSuccess) {                                                           \
+      throw_cuda(e_, #__VA_ARGS__, __LINE__);                                               \
+    }                                                                                  \
+  } while (0)
+
+thread_local std::string *t_err = nullptr;
+
+[[noreturn]] void throw_cuda(cudaError_t e, const char *what, int line) {
+  if (t_err) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "CUDA error %s (%s) at solver.cu:%d in %s", cudaGetErrorName(e),
+             cudaGetErrorString(e), line, what);
+    *t_err = buf;
+  }
+  throw Fail{e == cudaErrorMemoryAllocation ? SIPG_ENOMEM : SIPG_ECUDA};
+}
+[[noreturn]] void throw_inval(const std::string &msg) {
+  if (t_err) *t_err = msg;
+  throw Fail{SIPG_EINVAL};
+}
+
+template <typename T>
+T *dalloc(sipg_ctx *c, int64_t n) {
+  void *p = nullptr;
+  CK(cudaMalloc(&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T)));
+  c->allocs.push_back(p);
+  return (T *)p;
+}
+
+// upload host doubles as both precisions
+void upload2(sipg_ctx *c, const std::vector<double> &h, void *out[2]) {
+  if (h.empty()) {
+    out[0] = out[1] = nullptr;
+    return;
+  }
+  double *d = dalloc<double>(c, (int64_t)h.size());
+  float *f = dalloc<float>(c, (int64_t)h.size());
+  CK(cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(launch_cast<float, double>(f, d, (int64_t)h.size(), nullptr));
+  out[0] = d;
+  out[1] = f;
+}
+
+template <typename T>
+constexpr int pidx() {
+  return sizeof(T) == 8 ? 0 : 1;
+}
+
+template <typename T>
+DGArgs<T> dg_args(sipg_ctx *c, const Level &L) {
+  constexpr int pi = pidx<T>();
+  DGArgs<T> a{};
+  a.grad = (T *)c->dg_grad[pi];
+  a.trace = (T *)c->dg_trace[pi];
+  a.metric = (const T *)L.metric[pi];
+  a.wcart = (const T *)L.wcart[pi];
+  for (int d = 0; d < 3; ++d) {
+    a.fdA[d] = (const T *)L.fdA[pi][d];
+    a.fc[d] = (const T *)L.fc[pi][d];
+    a.ih[d] = (T)(1.0 / L.h[d]);
+    a.m[d] = L.m[d];
+  }
+  a.fwcart = (const T *)L.fwcart[pi];
+  a.tau = (const T *)L.tau[pi];
+  a.ncells = (int)L.ncells;
+  for (int s = 0; s < 6; ++s) a.bc[s] = c->mesh.bc[s];
+  return a;
+}
+
+template <typename T>
+FEArgs<T> fe_args(sipg_ctx *c, const Level &L) {
+  constexpr int pi = pidx<T>();
+  FEArgs<T> a{};
+  a.ebuf = (T *)c->ebuf[pi];
+  a.metric = (const T *)L.metric[pi];
+  a.wcart = (const T *)L.wcart[pi];
+  a.deg = L.deg;
+  a.ncells = (int)L.ncells;
+  for (int d = 0; d < 3; ++d) {
+    a.m[d] = L.m[d];
+    a.grid[d] = L.grid[d];
+  }
+  for (int s = 0; s < 6; ++s) a.bc[s] = c->mesh.bc[s];
+  return a;
+}
+
+// out = epilogue(A_l u): mode 0 Au, 1 c1 x + c2 xp + c3 dinv (b - Au), 2 b - Au
+template <typename T>
+void apply_level(sipg_ctx *c, int l, const T *u, T *out, int mode, const T *x = nullptr, const T *xp = nullptr,
+                 const T *b = nullptr, const T *dinv = nullptr, T c1 = 0, T c2 = 0, T c3 = 0) {
+  const Level &L = c->lv[l];
+  if (L.kind == 0) {
+    DGArgs<T> a = dg_args<T>(c, L);
+    a.u = u;
+    a.out = out;
+    a.mode = mode;
+    a.x = x;
+    a.xp = xp;
+    a.b = b;
+    a.dinv = dinv;
+    a.c1 = c1;
+    a.c2 = c2;
+    a.c3 = c3;
+    CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream));
+    CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream));
+  } else {
+    FEArgs<T> a = fe_args<T>(c, L);
+    a.u = u;
+    a.out = out;
+    a.mode = mode;
+    a.x = x;
+    a.xp = xp;
+    a.b = b;
+    a.dinv = dinv;
+    a.c1 = c1;
+    a.c2 = c2;
+    a.c3 = c3;
+    CK(launch_fe_cells<T>(L.n, L.curved, a, false, c->stream));
+    CK(launch_fe_gather<T>(a, c->stream));
+  }
+}
+
+XferGeom xfer(sipg_ctx *c, int l) {
+  const Level &F = c->lv[l], &C = c->lv[l - 1];
+  XferGeom g{};
+  g.kind = F.t_kind;
+  for (int d = 0; d < 3; ++d) {
+    g.mf[d] = F.m[d];
+    g.mc[d] = C.m[d];
+    g.gf[d] = F.grid[d];
+    g.gc[d] = C.grid[d];
+  }
+  g.pf = F.deg;
+  g.pc = C.deg;
+  for (int s = 0; s < 6; ++s) g.bc[s] = c->mesh.bc[s];
+  return g;
+}
+
+// rc = R r from level l to l-1
+template <typename T>
+void restrict_level(sipg_ctx *c, int l, const T *r, T *rc) {
+  constexpr int pi = pidx<T>();
+  const Level &F = c->lv[l];
+  FEArgs<T> a = fe_args<T>(c, c->lv[l - 1]);
+  a.mode = 3;
+  a.out = rc;
+  if (F.t_kind == 0) {
+    a.ebuf = const_cast<T *>(r);   // the DG vector is the element buffer of the FE level
+  } else {
+    CK(launch_fe_restrict_cells<T>(xfer(c, l), (const T *)F.P1[pi], r, (T *)c->ebuf[pi], c->stream));
+  }
+  CK(launch_fe_gather<T>(a, c->stream));
+}
+
+// x += P xc from level l-1 to l
+template <typename T>
+void prolongate_level(sipg_ctx *c, int l, const T *xc, T *x) {
+  constexpr int pi = pidx<T>();
+  const Level &F = c->lv[l];
+  if (F.t_kind == 0) {
+    FEArgs<T> a = fe_args<T>(c, c->lv[l - 1]);
+    CK(launch_c_prolongate_add<T>(a, xc, x, c->stream));
+  } else {
+    CK(launch_fe_prolongate_add<T>(xfer(c, l), (const T *)F.P1[pi], xc, x, c->stream));
+  }
+}
+
+// Algorithm 3 on level l: x (in/out buffer pointer) with scratch xt; the
+// buffers are swapped as the iteration proceeds.
+template <typename T>
+void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_start) {
+  constexpr int pi = pidx<T>();
+  const Level &L = c->lv[l];
+  const T *dinv = (const T *)L.dinv[pi];
+  const double lam = L.lambda;
+  const double lhi = c->prm.cheb_hi * lam, llo = c->prm.cheb_lo * lam;
+  const double theta = 0.5 * (lhi + llo), delta = 0.5 * (lhi - llo);
+  bool have_prev;
+  if (zero_start) {
+    CK(launch_xdb<T>(x, (T)(1.0 / theta), dinv, b, L.ndofs, c->stream));
+    have_prev = false;   // x_0 = 0
+  } else {
+    apply_level<T>(c, l, x, xt, 1, x, nullptr, b, dinv, T(1), T(0), (T)(1.0 / theta));
+    std::swap(x, xt);
+    have_prev = true;
+  }
+  double rho_prev = delta / theta;
+  for (int j = 1; j < ns; ++j) {
+    const double rho = 1.0 / (2.0 * theta / delta - rho_prev);
+    const double sigma = rho * rho_prev, th = 2.0 * rho / delta;
+    apply_level<T>(c, l, x, xt, 1, x, have_prev ? xt : nullptr, b, dinv, (T)(1.0 + sigma), (T)(-sigma), (T)th);
+    std::swap(x, xt);
+    have_prev = true;
+    rho_prev = rho;
+  }
+}
+
+// Algorithm 2 with x^(l) = 0 on entry: lv[l].vb -> lv[l].vx
+template <typename T>
+void vcycle_rec(sipg_ctx *c, int l) {
+  constexpr int pi = pidx<T>();
+  Level &L = c->lv[l];
+  T *b = (T *)L.vb[pi];
+  if (l == 0) {
+    CK((launch_dense_gemv<T, T>(c->Ainv, b, (T *)L.vx[pi], c->n0, c->stream)));
+    return;
+  }
+  T *x = (T *)L.vx[pi], *xt = (T *)L.vt[pi];
+  const int ns = c->prm.cheb_degree;
+  chebyshev<T>(c, l, b, x, xt, ns, true);
+  apply_level<T>(c, l, x, (T *)L.vr[pi], 2, nullptr, nullptr, b);
+  restrict_level<T>(c, l, (const T *)L.vr[pi], (T *)c->lv[l - 1].vb[pi]);
+  vcycle_rec<T>(c, l - 1);
+  prolongate_level<T>(c, l, (const T *)c->lv[l - 1].vx[pi], x);
+  chebyshev<T>(c, l, b, x, xt, ns, false);
+  L.vx[pi] = x;
+  L.vt[pi] = xt;
+}
+
+// z = M^-1 r with FP64 vectors in and out
+void vcycle_fp64io(sipg_ctx *c, const double *r, double *z) {
+  Level &F = c->lv[c->L];
+  if (c->prm.precision == 0) {
+    CK(cudaMemcpyAsync(F.vb[0], r, F.ndofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    vcycle_rec<double>(c, c->L);
+    CK(cudaMemcpyAsync(z, F.vx[0], F.ndofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK((launch_cast<float, double>((float *)F.vb[1], r, F.ndofs, c->stream)));
+    vcycle_rec<float>(c, c->L);
+    CK((launch_cast<double, float>(z, (const float *)F.vx[1], F.ndofs, c->stream)));
+  }
+}
+
+double read_scalar(sipg_ctx *c, int slot) {
+  double v;
+  CK(cudaMemcpyAsync(&v, c->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return v;
+}
+
+double dot(sipg_ctx *c, const double *x, const double *y, int64_t n, int slot) {
+  CK(launch_dot2(x, y, nullptr, nullptr, n, c->partials, c->counter, c->scal + slot, c->stream));
+  return read_scalar(c, slot);
+}
+
+// lambda_max of D^-1 A on level l from Jacobi-PCG (Section 3.1: 20 CG iterations)
+double estimate_lambda(sipg_ctx *c, int l) {
+  Level &L = c->lv[l];
+  const int64_t n = L.ndofs;
+  std::vector<double> r0(n);
+  for (int64_t i = 0; i < n; ++i) r0[i] = uniform_pm1(1910, (uint64_t)i);
+  double *r = (double *)L.vb[0], *z = (double *)L.vx[0], *p = (double *)L.vr[0], *Ap = (double *)L.vt[0];
+  CK(cudaMemcpy(r, r0.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  if (L.kind == 1) {   // the start vector is zero on constrained FE nodes
+    std::vector<double> h(n);
+    for (int64_t g = 0; g < n; ++g) {
+      const int gx = (int)(g % L.grid[0]), gy = (int)((g / L.grid[0]) % L.grid[1]),
+                gz = (int)(g / ((int64_t)L.grid[0] * L.grid[1]));
+      const int *bc = c->mesh.bc;
+      const bool cons = (gx == 0 && bc[0] == 0) || (gx == L.grid[0] - 1 && bc[1] == 0) ||
+                        (gy == 0 && bc[2] == 0) || (gy == L.grid[1] - 1 && bc[3] == 0) ||
+                        (gz == 0 && bc[4] == 0) || (gz == L.grid[2] - 1 && bc[5] == 0);
+      h[g] = cons ? 0.0 : r0[g];
+    }
+    CK(cudaMemcpy(r, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  const double *dinv = (const double *)L.dinv[0];
+  CK(launch_xdb<double>(z, 1.0, dinv, r, n, c->stream));
+  CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  double rz = dot(c, r, z, n, 8);
+  const double rz0 = rz;
+  std::vector<double> alphas, betas;
+  for (int it = 0; it < c->prm.eig_iters; ++it) {
+    apply_level<double>(c, l, p, Ap, 0);
+    const double pAp = dot(c, p, Ap, n, 9);
+    const double alpha = rz / pAp;
+    CK(launch_axpy<double>(r, -alpha, Ap, n, c->stream));
+    CK(launch_xdb<double>(z, 1.0, dinv, r, n, c->stream));
+    const double rz_new = dot(c, r, z, n, 10);
+    alphas.push_back(alpha);
+    if (!(rz_new > 1e-28 * rz0)) break;
+    const double beta = rz_new / rz;
+    betas.push_back(beta);
+    CK(launch_xpby<double>(p, z, beta, n, c->stream));
+    rz = rz_new;
+  }
+  const int m = (int)alphas.size();
+  std::vector<double> dg(m), off(m > 1 ? m - 1 : 0);
+  for (int j = 0; j < m; ++j) {
+    dg[j] = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
+    if (j + 1 < m) off[j] = std::sqrt(betas[j]) / alphas[j];
+  }
+  return tridiag_max_eig(dg, off);
+}
+
+void build_level_geometry(sipg_ctx *c, Level &L, const MeshDesc &md, bool faces) {
+  Mapping map(md);
+  std::vector<double> metric, wcart;
+  cell_geometry(map, L.n, metric, wcart);
+  upload2(c, metric, L.metric);
+  upload2(c, wcart, L.wcart);
+  for (int d = 0; d < 3; ++d) L.h[d] = map.h[d];
+  if (faces) {
+    std::vector<double> fdA[3], fc[3], fw, tau;
+    face_geometry(map, L.n, fdA, fc, fw);
+    for (int d = 0; d < 3; ++d) {
+      void *o[2];
+      upload2(c, fdA[d], o);
+      L.fdA[0][d] = o[0];
+      L.fdA[1][d] = o[1];
+      upload2(c, fc[d], o);
+      L.fc[0][d] = o[0];
+      L.fc[1][d] = o[1];
+    }
+    upload2(c, fw, L.fwcart);
+    penalty(map, L.n, c->prm.penalty_factor, tau);
+    upload2(c, tau, L.tau);
+  }
+}
+
+void alloc_work(sipg_ctx *c, Level &L) {
+  for (int pi = 0; pi < 2; ++pi) {
+    const size_t es = pi == 0 ? 8 : 4;
+    void **v[4] = {&L.vb[pi], &L.vx[pi], &L.vr[pi], &L.vt[pi]};
+    for (auto *pp : v) {
+      void *p;
+      CK(cudaMalloc(&p, std::max<size_t>(L.ndofs, 1) * es));
+      c->allocs.push_back(p);
+      *pp = p;
+    }
+  }
+}
+
+void setup(sipg_ctx *c) {
+  const sipg_mesh &M = c->mesh;
+  const sipg_params &P = c->prm;
+  {
+    static Tables<double> td;
+    static Tables<float> tf;
+    static bool built = false;
+    if (!built) {
+      build_tables(td);
+      build_tables(tf);
+      built = true;
+    }
+    upload_tables_dg<double>(td);
+    upload_tables_dg<float>(tf);
+    upload_tables_fe<double>(td);
+    upload_tables_fe<float>(tf);
+    CK(cudaGetLastError());
+  }
+  MeshDesc md{};
+  for (int d = 0; d < 3; ++d) {
+    md.m[d] = M.m[d];
+    md.lo[d] = M.lo[d];
+    md.hi[d] = M.hi[d];
+  }
+  md.deform = M.deform;
+  md.amp = M.amp;
+  for (int s = 0; s < 6; ++s) md.bc[s] = M.bc[s];
+  c->md = md;
+  bool any_dir = false;
+  for (int s = 0; s < 6; ++s) any_dir |= (M.bc[s] == 0);
+  c->solver = !P.operator_only && any_dir;
+
+  // fine-to-coarse list of (kind, degree, mesh)
+  struct Spec {
+    int kind, deg;
+    MeshDesc md;
+    int t_kind;   // transfer to the next coarser level
+  };
+  std::vector<Spec> specs;
+  specs.push_back({0, P.degree, md, 0});
+  if (c->solver) {
+    int p = P.degree;
+    specs.push_back({1, p, md, -1});
+    while (p > 1) {
+      specs.back().t_kind = 1;
+      p = std::max(1, p / 2);
+      specs.push_back({1, p, md, -1});
+    }
+    MeshDesc cm = md;
+    while (cm.m[0] % 2 == 0 && cm.m[1] % 2 == 0 && cm.m[2] % 2 == 0 && cm.m[0] / 2 >= 3 && cm.m[1] / 2 >= 3 &&
+           cm.m[2] / 2 >= 3) {
+      for (int d = 0; d < 3; ++d) cm.m[d] /= 2;
+      specs.back().t_kind = 2;
+      specs.push_back({1, 1, cm, -1});
+    }
+  }
+  const int nl = (int)specs.size();
+  c->lv.assign(nl, Level());
+  c->L = nl - 1;
+  int64_t ebuf_len = 0;
+  for (int i = 0; i < nl; ++i) {
+    const Spec &s = specs[i];
+    Level &L = c->lv[nl - 1 - i];
+    L.kind = s.kind;
+    L.deg = s.deg;
+    L.n = s.deg + 1;
+    L.curved = md.deform != 0;
+    for (int d = 0; d < 3; ++d) {
+      L.m[d] = s.md.m[d];
+      L.grid[d] = s.md.m[d] * s.deg + 1;
+    }
+    L.ncells = (int64_t)L.m[0] * L.m[1] * L.m[2];
+    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    L.ndofs = s.kind == 0 ? L.ncells * n3 : (int64_t)L.grid[0] * L.grid[1] * L.grid[2];
+    build_level_geometry(c, L, s.md, s.kind == 0);
+    if (s.kind == 1) ebuf_len = std::max(ebuf_len, L.ncells * n3);
+    if (c->solver) alloc_work(c, L);
+  }
+  // transfer tables: level l (fine) from l-1 (coarse)
+  for (int l = 1; l < nl; ++l) {
+    Level &F = c->lv[l];
+    const Spec &s = specs[nl - 1 - l];
+    F.t_kind = s.t_kind;
+    if (F.t_kind == 0) continue;
+    const Level &C = c->lv[l - 1];
+    const int nf = F.n, nc = C.n;
+    const Rules1D &rf = rules(nf), &rc = rules(nc);
+    const int nch = F.t_kind == 2 ? 2 : 1;
+    std::vector<double> P1((size_t)nch * nf * nc);
+    for (int ch = 0; ch < nch; ++ch)
+      for (int i = 0; i < nf; ++i) {
+        const double x = F.t_kind == 2 ? 0.5 * (ch + rf.gl[i]) : rf.gl[i];
+        const auto v = lagrange_values(rc.gl, x);
+        for (int j = 0; j < nc; ++j) P1[((size_t)ch * nf + i) * nc + j] = v[j];
+      }
+    upload2(c, P1, F.P1);
+    ebuf_len = std::max(ebuf_len, C.ncells * (int64_t)nc * nc * nc);
+  }
+  // DG scratch (both precisions)
+  {
+    const Level &F = c->lv[c->L];
+    const int64_t n3 = (int64_t)F.n * F.n * F.n, n2 = (int64_t)F.n * F.n;
+    c->dg_grad[0] = dalloc<double>(c, F.ncells * 3 * n3);
+    c->dg_trace[0] = dalloc<double>(c, F.ncells * 12 * n2);
+    c->dg_grad[1] = dalloc<float>(c, F.ncells * 3 * n3);
+    c->dg_trace[1] = dalloc<float>(c, F.ncells * 12 * n2);
+  }
+  c->scal = dalloc<double>(c, 64);
+  c->partials = dalloc<double>(c, 2 * 304);
+  c->counter = dalloc<unsigned>(c, 4);
+  CK(cudaMemset(c->counter, 0, 4 * sizeof(unsigned)));
+  if (!c->solver) {
+    CK(cudaDeviceSynchronize());
+    return;
+  }
+  c->ebuf[0] = dalloc<double>(c, ebuf_len);
+  c->ebuf[1] = dalloc<float>(c, ebuf_len);
+  // inverse diagonals
+  for (int l = 1; l < nl; ++l) {
+    Level &L = c->lv[l];
+    double *d = dalloc<double>(c, L.ndofs);
+    if (L.kind == 0) {
+      DGArgs<double> a = dg_args<double>(c, L);
+      CK(launch_dg_diag(L.n, L.curved, a, d, c->stream));
+    } else {
+      FEArgs<double> a = fe_args<double>(c, L);
+      CK(launch_fe_cells<double>(L.n, L.curved, a, true, c->stream));
+      a.mode = 4;
+      a.out = d;
+      CK(launch_fe_gather<double>(a, c->stream));
+    }
+    CK(launch_invert(d, L.ndofs, c->stream));
+    float *f = dalloc<float>(c, L.ndofs);
+    CK((launch_cast<float, double>(f, d, L.ndofs, c->stream)));
+    L.dinv[0] = d;
+    L.dinv[1] = f;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  // smoothing range
+  for (int l = 1; l < nl; ++l)
+    c->lv[l].lambda = P.lambda_override > 0 ? P.lambda_override : estimate_lambda(c, l);
+  // coarse matrix and its inverse
+  {
+    std::vector<double> A;
+    int N;
+    Mapping cmap(specs.back().md);
+    coarse_matrix(cmap, M.bc, A, N);
+    if (!cholesky_inverse(A, N)) throw_inval("coarse matrix is not positive definite");
+    c->n0 = N;
+    c->Ainv = dalloc<double>(c, (int64_t)N * N);
+    CK(cudaMemcpy(c->Ainv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  const int64_t N = c->lv[c->L].ndofs;
+  c->fr = dalloc<double>(c, N);
+  c->fz = dalloc<double>(c, N);
+  c->fp = dalloc<double>(c, N);
+  c->fv = dalloc<double>(c, N);
+  c->fx = dalloc<double>(c, N);
+  c->fb = dalloc<double>(c, N);
+  CK(cudaDeviceSynchronize());
+}
+
+// Flexible CG (Algorithm 1 structure) preconditioned by one V-cycle.
+sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int maxit, int fixed,
+                       sipg_solve_info *info) {
+  const int64_t N = c->lv[c->L].ndofs;
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  // r = b - A x
+  apply_level<double>(c, c->L, x, c->fr, 2, nullptr, nullptr, b);
+  const double bn = std::sqrt(dot(c, b, b, N, 4));
+  if (!std::isfinite(bn)) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->err = "right-hand side is not finite";
+    return SIPG_ENAN;
+  }
+  const double r0 = std::sqrt(dot(c, c->fr, c->fr, N, 3));
+  std::vector<double> hist{r0};
+  vcycle_fp64io(c, c->fr, c->fz);
+  CK(launch_dot2(c->fr, c->fz, nullptr, nullptr, N, c->partials, c->counter, c->scal + 0, s));
+  CK(cudaMemcpyAsync(c->fp, c->fz, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int it = 0;
+  sipg_status st = SIPG_OK;
+  double rn = r0;
+  const bool fixed_mode = fixed > 0;
+  while (true) {
+    if (fixed_mode) {
+      if (it >= fixed) break;
+    } else if (rn <= rtol * r0 || r0 == 0.0) {
+      break;
+    } else if (it >= maxit) {
+      st = SIPG_ENOTCONV;
+      break;
+    }
+    apply_level<double>(c, c->L, c->fp, c->fv, 0);
+    CK(launch_dot2(c->fp, c->fv, nullptr, nullptr, N, c->partials, c->counter, c->scal + 2, s));
+    CK(launch_fcg_update_xr(x, c->fr, c->fp, c->fv, N, c->scal, c->partials, c->counter, c->scal + 3, s));
+    double sc[4];
+    CK(cudaMemcpyAsync(sc, c->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!(sc[2] > 0) || !std::isfinite(sc[0]) || !std::isfinite(sc[3])) {
+      c->err = "flexible CG breakdown: p^T A p <= 0 or a non-finite scalar";
+      st = SIPG_EBREAKDOWN;
+      ++it;
+      break;
+    }
+    rn = std::sqrt(sc[3]);
+    ++it;
+    hist.push_back(rn);
+    if (!fixed_mode && rn <= rtol * r0) break;
+    vcycle_fp64io(c, c->fr, c->fz);
+    CK(launch_dot2(c->fr, c->fz, c->fz, c->fv, N, c->partials, c->counter, c->scal + 0, s));   // gamma, z.Ap
+    CK(launch_fcg_update_p(c->fp, c->fz, c->scal, N, s));
+  }
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iterations = it;
+    info->r0_norm = r0;
+    info->r_norm = rn;
+    info->converged = (r0 == 0.0 || rn <= rtol * r0) ? 1 : 0;
+    info->rho = (it > 0 && r0 > 0) ? std::pow(rn / r0, 1.0 / it) : 0.0;
+    info->n10 = (info->rho > 0 && info->rho < 1) ? -10.0 / std::log10(info->rho) : 0.0;
+    info->seconds = ms * 1e-3;
+    for (int j = 0; j < (int)hist.size() && j < 256; ++j) info->res_history[j] = hist[j];
+  }
+  if (st == SIPG_ENOTCONV) c->err = "flexible CG reached maxit before the tolerance";
+  return st;
+}
+
+template <typename F>
+sipg_status guarded(sipg_ctx *c, F &&f) {
+  std::string *prev = t_err;
+  t_err = c ? &c->err : &g_create_err;
+  sipg_status st;
+  try {
+    st = f();
+  } catch (const Fail &e) {
+    st = e.st;
+  } catch (const std::exception &e) {
+    if (t_err) *t_err = e.what();
+    st = SIPG_ENOMEM;
+  }
+  t_err = prev;
+  return st;
+}
+
+bool level_ok(const sipg_ctx *c, int l) { return c && l >= 0 && l <= c->L; }
+
+}  // namespace
+
+extern "C" {
+
+void sipg_default_params(sipg_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->degree = 3;
+  p->penalty_factor = 1.0;
+  p->precision = 0;
+  p->p_coarsen = 0;
+  p->cheb_degree = 5;
+  p->cheb_lo = 0.06;
+  p->cheb_hi = 1.2;
+  p->eig_iters = 20;
+  p->lambda_override = 0.0;
+  p->smoother = 0;
+  p->operator_only = 0;
+  p->stream = nullptr;
+}
+
+sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_ctx **out) {
+  if (!out) return SIPG_EINVAL;
+  *out = nullptr;
+  auto c = std::make_unique<sipg_ctx>();
+  sipg_status st = guarded(nullptr, [&]() -> sipg_status {
+    if (!mesh || !params) throw_inval("null mesh or params");
+    const sipg_mesh &M = *mesh;
+    const sipg_params &P = *params;
+    if (P.degree < 1 || P.degree > 8) throw_inval("degree must be in 1..8");
+    for (int d = 0; d < 3; ++d) {
+      if (M.m[d] < 1) throw_inval("m must be >= 1");
+      if (!(M.hi[d] > M.lo[d])) throw_inval("box extents must be positive");
+    }
+    if (M.deform && M.mapping_degree != 3) throw_inval("curved cells need mapping_degree 3");
+    if (!(P.penalty_factor > 0)) throw_inval("penalty factor must be positive");
+    if (P.precision != 0 && P.precision != 1) throw_inval("precision must be 0 or 1");
+    if (P.cheb_degree < 1 || P.eig_iters < 1 || P.p_coarsen != 0 || P.smoother != 0)
+      throw_inval("unsupported smoother parameters");
+    for (int s = 0; s < 6; ++s)
+      if (M.bc[s] != 0 && M.bc[s] != 1) throw_inval("bc must be 0 (Dirichlet) or 1 (Neumann)");
+    const double cells = (double)M.m[0] * M.m[1] * M.m[2];
+    if (cells * std::pow(P.degree + 1.0, 3) > 2.0e9) throw_inval("problem too large");
+    c->mesh = M;
+    c->prm = P;
+    c->stream = (cudaStream_t)P.stream;
+    t_err = &c->err;
+    setup(c.get());
+    return SIPG_OK;
+  });
+  if (st != SIPG_OK) {
+    if (!c->err.empty()) g_create_err = c->err;
+    for (void *p : c->allocs) cudaFree(p);
+    return st;
+  }
+  *out = c.release();
+  return SIPG_OK;
+}
+
+sipg_status sipg_destroy(sipg_ctx *c) {
+  if (!c) return SIPG_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) cudaFree(p);
+  delete c;
+  return SIPG_OK;
+}
+
+const char *sipg_last_error(const sipg_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+sipg_status sipg_num_levels(const sipg_ctx *c, int *nl) {
+  if (!c || !nl) return SIPG_EINVAL;
+  *nl = c->L + 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_num_dofs(const sipg_ctx *c, int level, int64_t *n) {
+  if (!level_ok(c, level) || !n) return SIPG_EINVAL;
+  *n = c->lv[level].ndofs;
+  return SIPG_OK;
+}
+
+sipg_status sipg_level_info(const sipg_ctx *c, int level, int *kind, int *degree, int m[3]) {
+  if (!level_ok(c, level)) return SIPG_EINVAL;
+  const Level &L = c->lv[level];
+  if (kind) *kind = L.kind;
+  if (degree) *degree = L.deg;
+  if (m)
+    for (int d = 0; d < 3; ++d) m[d] = L.m[d];
+  return SIPG_OK;
+}
+
+sipg_status sipg_lambda(const sipg_ctx *c, int level, double *lambda) {
+  if (!level_ok(c, level) || !lambda || !c->solver) return SIPG_EINVAL;
+  *lambda = c->lv[level].lambda;
+  return SIPG_OK;
+}
+
+sipg_status sipg_rhs(sipg_ctx *c, int kind, double *b) {
+  if (!c || !b || kind != 0) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    const Level &F = c->lv[c->L];
+    Mapping map(c->md);
+    std::vector<double> h, tau;
+    manufactured_rhs(map, F.n, tau, h);
+    CK(cudaMemcpyAsync(b, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_level_apply(sipg_ctx *c, int level, int precision, const void *u, void *v) {
+  if (!level_ok(c, level) || !u || !v || (precision != 0 && precision != 1)) return SIPG_EINVAL;
+  if (u == v) return SIPG_EINVAL;
+  if (level != c->L && !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    if (precision == 0)
+      apply_level<double>(c, level, (const double *)u, (double *)v, 0);
+    else
+      apply_level<float>(c, level, (const float *)u, (float *)v, 0);
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_operator_apply(sipg_ctx *c, int precision, const void *u, void *v) {
+  if (!c) return SIPG_EINVAL;
+  return sipg_level_apply(c, c->L, precision, u, v);
+}
+
+sipg_status sipg_inverse_diagonal(sipg_ctx *c, int level, int precision, void *d) {
+  if (!level_ok(c, level) || level == 0 || !d || !c->solver || (precision != 0 && precision != 1))
+    return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    const Level &L = c->lv[level];
+    CK(cudaMemcpyAsync(d, L.dinv[precision], L.ndofs * (precision ? 4 : 8), cudaMemcpyDeviceToDevice, c->stream));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_smooth(sipg_ctx *c, int level, const void *b, void *x, int nsteps) {
+  if (!level_ok(c, level) || level == 0 || !b || !x || nsteps < 1 || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    Level &L = c->lv[level];
+    const int pi = c->prm.precision;
+    const size_t bytes = L.ndofs * (pi ? 4 : 8);
+    CK(cudaMemcpyAsync(L.vx[pi], x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (pi == 0) {
+      double *xx = (double *)L.vx[0], *xt = (double *)L.vt[0];
+      chebyshev<double>(c, level, (const double *)b, xx, xt, nsteps, false);
+      CK(cudaMemcpyAsync(x, xx, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      float *xx = (float *)L.vx[1], *xt = (float *)L.vt[1];
+      chebyshev<float>(c, level, (const float *)b, xx, xt, nsteps, false);
+      CK(cudaMemcpyAsync(x, xx, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_restrict(sipg_ctx *c, int level, const void *r, void *rc) {
+  if (!level_ok(c, level) || level == 0 || !r || !rc || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    if (c->prm.precision == 0)
+      restrict_level<double>(c, level, (const double *)r, (double *)rc);
+    else
+      restrict_level<float>(c, level, (const float *)r, (float *)rc);
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_prolongate_add(sipg_ctx *c, int level, const void *xc, void *x) {
+  if (!level_ok(c, level) || level == 0 || !xc || !x || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    if (c->prm.precision == 0)
+      prolongate_level<double>(c, level, (const double *)xc, (double *)x);
+    else
+      prolongate_level<float>(c, level, (const float *)xc, (float *)x);
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_coarse_solve(sipg_ctx *c, const double *b, double *x) {
+  if (!c || !b || !x || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    CK((launch_dense_gemv<double, double>(c->Ainv, b, x, c->n0, c->stream)));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_vcycle(sipg_ctx *c, const double *r, double *z) {
+  if (!c || !r || !z || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    vcycle_fp64io(c, r, z);
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_solve(sipg_ctx *c, const double *b, double *x, double rtol, int maxit, int fixed_iters,
+                       sipg_solve_info *info) {
+  if (!c || !b || !x || !c->solver || maxit < 0 || fixed_iters < 0 || !(rtol >= 0)) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status { return solve_impl(c, b, x, rtol, maxit, fixed_iters, info); });
+}
+
+sipg_status sipg_solve_host(sipg_ctx *c, const double *bh, double *xh, double rtol, int maxit,
+                            sipg_solve_info *info) {
+  if (!c || !bh || !xh || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    const int64_t N = c->lv[c->L].ndofs;
+    CK(cudaMemcpyAsync(c->fb, bh, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->fx, 0, N * sizeof(double), c->stream));
+    const sipg_status st = solve_impl(c, c->fb, c->fx, rtol, maxit, 0, info);
+    CK(cudaMemcpyAsync(xh, c->fx, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return st;
+  });
+}
+
+sipg_status sipg_time_apply(sipg_ctx *c, int precision, const void *u, void *v, int repeats, float *ms_eval,
+                            float *ms_int) {
+  if (!c || !u || !v || repeats < 1 || (precision != 0 && precision != 1)) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    const Level &L = c->lv[c->L];
+    cudaEvent_t ev[3];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    float te = 0, ti = 0;
+    for (int r = 0; r < repeats; ++r) {
+      CK(cudaEventRecord(ev[0], c->stream));
+      if (precision == 0) {
+        DGArgs<double> a = dg_args<double>(c, L);
+        a.u = (const double *)u;
+        a.out = (double *)v;
+        CK(launch_dg_eval<double>(L.n, L.curved, a, c->stream));
+        CK(cudaEventRecord(ev[1], c->stream));
+        CK(launch_dg_integrate<double>(L.n, L.curved, a, c->stream));
+      } else {
+        DGArgs<float> a = dg_args<float>(c, L);
+        a.u = (const float *)u;
+        a.out = (float *)v;
+        CK(launch_dg_eval<float>(L.n, L.curved, a, c->stream));
+        CK(cudaEventRecord(ev[1], c->stream));
+        CK(launch_dg_integrate<float>(L.n, L.curved, a, c->stream));
+      }
+      CK(cudaEventRecord(ev[2], c->stream));
+      CK(cudaEventSynchronize(ev[2]));
+      float a1, a2;
+      CK(cudaEventElapsedTime(&a1, ev[0], ev[1]));
+      CK(cudaEventElapsedTime(&a2, ev[1], ev[2]));
+      te += a1;
+      ti += a2;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (ms_eval) *ms_eval = te / repeats;
+    if (ms_int) *ms_int = ti / repeats;
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_fma_peak(int precision, void *stream, double *flops) {
+  if (!flops || (precision != 0 && precision != 1)) return SIPG_EINVAL;
+  std::string dummy;
+  const cudaError_t e = fma_peak(precision, (cudaStream_t)stream, flops);
+  return e == cudaSuccess ? SIPG_OK : SIPG_ECUDA;
+}
+
+}  // extern "C"

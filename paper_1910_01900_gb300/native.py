@@ -1,0 +1,256 @@
+"""ctypes binding of libsipg (include/sipg.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Vectors are torch tensors on the
+context's device (or numpy arrays for the *_host calls); this module only
+passes their pointers and checks their sizes and dtypes.  Loading fails
+loudly when the shared library has not been built.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsipg.so")
+
+OK, EINVAL, ECUDA, ENOMEM, ENOTCONV, EBREAKDOWN, ETIMEOUT, ENAN = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ECUDA", "ENOMEM", "ENOTCONV", "EBREAKDOWN", "ETIMEOUT", "ENAN"]
+
+# every entry point the header declares (checked by the CPU test suite)
+EXPORTS = [
+    "sipg_default_params", "sipg_create", "sipg_destroy", "sipg_last_error", "sipg_num_levels",
+    "sipg_num_dofs", "sipg_level_info", "sipg_lambda", "sipg_rhs", "sipg_operator_apply",
+    "sipg_level_apply", "sipg_inverse_diagonal", "sipg_smooth", "sipg_restrict", "sipg_prolongate_add",
+    "sipg_coarse_solve", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
+]
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("deform", ctypes.c_int), ("amp", ctypes.c_double), ("mapping_degree", ctypes.c_int),
+                ("bc", ctypes.c_int * 6)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int), ("penalty_factor", ctypes.c_double), ("precision", ctypes.c_int),
+                ("p_coarsen", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("lambda_override", ctypes.c_double),
+                ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("r0_norm", ctypes.c_double),
+                ("r_norm", ctypes.c_double), ("rho", ctypes.c_double), ("n10", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("res_history", ctypes.c_double * 256)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsipg (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsipg.so is not built: run __graft_entry__.build() "
+                               "(python -m paper_1910_01900_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.sipg_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.sipg_default_params.restype = None
+        L.sipg_create.argtypes = [ctypes.POINTER(Mesh), ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        L.sipg_destroy.argtypes = [vp]
+        L.sipg_last_error.argtypes = [vp]
+        L.sipg_last_error.restype = ctypes.c_char_p
+        L.sipg_num_levels.argtypes = [vp, ctypes.POINTER(i32)]
+        L.sipg_num_dofs.argtypes = [vp, i32, ctypes.POINTER(i64)]
+        L.sipg_level_info.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32 * 3)]
+        L.sipg_lambda.argtypes = [vp, i32, ctypes.POINTER(dbl)]
+        L.sipg_rhs.argtypes = [vp, i32, vp]
+        L.sipg_operator_apply.argtypes = [vp, i32, vp, vp]
+        L.sipg_level_apply.argtypes = [vp, i32, i32, vp, vp]
+        L.sipg_inverse_diagonal.argtypes = [vp, i32, i32, vp]
+        L.sipg_smooth.argtypes = [vp, i32, vp, vp, i32]
+        L.sipg_restrict.argtypes = [vp, i32, vp, vp]
+        L.sipg_prolongate_add.argtypes = [vp, i32, vp, vp]
+        L.sipg_coarse_solve.argtypes = [vp, vp, vp]
+        L.sipg_vcycle.argtypes = [vp, vp, vp]
+        L.sipg_solve.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveInfo)]
+        L.sipg_solve_host.argtypes = [vp, vp, vp, dbl, i32, ctypes.POINTER(SolveInfo)]
+        L.sipg_time_apply.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_float)]
+        L.sipg_fma_peak.argtypes = [i32, vp, ctypes.POINTER(dbl)]
+        for name in EXPORTS:
+            if name not in ("sipg_default_params", "sipg_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class SipgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+def _ptr(t, dtype=None, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("expected %d elements, got %d" % (numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One SIPG problem: mesh, degree, level hierarchy, device data (sipg_create)."""
+
+    def __init__(self, m, degree, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
+                 precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
+                 operator_only=False, stream=None):
+        L = lib()
+        mesh = Mesh()
+        mm = tuple(m) if hasattr(m, "__len__") else (m, m, m)
+        for d in range(3):
+            mesh.m[d], mesh.lo[d], mesh.hi[d] = int(mm[d]), float(lo[d]), float(hi[d])
+        mesh.deform, mesh.amp, mesh.mapping_degree = int(deform), float(amp), 3
+        for s in range(6):
+            mesh.bc[s] = int(bc[s])
+        prm = Params()
+        L.sipg_default_params(ctypes.byref(prm))
+        prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
+        prm.cheb_degree, prm.eig_iters = int(cheb_degree), int(eig_iters)
+        prm.lambda_override, prm.operator_only = float(lambda_override), int(bool(operator_only))
+        prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
+        if st != OK:
+            raise SipgError(st, L.sipg_last_error(None).decode())
+        self.h = h
+        self.degree, self.precision = int(degree), int(precision)
+        self.m = mm
+
+    def _check(self, st):
+        if st != OK:
+            raise SipgError(st, lib().sipg_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sipg_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ queries
+    @property
+    def num_levels(self):
+        n = ctypes.c_int()
+        self._check(lib().sipg_num_levels(self.h, ctypes.byref(n)))
+        return n.value
+
+    def num_dofs(self, level=None):
+        level = self.num_levels - 1 if level is None else level
+        n = ctypes.c_int64()
+        self._check(lib().sipg_num_dofs(self.h, level, ctypes.byref(n)))
+        return n.value
+
+    def level_info(self, level):
+        kind, deg, m = ctypes.c_int(), ctypes.c_int(), (ctypes.c_int * 3)()
+        self._check(lib().sipg_level_info(self.h, level, ctypes.byref(kind), ctypes.byref(deg), ctypes.byref(m)))
+        return kind.value, deg.value, tuple(m)
+
+    def lam(self, level):
+        v = ctypes.c_double()
+        self._check(lib().sipg_lambda(self.h, level, ctypes.byref(v)))
+        return v.value
+
+    # ------------------------------------------------------------ hot path
+    def rhs(self, b, kind=0):
+        import torch
+        self._check(lib().sipg_rhs(self.h, kind, _ptr(b, torch.float64, self.num_dofs())))
+
+    def apply(self, u, v, precision=None):
+        import torch
+        precision = (0 if u.dtype == torch.float64 else 1) if precision is None else precision
+        dt = torch.float64 if precision == 0 else torch.float32
+        n = self.num_dofs()
+        self._check(lib().sipg_operator_apply(self.h, precision, _ptr(u, dt, n), _ptr(v, dt, n)))
+
+    def level_apply(self, level, u, v):
+        import torch
+        precision = 0 if u.dtype == torch.float64 else 1
+        n = self.num_dofs(level)
+        self._check(lib().sipg_level_apply(self.h, level, precision, _ptr(u, u.dtype, n), _ptr(v, u.dtype, n)))
+
+    def inverse_diagonal(self, level, d):
+        import torch
+        precision = 0 if d.dtype == torch.float64 else 1
+        self._check(lib().sipg_inverse_diagonal(self.h, level, precision, _ptr(d, d.dtype, self.num_dofs(level))))
+
+    def smooth(self, level, b, x, nsteps):
+        n = self.num_dofs(level)
+        self._check(lib().sipg_smooth(self.h, level, _ptr(b, x.dtype, n), _ptr(x, x.dtype, n), int(nsteps)))
+
+    def restrict(self, level, r, rc):
+        self._check(lib().sipg_restrict(self.h, level, _ptr(r, r.dtype, self.num_dofs(level)),
+                                        _ptr(rc, r.dtype, self.num_dofs(level - 1))))
+
+    def prolongate_add(self, level, xc, x):
+        self._check(lib().sipg_prolongate_add(self.h, level, _ptr(xc, x.dtype, self.num_dofs(level - 1)),
+                                              _ptr(x, x.dtype, self.num_dofs(level))))
+
+    def coarse_solve(self, b, x):
+        import torch
+        n = self.num_dofs(0)
+        self._check(lib().sipg_coarse_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
+
+    def vcycle(self, r, z):
+        import torch
+        n = self.num_dofs()
+        self._check(lib().sipg_vcycle(self.h, _ptr(r, torch.float64, n), _ptr(z, torch.float64, n)))
+
+    def solve(self, b, x, rtol=1e-10, maxit=200, fixed_iters=0, allow_notconv=False):
+        import torch
+        n = self.num_dofs()
+        info = SolveInfo()
+        st = lib().sipg_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n), float(rtol),
+                              int(maxit), int(fixed_iters), ctypes.byref(info))
+        if not (allow_notconv and st == ENOTCONV):
+            self._check(st)
+        return info
+
+    def solve_host(self, b_host, x_host, rtol=1e-10, maxit=200):
+        import numpy as np
+        n = self.num_dofs()
+        for a in (b_host, x_host):
+            if a.dtype != np.float64 or a.size != n or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host vectors must be contiguous float64 of length %d" % n)
+        info = SolveInfo()
+        self._check(lib().sipg_solve_host(self.h, ctypes.c_void_p(b_host.ctypes.data),
+                                          ctypes.c_void_p(x_host.ctypes.data), float(rtol), int(maxit),
+                                          ctypes.byref(info)))
+        return info
+
+    def time_apply(self, u, v, repeats=20):
+        import torch
+        precision = 0 if u.dtype == torch.float64 else 1
+        te, ti = ctypes.c_float(), ctypes.c_float()
+        n = self.num_dofs()
+        self._check(lib().sipg_time_apply(self.h, precision, _ptr(u, u.dtype, n), _ptr(v, u.dtype, n),
+                                          int(repeats), ctypes.byref(te), ctypes.byref(ti)))
+        return te.value, ti.value
+
+
+def fma_peak(precision, stream=None):
+    v = ctypes.c_double()
+    st = lib().sipg_fma_peak(int(precision), ctypes.c_void_p(stream.cuda_stream if stream else 0), ctypes.byref(v))
+    if st != OK:
+        raise SipgError(st, "fma peak probe failed")
+    return v.value

@@ -1,0 +1,254 @@
+"""GPU parity: libsipg (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative 2-norm): FP64 <= 1e-12, FP32 <= 1e-5 for single operator
+applications; whole-cycle and solve comparisons use the bounds stated at each
+test (more operations, same arithmetic up to summation order).
+"""
+import numpy as np
+import pytest
+
+import sipg_inputs
+from oracle.dg import SIPG
+from oracle.fe import FESpace
+from oracle.mesh import Mesh
+from oracle.multigrid import CPHMultigrid, chebyshev, fcg
+from oracle.transfer import c_transfer, fe_transfer
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _ctx(*a, **kw):
+    from paper_1910_01900_gb300 import Context
+    return Context(*a, **kw)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def gpu(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(DEV, dtype)
+
+
+# meshes spanning several thread blocks with a ragged last block for every degree
+SHAPES = {1: (6, 5, 5), 2: (5, 4, 3), 3: (5, 3, 3), 4: (4, 3, 3), 5: (3, 3, 3), 6: (4, 2, 2), 7: (3, 2, 2),
+          8: (3, 2, 2)}
+
+
+@pytest.mark.parametrize("deform", [0, 1])
+@pytest.mark.parametrize("k", range(1, 9))
+def test_operator_apply_fp64_fp32(k, deform):
+    m = SHAPES[k]
+    lo, hi = (0.0, -0.5, 0.2), (1.0, 1.0, 1.4)
+    bc = (0, 1, 0, 0, 1, 0)
+    ctx = _ctx(m, k, deform=deform, lo=lo, hi=hi, bc=bc, operator_only=True)
+    u = sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_APPLY)
+    ref = SIPG(Mesh(m, lo=lo, hi=hi, deform=deform, bc=bc), k).apply(u)
+    v = torch.empty(len(u), dtype=torch.float64, device=DEV)
+    ctx.apply(gpu(u), v)
+    assert rel(v.cpu().numpy(), ref) <= 1e-12
+    v32 = torch.empty(len(u), dtype=torch.float32, device=DEV)
+    ctx.apply(gpu(u, torch.float32), v32)
+    assert rel(v32.cpu().numpy(), ref) <= 1e-5
+
+
+def test_single_cell_and_pure_neumann():
+    for k in (1, 4, 8):
+        ctx = _ctx(1, k, operator_only=True)
+        u = sipg_inputs.uniform(ctx.num_dofs(), 7)
+        v = torch.empty(len(u), dtype=torch.float64, device=DEV)
+        ctx.apply(gpu(u), v)
+        assert rel(v.cpu().numpy(), SIPG(Mesh(1), k).apply(u)) <= 1e-12
+    ctx = _ctx(3, 3, deform=1, bc=(1,) * 6, operator_only=True)
+    one = torch.ones(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+    v = torch.empty_like(one)
+    ctx.apply(one, v)
+    u = sipg_inputs.uniform(ctx.num_dofs(), 3)
+    w = torch.empty_like(one)
+    ctx.apply(gpu(u), w)
+    assert v.abs().max().item() <= 1e-12 * w.abs().max().item()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_1910_01900_gb300 import SipgError
+    with pytest.raises(SipgError):
+        _ctx(0, 3)
+    with pytest.raises(SipgError):
+        _ctx(2, 9)
+    ctx = _ctx(2, 2, operator_only=True)
+    with pytest.raises(SipgError):
+        ctx.vcycle(torch.zeros(ctx.num_dofs(), dtype=torch.float64, device=DEV),
+                   torch.zeros(ctx.num_dofs(), dtype=torch.float64, device=DEV))
+
+
+def _hierarchy(m, k, deform, **kw):
+    ctx = _ctx(m, k, deform=deform, **kw)
+    mg = CPHMultigrid(Mesh(m, deform=deform), k,
+                      lambdas=[kw["lambda_override"]] * 16 if kw.get("lambda_override") else None)
+    return ctx, mg
+
+
+@pytest.mark.parametrize("m,k,deform", [(4, 3, 0), (6, 4, 1), (4, 5, 0)])
+def test_levels_diagonals_and_fe_apply(m, k, deform):
+    ctx, mg = _hierarchy(m, k, deform, lambda_override=2.0)
+    assert ctx.num_levels == len(mg.levels)
+    for l, lev in enumerate(mg.levels):
+        kind, deg, mm = ctx.level_info(l)
+        assert (kind == 0) == (lev.kind == "dg") and ctx.num_dofs(l) == lev.n
+        u = sipg_inputs.uniform(lev.n, 100 + l)
+        if lev.kind == "fe":
+            u[lev.space.constrained] *= 0.5   # identity rows are exercised too
+        ref = lev.apply(u)
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            v = torch.empty(lev.n, dtype=dt, device=DEV)
+            ctx.level_apply(l, gpu(u, dt), v)
+            assert rel(v.cpu().numpy(), ref) <= tol, (l, dt)
+        if l > 0:
+            d = torch.empty(lev.n, dtype=torch.float64, device=DEV)
+            ctx.inverse_diagonal(l, d)
+            assert rel(d.cpu().numpy(), lev.dinv) <= 1e-12
+
+
+@pytest.mark.parametrize("m,k,deform", [(6, 4, 0), (6, 5, 1), (8, 2, 0)])
+def test_transfers_match_sparse_matrices(m, k, deform):
+    ctx, mg = _hierarchy(m, k, deform, lambda_override=2.0)
+    for l in range(1, len(mg.levels)):
+        P = mg.levels[l].P
+        r = sipg_inputs.uniform(mg.levels[l].n, 200 + l)
+        rc = torch.empty(mg.levels[l - 1].n, dtype=torch.float64, device=DEV)
+        ctx.restrict(l, gpu(r), rc)
+        assert rel(rc.cpu().numpy(), P.T @ r) <= 1e-12, l
+        xc = sipg_inputs.uniform(mg.levels[l - 1].n, 300 + l)
+        sp = mg.levels[l - 1].space
+        xc[sp.constrained] = 0.0
+        x0 = sipg_inputs.uniform(mg.levels[l].n, 400 + l)
+        if mg.levels[l].kind == "fe":
+            x0[mg.levels[l].space.constrained] = 0.0
+        x = gpu(x0)
+        ctx.prolongate_add(l, gpu(xc), x)
+        assert rel(x.cpu().numpy(), x0 + P @ xc) <= 1e-12, l
+
+
+def test_coarse_solve_and_lambda_estimates():
+    m, k = 6, 4
+    ctx, mg = _hierarchy(m, k, 1)
+    b = sipg_inputs.uniform(mg.levels[0].n, 5)
+    b[mg.levels[0].space.constrained] = 0.0
+    x = torch.empty(len(b), dtype=torch.float64, device=DEV)
+    ctx.coarse_solve(gpu(b), x)
+    assert rel(x.cpu().numpy(), mg.coarse.solve(b)) <= 1e-12
+    for l in range(1, len(mg.levels)):
+        assert abs(ctx.lam(l) - mg.levels[l].lam) <= 1e-10 * mg.levels[l].lam, l
+
+
+@pytest.mark.parametrize("level_from_top", [0, 1])
+def test_chebyshev_smoother(level_from_top):
+    m, k = 4, 4
+    ctx, mg = _hierarchy(m, k, 1, lambda_override=1.7)
+    l = len(mg.levels) - 1 - level_from_top
+    lev = mg.levels[l]
+    b = sipg_inputs.uniform(lev.n, 11)
+    x0 = sipg_inputs.uniform(lev.n, 12)
+    if lev.kind == "fe":
+        b[lev.space.constrained] = 0.0
+        x0[lev.space.constrained] = 0.0
+    ref = chebyshev(lev.apply, lev.dinv, b, x0, 1.7, 5)
+    x = gpu(x0)
+    ctx.smooth(l, gpu(b), x, 5)
+    assert rel(x.cpu().numpy(), ref) <= 1e-11
+
+
+@pytest.mark.parametrize("m,k,deform", [(4, 3, 0), (6, 3, 1), (4, 2, 1)])
+def test_vcycle_fp64_and_fp32(m, k, deform):
+    ctx, mg = _hierarchy(m, k, deform, lambda_override=2.2)
+    r = sipg_inputs.uniform(mg.levels[-1].n, 21)
+    ref = mg.vcycle(r)
+    z = torch.empty(len(r), dtype=torch.float64, device=DEV)
+    ctx.vcycle(gpu(r), z)
+    assert rel(z.cpu().numpy(), ref) <= 1e-11
+    ctx32 = _ctx(m, k, deform=deform, precision=1, lambda_override=2.2)
+    ctx32.vcycle(gpu(r), z)
+    assert rel(z.cpu().numpy(), ref) <= 1e-5
+
+
+def test_fixed_iteration_fcg_matches_oracle():
+    m, k = 4, 3
+    ctx, mg = _hierarchy(m, k, 0, lambda_override=2.2)
+    b = sipg_inputs.uniform(mg.levels[-1].n, sipg_inputs.SEED_RHS)
+    ref, _, hist = fcg(mg.levels[-1].apply, b, np.zeros_like(b), mg.vcycle, fixed_iters=3)
+    x = torch.zeros(len(b), dtype=torch.float64, device=DEV)
+    info = ctx.solve(gpu(b), x, fixed_iters=3)
+    assert info.iterations == 3
+    assert rel(x.cpu().numpy(), ref) <= 1e-11
+    assert abs(info.res_history[3] - hist[3]) <= 1e-9 * hist[3]
+
+
+@pytest.mark.parametrize("m,k,deform", [(4, 3, 0), (4, 3, 1), (6, 2, 0)])
+def test_solve_to_1e10_same_iterations_as_oracle(m, k, deform):
+    ctx, mg = _hierarchy(m, k, deform)
+    b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+    ctx.rhs(b)
+    bo = mg.levels[-1].space.rhs(lambda x: 3 * np.pi ** 2 * np.prod(np.sin(np.pi * x), axis=-1))
+    assert rel(b.cpu().numpy(), bo) <= 1e-12
+    ref, it, hist = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
+    x = torch.zeros_like(b)
+    info = ctx.solve(b, x, rtol=1e-10)
+    assert info.converged and info.iterations == it
+    assert rel(x.cpu().numpy(), ref) <= 1e-10
+    # mixed precision: FP32 cycle, FP64 residual, same tolerance reached
+    ctx32 = _ctx(m, k, deform=deform, precision=1)
+    x32 = torch.zeros_like(b)
+    info32 = ctx32.solve(b, x32, rtol=1e-10)
+    assert info32.converged and abs(info32.iterations - it) <= 1
+    assert rel(x32.cpu().numpy(), ref) <= 1e-8
+
+
+def test_solve_host_round_trip_and_nan_rejected():
+    ctx = _ctx(4, 2)
+    b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+    ctx.rhs(b)
+    x = torch.zeros_like(b)
+    ctx.solve(b, x)
+    bh = b.cpu().numpy().copy()
+    xh = np.zeros_like(bh)
+    ctx.solve_host(bh, xh)
+    assert rel(xh, x.cpu().numpy()) <= 1e-13
+    from paper_1910_01900_gb300 import SipgError
+    bh[3] = np.nan
+    with pytest.raises(SipgError):
+        ctx.solve_host(bh, xh)
+
+
+def _sampled_apply_check(m, k, deform, cells, precision=0):
+    ctx = _ctx(m, k, deform=deform, operator_only=True)
+    n = ctx.num_dofs()
+    u = sipg_inputs.uniform(n, sipg_inputs.SEED_APPLY)
+    dt = torch.float64 if precision == 0 else torch.float32
+    v = torch.empty(n, dtype=dt, device=DEV)
+    ctx.apply(gpu(u, dt), v)
+    vv = v.cpu().numpy().astype(np.float64)
+    ref = SIPG(Mesh(m, deform=deform), k).apply(u, cells=cells)
+    n3 = (k + 1) ** 3
+    sel = np.concatenate([np.arange(c * n3, (c + 1) * n3) for c in cells])
+    return rel(vv[sel], ref[sel])
+
+
+def test_full_size_curved16_k5_sampled():
+    """The 16^3 curved k=5 workload at full size, checked on sampled cells."""
+    m = 16
+    cells = [0, 15, 255, 256 * 7 + 16 * 5 + 9, 4095, 2048 + 3]
+    assert _sampled_apply_check(m, 5, 1, cells) <= 1e-12
+    assert _sampled_apply_check(m, 5, 1, cells, precision=1) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 8])
+def test_sweep_sizes_sampled(k):
+    """The ~16 MDoF apply-sweep meshes at full size, sampled cells (curved)."""
+    m = sipg_inputs.SWEEP_M[k]
+    E = m ** 3
+    cells = [0, m - 1, m * m * (m // 2) + m * 3 + 1, E // 2 + 7, E - 1]
+    assert _sampled_apply_check(m, k, 1, cells) <= 1e-12
