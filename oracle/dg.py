@@ -88,6 +88,8 @@ class SIPG:
     def tau_of(self, cells):
         """tau_e of the given cells only (each cell's value depends on that cell alone)."""
         cells = np.asarray(cells)
+        if self._tau is None and len(cells) > self.mesh.n_cells // 4:
+            return self.tau[cells]
         if self._tau is not None:
             return self._tau[cells]
         uniq, inv = np.unique(cells, return_inverse=True)
