@@ -185,6 +185,29 @@ sipg_status sipg_time_apply(sipg_ctx *ctx, int precision, const void *u_dev, voi
  * FLOP/s (2 per FMA).  Not part of the method: used for the roofline. */
 sipg_status sipg_fma_peak(int precision, void *stream, double *flops_per_s);
 
+/* Operator apply that allocates no device memory.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc when
+ * they need A u -- for example code inside a framework whose caching allocator
+ * already holds the GPU's memory, or a time-stepping loop that must not
+ * allocate once it runs.  Computes v = A u, the same FP64 operator as
+ * sipg_operator_apply for affine cells (mesh->deform must be 0), with
+ * penalty_factor as in sipg_params.  The caller passes the device vectors u
+ * and v (length m0 m1 m2 (degree+1)^3, DG order, must not overlap); every
+ * other buffer lives in one static device array of 64 MiB that each GPU
+ * loading the library holds until the process exits.  Problems whose scratch
+ * (3 (k+1)^3 + 12 (k+1)^2 + 1 doubles per cell, plus small tables) exceeds
+ * 64 MiB are rejected with SIPG_EINVAL (about 1.4 million DoF at degree 3).
+ * The first call on a device looks up the array's device address and uploads
+ * the 1D tables (both synchronous); make that first call before any stream
+ * capture.  All calls share the one array: two calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race and give wrong
+ * results; calls ordered on one stream are safe.  Nothing in the array needs
+ * to start at zero (every call rewrites what it reads).  Work is queued on
+ * `stream` (cudaStream_t, NULL = legacy default stream); on failure
+ * sipg_last_error(NULL) describes it. */
+sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int degree, double penalty_factor,
+                                        const double *u_dev, double *v_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -171,4 +171,7 @@ cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cud
 
 cudaError_t fma_peak(int precision, cudaStream_t s, double *flops);
 
+// Text returned by sipg_last_error(NULL).
+void set_global_error(const std::string &msg);
+
 }  // namespace sipg

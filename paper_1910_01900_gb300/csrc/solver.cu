@@ -34,6 +34,8 @@ struct sipg_ctx {
 
 static std::string g_create_err;
 
+void sipg::set_global_error(const std::string &msg) { g_create_err = msg; }
+
 namespace {
 
 struct Fail {

@@ -20,6 +20,7 @@ EXPORTS = [
     "sipg_num_dofs", "sipg_level_info", "sipg_lambda", "sipg_rhs", "sipg_operator_apply",
     "sipg_level_apply", "sipg_inverse_diagonal", "sipg_smooth", "sipg_restrict", "sipg_prolongate_add",
     "sipg_coarse_solve", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
+    "sipg_operator_apply_noalloc",
 ]
 
 
@@ -78,6 +79,7 @@ def lib():
         L.sipg_time_apply.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_float)]
         L.sipg_fma_peak.argtypes = [i32, vp, ctypes.POINTER(dbl)]
+        L.sipg_operator_apply_noalloc.argtypes = [ctypes.POINTER(Mesh), i32, dbl, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("sipg_default_params", "sipg_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -246,6 +248,30 @@ class Context:
         self._check(lib().sipg_time_apply(self.h, precision, _ptr(u, u.dtype, n), _ptr(v, u.dtype, n),
                                           int(repeats), ctypes.byref(te), ctypes.byref(ti)))
         return te.value, ti.value
+
+
+def operator_apply_noalloc(m, degree, u, v, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
+                           penalty_factor=1.0, stream=None):
+    """v = A u (FP64, affine cells) through sipg_operator_apply_noalloc.
+
+    For callers that cannot allocate device memory when they need A u: the
+    library uses its static 64 MiB device scratch instead of allocating.
+    Calls that overlap on the GPU race (they share that scratch).
+    """
+    import torch
+    mesh = Mesh()
+    mm = tuple(m) if hasattr(m, "__len__") else (m, m, m)
+    for d in range(3):
+        mesh.m[d], mesh.lo[d], mesh.hi[d] = int(mm[d]), float(lo[d]), float(hi[d])
+    mesh.deform, mesh.amp, mesh.mapping_degree = 0, 0.0, 3
+    for s in range(6):
+        mesh.bc[s] = int(bc[s])
+    n = mm[0] * mm[1] * mm[2] * (int(degree) + 1) ** 3
+    st = lib().sipg_operator_apply_noalloc(ctypes.byref(mesh), int(degree), float(penalty_factor),
+                                           _ptr(u, torch.float64, n), _ptr(v, torch.float64, n),
+                                           ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))
+    if st != OK:
+        raise SipgError(st, lib().sipg_last_error(None).decode())
 
 
 def fma_peak(precision, stream=None):
