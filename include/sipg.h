@@ -83,6 +83,10 @@ typedef struct {
   int smoother;            /* 0: Chebyshev-Jacobi (Algorithm 3)               */
   int operator_only;       /* 1: build only the finest DG operator (for
                               operator_apply); the solver calls then fail   */
+  int autotune;            /* 1: at setup, time the compiled tile shapes
+                              (cells per thread block) of both DG passes in
+                              both precisions and keep the fastest; cached
+                              per (degree, geometry) for the process       */
   void *stream;            /* cudaStream_t or NULL                             */
 } sipg_params;
 
@@ -179,6 +183,38 @@ sipg_status sipg_solve_host(sipg_ctx *ctx, const double *b_host, double *x_host,
  * DG integration pass, in milliseconds (for roofline accounting). */
 sipg_status sipg_time_apply(sipg_ctx *ctx, int precision, const void *u_dev, void *v_dev,
                             int repeats, float *ms_eval, float *ms_integrate);
+
+/* ---- Many problems at once (not in the paper, whose solver handles one
+ * problem per run; each problem's method is unchanged).  A batch holds nprob
+ * independent problems -- uneven meshes and degrees, or the same mesh repeated
+ * for many right-hand sides.  meshes[i], params[i] describe problem i (all
+ * affine or all curved; one precision for all; each needs a Dirichlet side);
+ * params[0].stream is the stream of the batched work.  The finest-level
+ * operators of all problems run as one persistent launch per pass (a fixed
+ * grid walking a work list of (problem, cell block) items, longest first);
+ * the flexible-CG iterations run in lockstep with batched inner products and
+ * updates and each problem's V-cycle (a CUDA graph) on its own stream. */
+typedef struct sipg_batch sipg_batch;
+sipg_status sipg_batch_create(int nprob, const sipg_mesh *meshes, const sipg_params *params, sipg_batch **out);
+sipg_status sipg_batch_destroy(sipg_batch *batch);
+const char *sipg_batch_last_error(const sipg_batch *batch);
+/* The context of problem i (owned by the batch; do not destroy it). */
+sipg_status sipg_batch_context(sipg_batch *batch, int i, sipg_ctx **ctx);
+/* v[i] = A_i u[i] (FP64, finest level) for every problem: two launches total. */
+sipg_status sipg_batch_apply(sipg_batch *batch, const double *const *u_dev, double *const *v_dev);
+/* Solve A_i x[i] = b[i] for every problem to ||r||/||r0|| <= rtol (x[i] holds
+ * the start vector); infos (array of nprob, may be NULL) gets each problem's
+ * history.  Status as sipg_solve, worst over the problems. */
+sipg_status sipg_batch_solve(sipg_batch *batch, const double *const *b_dev, double *const *x_dev, double rtol,
+                             int maxit, sipg_solve_info *infos);
+
+/* Cells per thread block the finest-level DG pass uses (pass 0 evaluation,
+ * 1 integration) in the given precision: the autotuned value or the default. */
+sipg_status sipg_tile_shape(const sipg_ctx *ctx, int precision, int pass, int *cells_per_block);
+
+/* Number of kernel launches (and CUDA-graph launches) the library has issued
+ * in this process so far, all contexts together.  For launch accounting. */
+sipg_status sipg_launch_count(unsigned long long *n);
 
 /* Peak arithmetic probe: runs an independent-FMA loop on every SM for the
  * given precision (0 FP64 DFMA, 1 FP32 FFMA) and returns the measured rate in

@@ -15,5 +15,7 @@ cudaError_t launch_dg_integrate<float>(int n, bool curved, const DGArgs<float> &
 }
 template <>
 int dg_cells_per_block<float>(int n) { return default_cb(n); }
+template <>
+cudaError_t prepare_dg_kernels<float>() { return prep_dg_all<float>(); }
 
 }  // namespace sipg

@@ -15,6 +15,8 @@ cudaError_t launch_dg_integrate<double>(int n, bool curved, const DGArgs<double>
 }
 template <>
 int dg_cells_per_block<double>(int n) { return default_cb(n); }
+template <>
+cudaError_t prepare_dg_kernels<double>() { return prep_dg_all<double>(); }
 
 cudaError_t launch_dg_diag(int n, bool curved, const DGArgs<double> &a, double *diag, cudaStream_t s) {
   const Rules1D &r = rules(n);
@@ -49,6 +51,7 @@ cudaError_t launch_dg_diag(int n, bool curved, const DGArgs<double> &a, double *
       return cudaErrorInvalidValue;
   }
 #undef SIPG_DIAG_CASE
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -31,14 +31,14 @@
 
 namespace sipg {
 
-template <typename T, int N, bool CURVED, int CB>
-__global__ void __launch_bounds__(CB *N *N) dg_eval_kernel(const DGArgs<T> a) {
-  constexpr int N2 = N * N, N3 = N2 * N, NT = CB * N2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sm = reinterpret_cast<T *>(smem_raw);
+// Evaluation pass for the cells cell0 .. cell0+ncta-1 of one problem, on a
+// thread block of blockDim.x >= ncta * N^2 threads with 4 ncta N^3 values of
+// shared memory at sm.  Shared by the per-problem and the batched kernels.
+template <typename T, int N, bool CURVED>
+__device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0, const int ncta, T *sm) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
-  const int cell0 = blockIdx.x * CB;
-  const int ncta = min(CB, a.ncells - cell0);
   const bool act = cl < ncta;
   T *su = sm + cl * 4 * N3;
 
@@ -130,14 +130,12 @@ __global__ void __launch_bounds__(CB *N *N) dg_eval_kernel(const DGArgs<T> a) {
   }
 }
 
-template <typename T, int N, bool CURVED, int CB>
-__global__ void __launch_bounds__(CB *N *N) dg_integrate_kernel(const DGArgs<T> a) {
-  constexpr int N2 = N * N, N3 = N2 * N, NT = CB * N2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sm = reinterpret_cast<T *>(smem_raw);
+// Integration pass (same thread and shared-memory contract as the evaluation).
+template <typename T, int N, bool CURVED>
+__device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int cell0, const int ncta, T *sm) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
-  const int cell0 = blockIdx.x * CB;
-  const int ncta = min(CB, a.ncells - cell0);
   const bool act = cl < ncta;
   T *st = sm + cl * 4 * N3;   // value accumulator, then the integrated tile
   T *sg = st + N3;            // three gradient components
@@ -283,6 +281,20 @@ __global__ void __launch_bounds__(CB *N *N) dg_integrate_kernel(const DGArgs<T> 
       a.out[i] = v;
     }
   }
+}
+
+template <typename T, int N, bool CURVED, int CB>
+__global__ void __launch_bounds__(CB *N *N) dg_eval_kernel(const DGArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * CB;
+  dg_eval_body<T, N, CURVED>(a, cell0, min(CB, a.ncells - cell0), reinterpret_cast<T *>(smem_raw));
+}
+
+template <typename T, int N, bool CURVED, int CB>
+__global__ void __launch_bounds__(CB *N *N) dg_integrate_kernel(const DGArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * CB;
+  dg_integrate_body<T, N, CURVED>(a, cell0, min(CB, a.ncells - cell0), reinterpret_cast<T *>(smem_raw));
 }
 
 // Diagonal of the DG operator (setup, FP64), one thread per DoF: the cell

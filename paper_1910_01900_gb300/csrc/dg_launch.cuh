@@ -11,18 +11,43 @@ static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s) {
   const size_t smem = (size_t)CB * 4 * N3 * sizeof(T);
   const int grid = (a.ncells + CB - 1) / CB;
   if (grid == 0) return cudaSuccess;
-  if (integrate) {
-    auto k = dg_integrate_kernel<T, N, CURVED, CB>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, CB * N * N, smem, s>>>(a);
-  } else {
-    auto k = dg_eval_kernel<T, N, CURVED, CB>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, CB * N * N, smem, s>>>(a);
-  }
+  if (integrate)
+    dg_integrate_kernel<T, N, CURVED, CB><<<grid, CB * N * N, smem, s>>>(a);
+  else
+    dg_eval_kernel<T, N, CURVED, CB><<<grid, CB * N * N, smem, s>>>(a);
+  note_launch();
   return cudaGetLastError();
+}
+
+// Opt every compiled tile shape into its dynamic shared memory size (once per
+// device, before any launch or stream capture).
+template <typename T, int N, bool CURVED, int CB>
+static cudaError_t prep_dg() {
+  const int smem = CB * 4 * N * N * N * (int)sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(dg_integrate_kernel<T, N, CURVED, CB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(dg_eval_kernel<T, N, CURVED, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <typename T, int N>
+static cudaError_t prep_dg_n() {
+  constexpr int D = default_cb(N);
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t r : {prep_dg<T, N, false, D>(), prep_dg<T, N, true, D>(), prep_dg<T, N, false, 1>(),
+                        prep_dg<T, N, true, 1>(), prep_dg<T, N, false, 2 * D>(), prep_dg<T, N, true, 2 * D>(),
+                        prep_dg<T, N, false, (D + 1) / 2>(), prep_dg<T, N, true, (D + 1) / 2>()})
+    if (r != cudaSuccess) e = r;
+  return e;
+}
+
+template <typename T>
+static cudaError_t prep_dg_all() {
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t r : {prep_dg_n<T, 2>(), prep_dg_n<T, 3>(), prep_dg_n<T, 4>(), prep_dg_n<T, 5>(),
+                        prep_dg_n<T, 6>(), prep_dg_n<T, 7>(), prep_dg_n<T, 8>(), prep_dg_n<T, 9>()})
+    if (r != cudaSuccess) e = r;
+  return e;
 }
 
 template <typename T, int N, bool CURVED>

@@ -236,46 +236,71 @@ __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__
   xf[gid] += sum;
 }
 
-// p/h restriction, cell part: for every coarse cell and coarse node j, the sum
-// over its fine cells (1 for p, 8 children for h) and their nodes i of
-// P_e[i][j] r_f[node i] / multiplicity(node i) -- the transposed, weighted
-// scatter of Section 3.2.  The node pass then sums the coarse cells.
+// p/h restriction, cell part, by sum factorisation: one thread block per
+// coarse cell visits its fine cells (1 for p, 8 children for h); for each it
+// loads the fine nodal values weighted by 1/multiplicity (the transposed,
+// weighted scatter of Section 3.2; the weight is a product of per-direction
+// factors 1 or 1/2, exact) and contracts them with the 1D matrix P1^T along x,
+// y and z.  The coarse cell's local sums go to the element buffer; the node
+// pass then sums the coarse cells sharing each coarse node.
 template <typename T>
 __global__ void fe_restrict_cells_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ rf,
                                          T *__restrict__ ebuf) {
-  const int nf = G.pf + 1, nc = G.pc + 1, nc3 = nc * nc * nc;
-  const long ncc = (long)G.mc[0] * G.mc[1] * G.mc[2];
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= ncc * nc3) return;
-  const int cc = (int)(idx / nc3), j = (int)(idx - (long)cc * nc3);
-  const int jj[3] = {j % nc, (j / nc) % nc, j / (nc * nc)};
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const int nf = G.pf + 1, nc = G.pc + 1;
+  const int nf3 = nf * nf * nf, nc3 = nc * nc * nc;
+  T *A = sm;                        // nf^3
+  T *B = A + nf3;                   // nf^2 nc   [iz][iy][jx]
+  T *C = B + nf * nf * nc;          // nf nc^2   [iz][jy][jx]
+  T *acc = C + nf * nc * nc;        // nc^3
+  const int cc = blockIdx.x;
   const int cijk[3] = {cc % G.mc[0], (cc / G.mc[0]) % G.mc[1], cc / (G.mc[0] * G.mc[1])};
   const int nch = G.kind == 2 ? 2 : 1;
-  T sum = T(0);
-  for (int kz = 0; kz < nch; ++kz)
-    for (int ky = 0; ky < nch; ++ky)
-      for (int kx = 0; kx < nch; ++kx) {
-        const int child[3] = {kx, ky, kz};
-        int fijk[3];
-        for (int d = 0; d < 3; ++d) fijk[d] = G.kind == 2 ? 2 * cijk[d] + child[d] : cijk[d];
-        for (int iz = 0; iz < nf; ++iz)
-          for (int iy = 0; iy < nf; ++iy)
-            for (int ix = 0; ix < nf; ++ix) {
-              const int ii[3] = {ix, iy, iz};
-              int g[3];
-              T w = T(1);
-              int mult = 1;
-              for (int d = 0; d < 3; ++d) {
-                g[d] = fijk[d] * G.pf + ii[d];
-                w *= P1[((size_t)child[d] * nf + ii[d]) * nc + jj[d]];
-                if (ii[d] == 0 && fijk[d] > 0) mult *= 2;
-                if (ii[d] == G.pf && fijk[d] < G.mf[d] - 1) mult *= 2;
-              }
-              if (node_constrained(g, G.gf, G.bc)) continue;
-              sum += w * rf[g[0] + (size_t)G.gf[0] * (g[1] + (size_t)G.gf[1] * g[2])] / T(mult);
-            }
+  for (int j = threadIdx.x; j < nc3; j += blockDim.x) acc[j] = T(0);
+  for (int ch = 0; ch < nch * nch * nch; ++ch) {
+    const int child[3] = {ch & (nch - 1), (ch / nch) & (nch - 1), ch / (nch * nch)};
+    int fijk[3];
+    for (int d = 0; d < 3; ++d) fijk[d] = G.kind == 2 ? 2 * cijk[d] + child[d] : cijk[d];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf3; i += blockDim.x) {
+      const int ii[3] = {i % nf, (i / nf) % nf, i / (nf * nf)};
+      int g[3];
+      T w = T(1);
+      for (int d = 0; d < 3; ++d) {
+        g[d] = fijk[d] * G.pf + ii[d];
+        if ((ii[d] == 0 && fijk[d] > 0) || (ii[d] == G.pf && fijk[d] < G.mf[d] - 1)) w *= T(0.5);
       }
-  ebuf[idx] = sum;
+      A[i] = node_constrained(g, G.gf, G.bc)
+                 ? T(0)
+                 : w * rf[g[0] + (size_t)G.gf[0] * (g[1] + (size_t)G.gf[1] * g[2])];
+    }
+    __syncthreads();
+    const T *Px = P1 + (size_t)child[0] * nf * nc, *Py = P1 + (size_t)child[1] * nf * nc,
+            *Pz = P1 + (size_t)child[2] * nf * nc;
+    for (int o = threadIdx.x; o < nf * nf * nc; o += blockDim.x) {   // B[iz][iy][jx]
+      const int jx = o % nc, r = o / nc;
+      T s = T(0);
+      for (int ix = 0; ix < nf; ++ix) s += Px[ix * nc + jx] * A[r * nf + ix];
+      B[o] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nf * nc * nc; o += blockDim.x) {   // C[iz][jy][jx]
+      const int jx = o % nc, jy = (o / nc) % nc, iz = o / (nc * nc);
+      T s = T(0);
+      for (int iy = 0; iy < nf; ++iy) s += Py[iy * nc + jy] * B[(iz * nf + iy) * nc + jx];
+      C[o] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nc3; o += blockDim.x) {   // acc[jz][jy][jx]
+      const int jxy = o % (nc * nc), jz = o / (nc * nc);
+      T s = T(0);
+      for (int iz = 0; iz < nf; ++iz) s += Pz[iz * nc + jz] * C[iz * nc * nc + jxy];
+      acc[o] += s;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nc3; j += blockDim.x) ebuf[(size_t)cc * nc3 + j] = acc[j];
 }
 
 // ---------------------------------------------------------------- launchers
@@ -285,11 +310,28 @@ static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s) {
   const size_t smem = (size_t)CB * 4 * N3 * sizeof(T);
   const int grid = (a.ncells + CB - 1) / CB;
   if (grid == 0) return cudaSuccess;
-  auto k = fe_cell_kernel<T, N, CURVED, CB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, CB * N * N, smem, s>>>(a);
+  fe_cell_kernel<T, N, CURVED, CB><<<grid, CB * N * N, smem, s>>>(a);
+  note_launch();
   return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t prep_fe_n() {
+  constexpr int CB = default_cb(N);
+  const int smem = CB * 4 * N * N * N * (int)sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(fe_cell_kernel<T, N, false, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fe_cell_kernel<T, N, true, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t prepare_fe_kernels() {
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t r : {prep_fe_n<double, 2>(), prep_fe_n<double, 3>(), prep_fe_n<double, 4>(), prep_fe_n<double, 5>(),
+                        prep_fe_n<double, 6>(), prep_fe_n<double, 7>(), prep_fe_n<double, 8>(), prep_fe_n<double, 9>(),
+                        prep_fe_n<float, 2>(), prep_fe_n<float, 3>(), prep_fe_n<float, 4>(), prep_fe_n<float, 5>(),
+                        prep_fe_n<float, 6>(), prep_fe_n<float, 7>(), prep_fe_n<float, 8>(), prep_fe_n<float, 9>()})
+    if (r != cudaSuccess) e = r;
+  return e;
 }
 
 template <int N, bool CURVED>
@@ -304,6 +346,7 @@ static cudaError_t run_fe_diag(const FEArgs<double> &a, cudaStream_t s) {
   const long total = (long)a.ncells * N * N * N;
   const int bs = 128;
   fe_diag_cells_kernel<N, CURVED><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(a, tabs, tabs + N * N);
+  note_launch();
   e = cudaGetLastError();
   cudaStreamSynchronize(s);
   cudaFreeAsync(tabs, s);
@@ -340,6 +383,7 @@ cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s) {
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
   const int bs = 256;
   fe_gather_kernel<T><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -349,6 +393,7 @@ cudaError_t launch_c_prolongate_add(const FEArgs<T> &a, const T *xc, T *xdg, cud
   const long total = (long)a.ncells * n * n * n;
   const int bs = 256;
   c_prolongate_add_kernel<T><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(a, xc, xdg);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -357,15 +402,18 @@ cudaError_t launch_fe_prolongate_add(const XferGeom &g, const T *P1, const T *xc
   const long total = (long)g.gf[0] * g.gf[1] * g.gf[2];
   const int bs = 256;
   fe_prolongate_add_kernel<T><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(g, P1, xc, xf);
+  note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf, T *ebuf, cudaStream_t s) {
-  const int nc = g.pc + 1;
-  const long total = (long)g.mc[0] * g.mc[1] * g.mc[2] * nc * nc * nc;
-  const int bs = 128;
-  fe_restrict_cells_kernel<T><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(g, P1, rf, ebuf);
+  const int nf = g.pf + 1, nc = g.pc + 1;
+  const long ncc = (long)g.mc[0] * g.mc[1] * g.mc[2];
+  const size_t smem = (size_t)(nf * nf * nf + nf * nf * nc + nf * nc * nc + nc * nc * nc) * sizeof(T);
+  if (ncc == 0) return cudaSuccess;
+  fe_restrict_cells_kernel<T><<<(int)ncc, 128, smem, s>>>(g, P1, rf, ebuf);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -128,7 +128,7 @@ extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int de
       static std::once_flag built;
       std::call_once(built, [] { build_tables(tab); });
       upload_tables_dg<double>(tab);
-      if (cudaGetLastError() != cudaSuccess) {
+      if (cudaGetLastError() != cudaSuccess || prepare_dg_kernels<double>() != cudaSuccess) {
         sipg::set_global_error("table upload failed");
         return SIPG_ECUDA;
       }
@@ -152,6 +152,7 @@ extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int de
   const int grid = (int)std::min<long>((total + bs - 1) / bs, 152L * 8);
   noalloc_prep_kernel<<<grid, bs, 0, s>>>(wcart, fwcart, tau, n, W, h[0], h[1], h[2], mesh->m[0], mesh->m[1],
                                           mesh->m[2], penalty_factor);
+  note_launch();
   DGArgs<double> a{};
   a.u = u_dev;
   a.out = v_dev;

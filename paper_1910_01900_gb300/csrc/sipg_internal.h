@@ -171,6 +171,57 @@ cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cud
 
 cudaError_t fma_peak(int precision, cudaStream_t s, double *flops);
 
+// ---- batched problems (batch.cu)
+template <typename T>
+struct BatchProb {
+  DGArgs<T> a;
+  int n;
+  int active;
+};
+
+struct WorkItem {
+  int p, cell0, ncta;
+};
+
+// Per-problem segments for the batched vector kernels.
+struct Seg {
+  double *x, *r, *p, *v, *z;
+  const double *b;
+  long n;
+  int active;
+};
+
+template <typename T>
+struct BatchPlan {
+  std::vector<BatchProb<T>> probs;
+  std::vector<WorkItem> items;
+  BatchProb<T> *d_probs = nullptr;
+  WorkItem *d_items = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  bool curved = false;
+};
+
+template <typename T>
+cudaError_t batch_plan_build(BatchPlan<T> &P, const std::vector<DGArgs<T>> &args, const std::vector<int> &ns);
+template <typename T>
+void batch_plan_free(BatchPlan<T> &P);
+template <typename T>
+cudaError_t batch_apply(BatchPlan<T> &P, cudaStream_t s);
+constexpr int kSegSlots = 8;   // scalar slots per problem (FCG layout of solver.cu, 4: b.b, 5: r0.r0)
+cudaError_t seg_dot(const Seg *segs, int np, int which, double *partials, unsigned *counter, double *sc,
+                    int sc_stride, int slot, cudaStream_t s);
+cudaError_t seg_update_xr(const Seg *segs, int np, double *partials, unsigned *counter, double *sc, int sc_stride,
+                          cudaStream_t s);
+cudaError_t seg_update_p(const Seg *segs, int np, const double *sc, int sc_stride, int init, cudaStream_t s);
+
+// Kernel-launch accounting (every launch of the library increments it).
+void note_launch();
+unsigned long long launch_count();
+template <typename T>
+cudaError_t prepare_dg_kernels();
+cudaError_t prepare_fe_kernels();
+
 // Text returned by sipg_last_error(NULL).
 void set_global_error(const std::string &msg);
 

@@ -1,12 +1,17 @@
 // Context, setup, V-cycle, Chebyshev smoother, flexible CG and the C ABI
 // (Section 3 of the paper: Algorithms 1-3, the cph level hierarchy, the
 // coarse solve; Section 4: mixed precision).
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "geometry.h"
 #include "sipg_internal.h"
@@ -30,11 +35,22 @@ struct sipg_ctx {
   unsigned *counter = nullptr;
   std::vector<void *> allocs;
   std::string err;
+  // V-cycle of the solver captured as a CUDA graph (per precision), reading
+  // fr and writing fz; captured on the second use, replayed afterwards
+  cudaGraphExec_t vgraph[2] = {nullptr, nullptr};
+  int vcalls[2] = {0, 0};
+  // cells per thread block of the finest-level DG passes, [precision][eval, integrate]
+  // (0 = compiled default; set by the autotuner)
+  int cb[2][2] = {{0, 0}, {0, 0}};
 };
 
 static std::string g_create_err;
 
 void sipg::set_global_error(const std::string &msg) { g_create_err = msg; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void sipg::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long sipg::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -148,8 +164,9 @@ void apply_level(sipg_ctx *c, int l, const T *u, T *out, int mode, const T *x = 
     a.c1 = c1;
     a.c2 = c2;
     a.c3 = c3;
-    CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream));
-    CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream));
+    const int fine = (l == c->L);
+    CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, fine ? c->cb[pidx<T>()][0] : 0));
+    CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream, fine ? c->cb[pidx<T>()][1] : 0));
   } else {
     FEArgs<T> a = fe_args<T>(c, L);
     a.u = u;
@@ -242,40 +259,76 @@ void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_
   }
 }
 
-// Algorithm 2 with x^(l) = 0 on entry: lv[l].vb -> lv[l].vx
+// Algorithm 2 with x^(l) = 0 on entry: rhs in lv[l].vb; returns the buffer
+// (vx or vt of that level) that holds x^(l).  No state changes between calls,
+// so the whole cycle can be captured once and replayed.
 template <typename T>
-void vcycle_rec(sipg_ctx *c, int l) {
+T *vcycle_rec(sipg_ctx *c, int l) {
   constexpr int pi = pidx<T>();
   Level &L = c->lv[l];
   T *b = (T *)L.vb[pi];
   if (l == 0) {
     CK((launch_dense_gemv<T, T>(c->Ainv, b, (T *)L.vx[pi], c->n0, c->stream)));
-    return;
+    return (T *)L.vx[pi];
   }
   T *x = (T *)L.vx[pi], *xt = (T *)L.vt[pi];
   const int ns = c->prm.cheb_degree;
   chebyshev<T>(c, l, b, x, xt, ns, true);
   apply_level<T>(c, l, x, (T *)L.vr[pi], 2, nullptr, nullptr, b);
   restrict_level<T>(c, l, (const T *)L.vr[pi], (T *)c->lv[l - 1].vb[pi]);
-  vcycle_rec<T>(c, l - 1);
-  prolongate_level<T>(c, l, (const T *)c->lv[l - 1].vx[pi], x);
+  const T *xc = vcycle_rec<T>(c, l - 1);
+  prolongate_level<T>(c, l, xc, x);
   chebyshev<T>(c, l, b, x, xt, ns, false);
-  L.vx[pi] = x;
-  L.vt[pi] = xt;
+  return x;
 }
 
 // z = M^-1 r with FP64 vectors in and out
-void vcycle_fp64io(sipg_ctx *c, const double *r, double *z) {
+void vcycle_body(sipg_ctx *c, const double *r, double *z) {
   Level &F = c->lv[c->L];
   if (c->prm.precision == 0) {
     CK(cudaMemcpyAsync(F.vb[0], r, F.ndofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    vcycle_rec<double>(c, c->L);
-    CK(cudaMemcpyAsync(z, F.vx[0], F.ndofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    const double *x = vcycle_rec<double>(c, c->L);
+    CK(cudaMemcpyAsync(z, x, F.ndofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   } else {
     CK((launch_cast<float, double>((float *)F.vb[1], r, F.ndofs, c->stream)));
-    vcycle_rec<float>(c, c->L);
-    CK((launch_cast<double, float>(z, (const float *)F.vx[1], F.ndofs, c->stream)));
+    const float *x = vcycle_rec<float>(c, c->L);
+    CK((launch_cast<double, float>(z, x, F.ndofs, c->stream)));
   }
+}
+
+void vcycle_fp64io(sipg_ctx *c, const double *r, double *z) { vcycle_body(c, r, z); }
+
+// The solver's preconditioner z = M^-1 r on its own vectors fr -> fz.  On a
+// non-default stream the cycle is captured into a CUDA graph on its second
+// use and replayed afterwards (one launch instead of ~100 per cycle).
+void precondition(sipg_ctx *c) {
+  const int pi = c->prm.precision;
+  if (c->vgraph[pi]) {
+    CK(cudaGraphLaunch(c->vgraph[pi], c->stream));
+    note_launch();
+    return;
+  }
+  if (c->stream == nullptr || c->vcalls[pi]++ < 1) {
+    vcycle_body(c, c->fr, c->fz);
+    return;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    vcycle_body(c, c->fr, c->fz);
+  } catch (...) {
+    cudaStreamEndCapture(c->stream, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  CK(cudaStreamEndCapture(c->stream, &g));
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  c->vgraph[pi] = ex;
+  CK(cudaGraphLaunch(ex, c->stream));
+  note_launch();
 }
 
 double read_scalar(sipg_ctx *c, int slot) {
@@ -378,6 +431,67 @@ void alloc_work(sipg_ctx *c, Level &L) {
   }
 }
 
+// Tile-shape autotuner: for each precision and each DG pass of the finest
+// level, time the compiled cells-per-block variants on this operator and keep
+// the fastest.  Results are cached per (n, geometry, precision, pass) for the
+// process, so batches of equal degrees tune once.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;
+
+template <typename T>
+void autotune_pass(sipg_ctx *c, int pass) {
+  constexpr int pi = pidx<T>();
+  const Level &L = c->lv[c->L];
+  const auto key = std::make_tuple(L.n, (int)L.curved, pi, pass);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      c->cb[pi][pass] = it->second;
+      return;
+    }
+  }
+  const int D = dg_cells_per_block<T>(L.n);
+  std::vector<int> cands{D, (D + 1) / 2, 2 * D, 1};
+  std::sort(cands.begin(), cands.end());
+  cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+  T *u = dalloc<T>(c, L.ndofs), *v = dalloc<T>(c, L.ndofs);
+  CK(cudaMemsetAsync(u, 0, L.ndofs * sizeof(T), c->stream));
+  DGArgs<T> a = dg_args<T>(c, L);
+  a.u = u;
+  a.out = v;
+  a.mode = 0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_cb = D;
+  for (int cb : cands) {
+    auto run = [&]() {
+      if (pass == 0) CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, cb));
+      else CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream, cb));
+    };
+    CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, 0));   // valid scratch for the integration pass
+    run();
+    CK(cudaEventRecord(e0, c->stream));
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r) run();
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_cb = cb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->cb[pi][pass] = best_cb;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best_cb;
+}
+
 void setup(sipg_ctx *c) {
   const sipg_mesh &M = c->mesh;
   const sipg_params &P = c->prm;
@@ -395,6 +509,9 @@ void setup(sipg_ctx *c) {
     upload_tables_fe<double>(td);
     upload_tables_fe<float>(tf);
     CK(cudaGetLastError());
+    CK(prepare_dg_kernels<double>());
+    CK(prepare_dg_kernels<float>());
+    CK(prepare_fe_kernels());
   }
   MeshDesc md{};
   for (int d = 0; d < 3; ++d) {
@@ -485,6 +602,12 @@ void setup(sipg_ctx *c) {
     c->dg_grad[1] = dalloc<float>(c, F.ncells * 3 * n3);
     c->dg_trace[1] = dalloc<float>(c, F.ncells * 12 * n2);
   }
+  if (P.autotune) {
+    for (int pass = 0; pass < 2; ++pass) {
+      autotune_pass<double>(c, pass);
+      autotune_pass<float>(c, pass);
+    }
+  }
   c->scal = dalloc<double>(c, 64);
   c->partials = dalloc<double>(c, 2 * 304);
   c->counter = dalloc<unsigned>(c, 4);
@@ -560,7 +683,7 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
   }
   const double r0 = std::sqrt(dot(c, c->fr, c->fr, N, 3));
   std::vector<double> hist{r0};
-  vcycle_fp64io(c, c->fr, c->fz);
+  precondition(c);
   CK(launch_dot2(c->fr, c->fz, nullptr, nullptr, N, c->partials, c->counter, c->scal + 0, s));
   CK(cudaMemcpyAsync(c->fp, c->fz, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   int it = 0;
@@ -592,7 +715,7 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
     ++it;
     hist.push_back(rn);
     if (!fixed_mode && rn <= rtol * r0) break;
-    vcycle_fp64io(c, c->fr, c->fz);
+    precondition(c);
     CK(launch_dot2(c->fr, c->fz, c->fz, c->fv, N, c->partials, c->counter, c->scal + 0, s));   // gamma, z.Ap
     CK(launch_fcg_update_p(c->fp, c->fz, c->scal, N, s));
   }
@@ -698,6 +821,8 @@ sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_c
 sipg_status sipg_destroy(sipg_ctx *c) {
   if (!c) return SIPG_EINVAL;
   cudaStreamSynchronize(c->stream);
+  for (auto &g : c->vgraph)
+    if (g) cudaGraphExecDestroy(g);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
   return SIPG_OK;
@@ -866,16 +991,16 @@ sipg_status sipg_time_apply(sipg_ctx *c, int precision, const void *u, void *v, 
         DGArgs<double> a = dg_args<double>(c, L);
         a.u = (const double *)u;
         a.out = (double *)v;
-        CK(launch_dg_eval<double>(L.n, L.curved, a, c->stream));
+        CK(launch_dg_eval<double>(L.n, L.curved, a, c->stream, c->cb[0][0]));
         CK(cudaEventRecord(ev[1], c->stream));
-        CK(launch_dg_integrate<double>(L.n, L.curved, a, c->stream));
+        CK(launch_dg_integrate<double>(L.n, L.curved, a, c->stream, c->cb[0][1]));
       } else {
         DGArgs<float> a = dg_args<float>(c, L);
         a.u = (const float *)u;
         a.out = (float *)v;
-        CK(launch_dg_eval<float>(L.n, L.curved, a, c->stream));
+        CK(launch_dg_eval<float>(L.n, L.curved, a, c->stream, c->cb[1][0]));
         CK(cudaEventRecord(ev[1], c->stream));
-        CK(launch_dg_integrate<float>(L.n, L.curved, a, c->stream));
+        CK(launch_dg_integrate<float>(L.n, L.curved, a, c->stream, c->cb[1][1]));
       }
       CK(cudaEventRecord(ev[2], c->stream));
       CK(cudaEventSynchronize(ev[2]));
@@ -892,11 +1017,321 @@ sipg_status sipg_time_apply(sipg_ctx *c, int precision, const void *u, void *v, 
   });
 }
 
+sipg_status sipg_tile_shape(const sipg_ctx *c, int precision, int pass, int *cells_per_block) {
+  if (!c || !cells_per_block || precision < 0 || precision > 1 || pass < 0 || pass > 1) return SIPG_EINVAL;
+  const int v = c->cb[precision][pass];
+  const int n = c->lv[c->L].n;
+  *cells_per_block = v ? v : (precision == 0 ? dg_cells_per_block<double>(n) : dg_cells_per_block<float>(n));
+  return SIPG_OK;
+}
+
+sipg_status sipg_launch_count(unsigned long long *n) {
+  if (!n) return SIPG_EINVAL;
+  *n = launch_count();
+  return SIPG_OK;
+}
+
 sipg_status sipg_fma_peak(int precision, void *stream, double *flops) {
   if (!flops || (precision != 0 && precision != 1)) return SIPG_EINVAL;
   std::string dummy;
   const cudaError_t e = fma_peak(precision, (cudaStream_t)stream, flops);
   return e == cudaSuccess ? SIPG_OK : SIPG_ECUDA;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct sipg_batch {
+  std::vector<sipg_ctx *> ctx;
+  std::vector<cudaStream_t> streams;   // one per problem (created here)
+  cudaStream_t stream = nullptr;       // caller's stream for the batched kernels
+  BatchPlan<double> plan;
+  std::vector<Seg> segs;
+  Seg *d_segs = nullptr;
+  double *sc = nullptr, *partials = nullptr;
+  unsigned *counters = nullptr;
+  cudaEvent_t ev_start = nullptr;
+  std::vector<cudaEvent_t> ev_done;
+  std::string err;
+};
+
+namespace {
+
+void batch_free(sipg_batch *B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  for (auto *c : B->ctx)
+    if (c) sipg_destroy(c);
+  for (auto s : B->streams) cudaStreamDestroy(s);
+  batch_plan_free(B->plan);
+  cudaFree(B->d_segs);
+  cudaFree(B->sc);
+  cudaFree(B->partials);
+  cudaFree(B->counters);
+  if (B->ev_start) cudaEventDestroy(B->ev_start);
+  for (auto e : B->ev_done) cudaEventDestroy(e);
+  delete B;
+}
+
+// all problems' preconditioners z = M^-1 r, each on its own stream, overlapping
+void batch_precondition(sipg_batch *B) {
+  CK(cudaEventRecord(B->ev_start, B->stream));
+  for (size_t p = 0; p < B->ctx.size(); ++p) {
+    if (!B->segs[p].active) continue;
+    CK(cudaStreamWaitEvent(B->streams[p], B->ev_start, 0));
+    precondition(B->ctx[p]);
+    CK(cudaEventRecord(B->ev_done[p], B->streams[p]));
+    CK(cudaStreamWaitEvent(B->stream, B->ev_done[p], 0));
+  }
+}
+
+void batch_set_plan(sipg_batch *B, int mode, const double *const *u, double *const *out) {
+  for (size_t p = 0; p < B->ctx.size(); ++p) {
+    DGArgs<double> &a = B->plan.probs[p].a;
+    a.mode = mode;
+    a.u = u[p];
+    a.out = out[p];
+    a.b = B->segs[p].b;
+    B->plan.probs[p].active = B->segs[p].active;
+  }
+}
+
+sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *const *x, double rtol, int maxit,
+                             sipg_solve_info *infos) {
+  const int np = (int)B->ctx.size();
+  cudaStream_t s = B->stream;
+  std::vector<const double *> xu(np), pu(np);
+  std::vector<double *> rout(np), vout(np);
+  for (int p = 0; p < np; ++p) {
+    sipg_ctx *c = B->ctx[p];
+    B->segs[p] = Seg{x[p], c->fr, c->fp, c->fv, c->fz, b[p], (long)c->lv[c->L].ndofs, 1};
+    xu[p] = x[p];
+    pu[p] = c->fp;
+    rout[p] = c->fr;
+    vout[p] = c->fv;
+  }
+  auto upload_segs = [&]() {
+    CK(cudaMemcpyAsync(B->d_segs, B->segs.data(), np * sizeof(Seg), cudaMemcpyHostToDevice, s));
+  };
+  const int st = kSegSlots;
+  std::vector<double> hsc((size_t)np * st);
+  auto read_sc = [&]() {
+    CK(cudaMemcpyAsync(hsc.data(), B->sc, hsc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  upload_segs();
+  batch_set_plan(B, 2, xu.data(), rout.data());   // r = b - A x
+  CK(batch_apply(B->plan, s));
+  CK(seg_dot(B->d_segs, np, 0, B->partials, B->counters, B->sc, st, 4, s));
+  batch_precondition(B);
+  CK(seg_dot(B->d_segs, np, 1, B->partials, B->counters, B->sc, st, 0, s));
+  CK(seg_update_p(B->d_segs, np, B->sc, st, 1, s));
+  read_sc();
+  std::vector<double> r0(np), rn(np);
+  std::vector<int> it(np, 0);
+  std::vector<std::vector<double>> hist(np);
+  sipg_status status = SIPG_OK;
+  for (int p = 0; p < np; ++p) {
+    if (!std::isfinite(hsc[p * st + 4])) {
+      B->err = "a right-hand side is not finite";
+      status = SIPG_ENAN;
+    }
+    r0[p] = rn[p] = std::sqrt(hsc[p * st + 5]);
+    hist[p].push_back(r0[p]);
+    if (r0[p] == 0.0) B->segs[p].active = 0;
+  }
+  if (status != SIPG_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return status;
+  }
+  upload_segs();
+  while (true) {
+    int nact = 0;
+    for (int p = 0; p < np; ++p) {
+      if (B->segs[p].active && it[p] >= maxit) {
+        B->segs[p].active = 0;
+        status = SIPG_ENOTCONV;
+      }
+      nact += B->segs[p].active;
+    }
+    if (nact == 0) break;
+    upload_segs();
+    batch_set_plan(B, 0, pu.data(), vout.data());   // v = A p
+    CK(batch_apply(B->plan, s));
+    CK(seg_dot(B->d_segs, np, 2, B->partials, B->counters, B->sc, st, 2, s));
+    CK(seg_update_xr(B->d_segs, np, B->partials, B->counters, B->sc, st, s));
+    read_sc();
+    for (int p = 0; p < np; ++p) {
+      if (!B->segs[p].active) continue;
+      const double *q = &hsc[p * st];
+      ++it[p];
+      if (!(q[2] > 0) || !std::isfinite(q[3])) {
+        B->segs[p].active = 0;
+        status = SIPG_EBREAKDOWN;
+        B->err = "flexible CG breakdown in a batched problem";
+        continue;
+      }
+      rn[p] = std::sqrt(q[3]);
+      hist[p].push_back(rn[p]);
+      if (rn[p] <= rtol * r0[p]) B->segs[p].active = 0;
+    }
+    upload_segs();
+    int still = 0;
+    for (int p = 0; p < np; ++p) still += B->segs[p].active;
+    if (still == 0) break;
+    batch_precondition(B);
+    CK(seg_dot(B->d_segs, np, 3, B->partials, B->counters, B->sc, st, 0, s));
+    CK(seg_update_p(B->d_segs, np, B->sc, st, 0, s));
+  }
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (infos)
+    for (int p = 0; p < np; ++p) {
+      sipg_solve_info &I = infos[p];
+      std::memset(&I, 0, sizeof(I));
+      I.iterations = it[p];
+      I.r0_norm = r0[p];
+      I.r_norm = rn[p];
+      I.converged = (r0[p] == 0.0 || rn[p] <= rtol * r0[p]) ? 1 : 0;
+      I.rho = (it[p] > 0 && r0[p] > 0) ? std::pow(rn[p] / r0[p], 1.0 / it[p]) : 0.0;
+      I.n10 = (I.rho > 0 && I.rho < 1) ? -10.0 / std::log10(I.rho) : 0.0;
+      I.seconds = ms * 1e-3;
+      for (int j = 0; j < (int)hist[p].size() && j < 256; ++j) I.res_history[j] = hist[p][j];
+    }
+  if (status == SIPG_ENOTCONV) B->err = "a batched problem reached maxit before the tolerance";
+  return status;
+}
+
+template <typename F>
+sipg_status bguarded(sipg_batch *B, F &&f) {
+  std::string *prev = t_err;
+  t_err = B ? &B->err : &g_create_err;
+  sipg_status st;
+  try {
+    st = f();
+  } catch (const Fail &e) {
+    st = e.st;
+  } catch (const std::exception &e) {
+    if (t_err) *t_err = e.what();
+    st = SIPG_ENOMEM;
+  }
+  t_err = prev;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+sipg_status sipg_batch_create(int nprob, const sipg_mesh *meshes, const sipg_params *params, sipg_batch **out) {
+  if (!out || nprob < 1 || nprob > 4096 || !meshes || !params) return SIPG_EINVAL;
+  *out = nullptr;
+  sipg_batch *B = new sipg_batch();
+  B->stream = (cudaStream_t)params[0].stream;
+  sipg_status st = SIPG_OK;
+  bool curved = false;
+  for (int p = 0; p < nprob && st == SIPG_OK; ++p) {
+    cudaStream_t ps;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
+      st = SIPG_ECUDA;
+      break;
+    }
+    B->streams.push_back(ps);
+    sipg_params prm = params[p];
+    prm.stream = ps;
+    prm.operator_only = 0;
+    if (prm.precision != params[0].precision) {
+      g_create_err = "all problems of a batch must use the same precision";
+      st = SIPG_EINVAL;
+      break;
+    }
+    if (p > 0 && (meshes[p].deform != 0) != (meshes[0].deform != 0)) {
+      g_create_err = "a batch holds either only affine or only curved meshes";
+      st = SIPG_EINVAL;
+      break;
+    }
+    curved = meshes[0].deform != 0;
+    sipg_ctx *c = nullptr;
+    st = sipg_create(&meshes[p], &prm, &c);
+    if (st == SIPG_OK && !c->solver) {
+      g_create_err = "every batched problem needs a Dirichlet side";
+      sipg_destroy(c);
+      st = SIPG_EINVAL;
+    }
+    if (st == SIPG_OK) B->ctx.push_back(c);
+  }
+  if (st == SIPG_OK)
+    st = bguarded(nullptr, [&]() -> sipg_status {
+      std::vector<DGArgs<double>> args;
+      std::vector<int> ns;
+      for (auto *c : B->ctx) {
+        args.push_back(dg_args<double>(c, c->lv[c->L]));
+        ns.push_back(c->lv[c->L].n);
+      }
+      CK(batch_plan_build(B->plan, args, ns));
+      B->plan.curved = curved;
+      B->segs.assign(nprob, Seg{});
+      CK(cudaMalloc(&B->d_segs, nprob * sizeof(Seg)));
+      CK(cudaMalloc(&B->sc, (size_t)nprob * kSegSlots * sizeof(double)));
+      CK(cudaMalloc(&B->partials, (size_t)nprob * 32 * 2 * sizeof(double)));
+      CK(cudaMalloc(&B->counters, (size_t)nprob * sizeof(unsigned)));
+      CK(cudaMemset(B->counters, 0, (size_t)nprob * sizeof(unsigned)));
+      CK(cudaEventCreateWithFlags(&B->ev_start, cudaEventDisableTiming));
+      B->ev_done.resize(nprob);
+      for (auto &e : B->ev_done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      CK(cudaDeviceSynchronize());
+      return SIPG_OK;
+    });
+  if (st != SIPG_OK) {
+    batch_free(B);
+    return st;
+  }
+  *out = B;
+  return SIPG_OK;
+}
+
+sipg_status sipg_batch_destroy(sipg_batch *B) {
+  if (!B) return SIPG_EINVAL;
+  batch_free(B);
+  return SIPG_OK;
+}
+
+const char *sipg_batch_last_error(const sipg_batch *B) { return B ? B->err.c_str() : g_create_err.c_str(); }
+
+sipg_status sipg_batch_context(sipg_batch *B, int i, sipg_ctx **ctx) {
+  if (!B || !ctx || i < 0 || i >= (int)B->ctx.size()) return SIPG_EINVAL;
+  *ctx = B->ctx[i];
+  return SIPG_OK;
+}
+
+sipg_status sipg_batch_apply(sipg_batch *B, const double *const *u, double *const *v) {
+  if (!B || !u || !v) return SIPG_EINVAL;
+  for (size_t p = 0; p < B->ctx.size(); ++p)
+    if (!u[p] || !v[p] || u[p] == v[p]) return SIPG_EINVAL;
+  return bguarded(B, [&]() -> sipg_status {
+    for (size_t p = 0; p < B->ctx.size(); ++p) B->segs[p].active = 1;
+    batch_set_plan(B, 0, u, v);
+    CK(batch_apply(B->plan, B->stream));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_batch_solve(sipg_batch *B, const double *const *b, double *const *x, double rtol, int maxit,
+                             sipg_solve_info *infos) {
+  if (!B || !b || !x || maxit < 0 || !(rtol >= 0)) return SIPG_EINVAL;
+  for (size_t p = 0; p < B->ctx.size(); ++p)
+    if (!b[p] || !x[p]) return SIPG_EINVAL;
+  return bguarded(B, [&]() -> sipg_status { return batch_solve_impl(B, b, x, rtol, maxit, infos); });
 }
 
 }  // extern "C"

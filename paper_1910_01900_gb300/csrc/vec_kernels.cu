@@ -44,23 +44,27 @@ template <typename T>
 cudaError_t launch_fill(T *x, T v, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   fill_kernel<T><<<grid_for(n), 256, 0, s>>>(x, v, n);
+  note_launch();
   return cudaGetLastError();
 }
 template <typename Tout, typename Tin>
 cudaError_t launch_cast(Tout *y, const Tin *x, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   cast_kernel<Tout, Tin><<<grid_for(n), 256, 0, s>>>(y, x, n);
+  note_launch();
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_axpy(T *y, T a, const T *x, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   axpy_kernel<T><<<grid_for(n), 256, 0, s>>>(y, a, x, n);
+  note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_invert(double *d, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   invert_kernel<<<grid_for(n), 256, 0, s>>>(d, n);
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_fill<double>(double *, double, int64_t, cudaStream_t);
@@ -131,6 +135,7 @@ __global__ void dot2_kernel(const double *x, const double *y, const double *z, c
 cudaError_t launch_dot2(const double *x, const double *y, const double *z, const double *w, int64_t n,
                         double *partials, unsigned *counter, double *out, cudaStream_t s) {
   dot2_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, z, w, n, partials, counter, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -152,6 +157,7 @@ cudaError_t launch_fcg_update_xr(double *x, double *r, const double *p, const do
                                  const double *sc, double *partials, unsigned *counter, double *out,
                                  cudaStream_t s) {
   fcg_update_xr_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, v, n, sc, partials, counter, out);
+  note_launch();
   return cudaGetLastError();
 }
 // p = z + beta p with beta = -z.Ap / p.Ap (flexible CG, one retained direction)
@@ -162,6 +168,7 @@ __global__ void fcg_update_p_kernel(double *p, const double *z, const double *sc
 }
 cudaError_t launch_fcg_update_p(double *p, const double *z, const double *sc, int64_t n, cudaStream_t s) {
   fcg_update_p_kernel<<<grid_for(n), 256, 0, s>>>(p, z, sc, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -181,6 +188,7 @@ template <typename Tb, typename Tx>
 cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cudaStream_t s) {
   const int bs = 256, wpb = bs / 32;
   dense_gemv_kernel<Tb, Tx><<<(n + wpb - 1) / wpb, bs, 0, s>>>(Ainv, b, x, n);
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_dense_gemv<double, double>(const double *, const double *, double *, int, cudaStream_t);
@@ -250,6 +258,7 @@ template <typename T>
 cudaError_t launch_xdb(T *x, T c, const T *dinv, const T *b, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   xdb_kernel<T><<<grid_for(n), 256, 0, s>>>(x, c, dinv, b, n);
+  note_launch();
   return cudaGetLastError();
 }
 // p = z + beta p
@@ -262,6 +271,7 @@ template <typename T>
 cudaError_t launch_xpby(T *p, const T *z, T beta, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   xpby_kernel<T><<<grid_for(n), 256, 0, s>>>(p, z, beta, n);
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_xdb<double>(double *, double, const double *, const double *, int64_t, cudaStream_t);

@@ -20,7 +20,8 @@ EXPORTS = [
     "sipg_num_dofs", "sipg_level_info", "sipg_lambda", "sipg_rhs", "sipg_operator_apply",
     "sipg_level_apply", "sipg_inverse_diagonal", "sipg_smooth", "sipg_restrict", "sipg_prolongate_add",
     "sipg_coarse_solve", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
-    "sipg_operator_apply_noalloc",
+    "sipg_operator_apply_noalloc", "sipg_launch_count", "sipg_batch_create", "sipg_batch_destroy",
+    "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_solve", "sipg_tile_shape",
 ]
 
 
@@ -34,7 +35,8 @@ class Params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("penalty_factor", ctypes.c_double), ("precision", ctypes.c_int),
                 ("p_coarsen", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("lambda_override", ctypes.c_double),
-                ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -79,9 +81,18 @@ def lib():
         L.sipg_time_apply.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_float)]
         L.sipg_fma_peak.argtypes = [i32, vp, ctypes.POINTER(dbl)]
+        L.sipg_launch_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+        L.sipg_tile_shape.argtypes = [vp, i32, i32, ctypes.POINTER(i32)]
+        L.sipg_batch_create.argtypes = [i32, ctypes.POINTER(Mesh), ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        L.sipg_batch_destroy.argtypes = [vp]
+        L.sipg_batch_last_error.argtypes = [vp]
+        L.sipg_batch_last_error.restype = ctypes.c_char_p
+        L.sipg_batch_context.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        L.sipg_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.sipg_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32, ctypes.POINTER(SolveInfo)]
         L.sipg_operator_apply_noalloc.argtypes = [ctypes.POINTER(Mesh), i32, dbl, vp, vp, vp]
         for name in EXPORTS:
-            if name not in ("sipg_default_params", "sipg_last_error"):
+            if name not in ("sipg_default_params", "sipg_last_error", "sipg_batch_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -106,41 +117,58 @@ def _ptr(t, dtype=None, numel=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def make_mesh(m, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6):
+    mesh = Mesh()
+    mm = tuple(m) if hasattr(m, "__len__") else (m, m, m)
+    for d in range(3):
+        mesh.m[d], mesh.lo[d], mesh.hi[d] = int(mm[d]), float(lo[d]), float(hi[d])
+    mesh.deform, mesh.amp, mesh.mapping_degree = int(deform), float(amp), 3
+    for s in range(6):
+        mesh.bc[s] = int(bc[s])
+    return mesh, mm
+
+
+def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
+                operator_only=False, stream=None, autotune=False):
+    prm = Params()
+    lib().sipg_default_params(ctypes.byref(prm))
+    prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
+    prm.cheb_degree, prm.eig_iters = int(cheb_degree), int(eig_iters)
+    prm.lambda_override, prm.operator_only = float(lambda_override), int(bool(operator_only))
+    prm.autotune = int(bool(autotune))
+    prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    return prm
+
+
 class Context:
     """One SIPG problem: mesh, degree, level hierarchy, device data (sipg_create)."""
 
     def __init__(self, m, degree, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
                  precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                 operator_only=False, stream=None):
+                 operator_only=False, stream=None, autotune=False, _handle=None):
         L = lib()
-        mesh = Mesh()
-        mm = tuple(m) if hasattr(m, "__len__") else (m, m, m)
-        for d in range(3):
-            mesh.m[d], mesh.lo[d], mesh.hi[d] = int(mm[d]), float(lo[d]), float(hi[d])
-        mesh.deform, mesh.amp, mesh.mapping_degree = int(deform), float(amp), 3
-        for s in range(6):
-            mesh.bc[s] = int(bc[s])
-        prm = Params()
-        L.sipg_default_params(ctypes.byref(prm))
-        prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
-        prm.cheb_degree, prm.eig_iters = int(cheb_degree), int(eig_iters)
-        prm.lambda_override, prm.operator_only = float(lambda_override), int(bool(operator_only))
-        prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        mesh, mm = make_mesh(m, deform, amp, lo, hi, bc)
+        self.degree, self.precision = int(degree), int(precision)
+        self.m = mm
         self.stream = stream
+        self._owned = _handle is None
+        if _handle is not None:
+            self.h = _handle
+            return
+        prm = make_params(degree, precision, penalty_factor, cheb_degree, eig_iters, lambda_override,
+                          operator_only, stream, autotune)
         h = ctypes.c_void_p()
         st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
         if st != OK:
             raise SipgError(st, L.sipg_last_error(None).decode())
         self.h = h
-        self.degree, self.precision = int(degree), int(precision)
-        self.m = mm
 
     def _check(self, st):
         if st != OK:
             raise SipgError(st, lib().sipg_last_error(self.h).decode())
 
     def close(self):
-        if getattr(self, "h", None) is not None and self.h.value:
+        if getattr(self, "_owned", False) and getattr(self, "h", None) is not None and self.h.value:
             lib().sipg_destroy(self.h)
             self.h = ctypes.c_void_p()
 
@@ -240,6 +268,11 @@ class Context:
                                           ctypes.byref(info)))
         return info
 
+    def tile_shape(self, precision, pass_):
+        v = ctypes.c_int()
+        self._check(lib().sipg_tile_shape(self.h, int(precision), int(pass_), ctypes.byref(v)))
+        return v.value
+
     def time_apply(self, u, v, repeats=20):
         import torch
         precision = 0 if u.dtype == torch.float64 else 1
@@ -272,6 +305,73 @@ def operator_apply_noalloc(m, degree, u, v, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.
                                            ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))
     if st != OK:
         raise SipgError(st, lib().sipg_last_error(None).decode())
+
+
+class Batch:
+    """Many independent problems solved together (sipg_batch_*).
+
+    problems: list of dicts with keys m, k and optionally deform, bc, lo, hi.
+    """
+
+    def __init__(self, problems, precision=0, stream=None, **kw):
+        L = lib()
+        n = len(problems)
+        meshes = (Mesh * n)()
+        prms = (Params * n)()
+        for i, p in enumerate(problems):
+            meshes[i], _ = make_mesh(p["m"], p.get("deform", 0), p.get("amp", 0.1), p.get("lo", (0.0,) * 3),
+                                     p.get("hi", (1.0,) * 3), p.get("bc", (0,) * 6))
+            prms[i] = make_params(p["k"], precision, stream=stream, **kw)
+        h = ctypes.c_void_p()
+        st = L.sipg_batch_create(n, meshes, prms, ctypes.byref(h))
+        if st != OK:
+            raise SipgError(st, L.sipg_batch_last_error(None).decode())
+        self.h, self.n, self.stream = h, n, stream
+        self.contexts = []
+        for i, p in enumerate(problems):
+            c = ctypes.c_void_p()
+            L.sipg_batch_context(h, i, ctypes.byref(c))
+            self.contexts.append(Context(p["m"], p["k"], deform=p.get("deform", 0), precision=precision,
+                                         stream=stream, _handle=c))
+
+    def _check(self, st):
+        if st != OK:
+            raise SipgError(st, lib().sipg_batch_last_error(self.h).decode())
+
+    def num_dofs(self, i):
+        return self.contexts[i].num_dofs()
+
+    def apply(self, us, vs):
+        import torch
+        U = (ctypes.c_void_p * self.n)(*[_ptr(u, torch.float64, self.num_dofs(i)).value for i, u in enumerate(us)])
+        V = (ctypes.c_void_p * self.n)(*[_ptr(v, torch.float64, self.num_dofs(i)).value for i, v in enumerate(vs)])
+        self._check(lib().sipg_batch_apply(self.h, U, V))
+
+    def solve(self, bs, xs, rtol=1e-10, maxit=200):
+        import torch
+        B = (ctypes.c_void_p * self.n)(*[_ptr(b, torch.float64, self.num_dofs(i)).value for i, b in enumerate(bs)])
+        X = (ctypes.c_void_p * self.n)(*[_ptr(x, torch.float64, self.num_dofs(i)).value for i, x in enumerate(xs)])
+        infos = (SolveInfo * self.n)()
+        self._check(lib().sipg_batch_solve(self.h, B, X, float(rtol), int(maxit), infos))
+        return list(infos)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sipg_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_count():
+    """Kernel and graph launches issued by libsipg so far in this process."""
+    n = ctypes.c_ulonglong()
+    lib().sipg_launch_count(ctypes.byref(n))
+    return n.value
 
 
 def fma_peak(precision, stream=None):

@@ -1,0 +1,109 @@
+"""Batched problems (persistent launch, lockstep FCG) and many right-hand sides (GPU).
+
+The batch path must give each problem exactly what the single-problem path
+gives (same sum-factorisation bodies, same cell grouping) and what the oracle
+gives.
+"""
+import numpy as np
+import pytest
+
+import sipg_inputs
+from oracle.dg import SIPG
+from oracle.mesh import Mesh
+from oracle.multigrid import CPHMultigrid, fcg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+PROBS = [dict(m=4, k=2), dict(m=(6, 4, 3), k=3), dict(m=4, k=5), dict(m=(2, 3, 2), k=8), dict(m=(7, 6, 5), k=1),
+         dict(m=3, k=6)]
+
+
+@pytest.mark.parametrize("deform", [0, 1])
+def test_batched_apply_equals_single_problem_and_oracle(deform):
+    from paper_1910_01900_gb300 import Batch
+    probs = [dict(p, deform=deform) for p in PROBS]
+    B = Batch(probs)
+    us, vs, refs = [], [], []
+    for i, p in enumerate(probs):
+        n = B.num_dofs(i)
+        u = torch.as_tensor(sipg_inputs.uniform(n, 50 + i)).to(DEV)
+        ref = torch.empty_like(u)
+        B.contexts[i].apply(u, ref)
+        us.append(u)
+        vs.append(torch.full_like(u, float("nan")))
+        refs.append(ref)
+    B.apply(us, vs)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        assert rel(vs[i].cpu().numpy(), refs[i].cpu().numpy()) <= 1e-14, i
+        o = SIPG(Mesh(p["m"], deform=deform), p["k"]).apply(us[i].cpu().numpy())
+        assert rel(vs[i].cpu().numpy(), o) <= 1e-12, i
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_solve_equals_single_solves(precision):
+    from paper_1910_01900_gb300 import Batch, Context
+    probs = [dict(m=4, k=3), dict(m=6, k=2), dict(m=4, k=4), dict(m=(4, 6, 4), k=2)]
+    B = Batch(probs, precision=precision)
+    bs = [torch.as_tensor(sipg_inputs.uniform(B.num_dofs(i), sipg_inputs.SEED_RHS + i)).to(DEV)
+          for i in range(len(probs))]
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = B.solve(bs, xs, rtol=1e-10)
+    for i, p in enumerate(probs):
+        c = Context(p["m"], p["k"], precision=precision)
+        x = torch.zeros_like(bs[i])
+        info = c.solve(bs[i], x, rtol=1e-10)
+        assert infos[i].converged and infos[i].iterations == info.iterations, i
+        assert rel(xs[i].cpu().numpy(), x.cpu().numpy()) <= (1e-12 if precision == 0 else 1e-9), i
+    # and one of them against the oracle's solve
+    mg = CPHMultigrid(Mesh(4), 3)
+    bo = bs[0].cpu().numpy()
+    xo, it, _ = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
+    assert infos[0].iterations == it or precision == 1
+    assert rel(xs[0].cpu().numpy(), xo) <= (1e-10 if precision == 0 else 1e-8)
+
+
+def test_seeded_uneven_batch_converges():
+    """The 16-problem draw (m in 8..24 even, k in 2..6): every problem reaches 1e-10."""
+    from paper_1910_01900_gb300 import Batch
+    probs = sipg_inputs.batch_problems()
+    B = Batch(probs, precision=1)
+    bs, xs = [], []
+    for i in range(len(probs)):
+        b = torch.empty(B.num_dofs(i), dtype=torch.float64, device=DEV)
+        B.contexts[i].rhs(b)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    infos = B.solve(bs, xs, rtol=1e-10)
+    for i in range(len(probs)):
+        assert infos[i].converged, i
+        r = torch.empty_like(bs[i])
+        B.contexts[i].apply(xs[i], r)
+        res = (torch.linalg.norm(bs[i] - r) / torch.linalg.norm(bs[i])).item()
+        assert res <= 2e-10, (i, res)
+        assert 3 <= infos[i].iterations <= 12, (i, infos[i].iterations)
+
+
+def test_32_right_hand_sides():
+    """32 seeded RHS on the 16^3 k=4 mesh, FP32 V-cycle / FP64 FCG."""
+    from paper_1910_01900_gb300 import Batch, Context
+    nrhs = 32
+    B = Batch([dict(m=16, k=4)] * nrhs, precision=1)
+    n = B.num_dofs(0)
+    bs = [torch.as_tensor(sipg_inputs.uniform(n, sipg_inputs.SEED_RHS + r)).to(DEV) for r in range(nrhs)]
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = B.solve(bs, xs, rtol=1e-10)
+    assert all(i.converged for i in infos)
+    c = Context(16, 4, precision=1)
+    for r in (0, 17, 31):
+        x = torch.zeros_like(bs[r])
+        info = c.solve(bs[r], x, rtol=1e-10)
+        assert info.iterations == infos[r].iterations
+        assert rel(xs[r].cpu().numpy(), x.cpu().numpy()) <= 1e-9

@@ -252,3 +252,20 @@ def test_sweep_sizes_sampled(k):
     E = m ** 3
     cells = [0, m - 1, m * m * (m // 2) + m * 3 + 1, E // 2 + 7, E - 1]
     assert _sampled_apply_check(m, k, 1, cells) <= 1e-12
+
+
+@pytest.mark.parametrize("k,deform", [(2, 0), (5, 1), (8, 0)])
+def test_autotuned_tile_shapes_keep_parity(k, deform):
+    m = SHAPES[k]
+    ctx = _ctx(m, k, deform=deform, operator_only=True, autotune=True)
+    from sipg_inputs import uniform
+    u = uniform(ctx.num_dofs(), 3)
+    ref = SIPG(Mesh(m, deform=deform), k).apply(u)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        v = torch.empty(len(u), dtype=dt, device=DEV)
+        ctx.apply(gpu(u, dt), v)
+        assert rel(v.cpu().numpy(), ref) <= tol
+    from paper_1910_01900_gb300.csrc_info import tile_candidates
+    for prec in (0, 1):
+        for p in (0, 1):
+            assert ctx.tile_shape(prec, p) in tile_candidates(k + 1)
