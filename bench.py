@@ -46,6 +46,10 @@ METRIC = "SIPG apply DoF/s & %roofline; solve s/MDoF to 1e-10 rel. res. vs plain
 # solve time: FE levels, transfers and vector updates are left out).
 ITERATIONS = 6
 NS = 5
+# DRAM bytes per DoF of the FP64 curved k=5 integration pass, from the ncu
+# capture summarised in profiles/dg_kernels_curved32_k5_fp64.md (32^3 cells,
+# scaled to this workload by the number of cells it processes).
+INTEGRATE_DRAM_BYTES_PER_DOF = 126.2
 DG_APPLIES_PER_SOLVE = (ITERATIONS + 1) * (2 * NS + 1) + ITERATIONS
 
 
@@ -156,6 +160,7 @@ def run_gb300(args):
             x32.zero_()
             ctx32.solve(b, x32, rtol=1e-10, maxit=100)
         t32, it32 = [], []
+        torch.cuda.nvtx.range_push("timed_mixed")
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -166,6 +171,7 @@ def run_gb300(args):
             e1.synchronize()
             t32.append(e0.elapsed_time(e1))
             it32.append(info32.iterations)
+        torch.cuda.nvtx.range_pop()
         err32 = (torch.linalg.norm(x32 - x) / torch.linalg.norm(x)).item()
     torch.cuda.synchronize()
     if world > 1:
@@ -219,7 +225,8 @@ def run_gb300(args):
         "apply": {"fp64_dof_per_s": N / ((te64 + ti64) * 1e-3), "fp32_dof_per_s": N / ((te32 + ti32) * 1e-3),
                   "fp64_ms": [te64, ti64], "fp32_ms": [te32, ti32]},
         "roofline": {"kernel": "dg_integrate_kernel<double,6,curved>", "bound": "alu", "achieved": ach / 1e12,
-                     "peak": peak64 / 1e12, "unit": "TFLOP/s", "frac": ach / peak64, "traffic": None,
+                     "peak": peak64 / 1e12, "unit": "TFLOP/s", "frac": ach / peak64, "traffic": INTEGRATE_DRAM_BYTES_PER_DOF * N,
+                     "traffic_source": "ncu dram__bytes_read+write of a 32^3 capture scaled by cells",
                      "peak_source": "measured DFMA probe in this run (sipg_fma_peak)"},
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / max(1, args.steps),

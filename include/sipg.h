@@ -99,6 +99,8 @@ typedef struct {
   double n10;              /* -10 / log10(rho)                                 */
   double seconds;          /* wall time of the solve on the stream             */
   double res_history[256]; /* ||r_j||_2, j = 0..min(iterations,255)            */
+  int learned;             /* 1 if the solve started with the learned smoother */
+  int fell_back;           /* 1 if it switched back to Chebyshev on the way    */
 } sipg_solve_info;
 
 /* Fills the defaults listed above (degree 3, FP64). */
@@ -130,6 +132,12 @@ sipg_status sipg_lambda(const sipg_ctx *ctx, int level, double *lambda);
  * Dirichlet sides (zero on the box), h = du/dn on Neumann sides.  Writes the
  * FP64 DG vector b_dev (length = dofs of the finest level). */
 sipg_status sipg_rhs(sipg_ctx *ctx, int kind, double *b_dev);
+
+/* L2 error || u_h - u ||_L2 of a finest-level FP64 solution against the
+ * manufactured solution of sipg_rhs kind (0 only), with an (k+3)-point Gauss
+ * rule per direction on the mapped cells; computed on the host (a diagnostic,
+ * not part of the solve). */
+sipg_status sipg_l2_error(sipg_ctx *ctx, int kind, const double *x_dev, double *err);
 
 /* v = A u on the finest (DG) level: the homogeneous SIPG operator of
  * Eq. WeakFormDG with fluxes InteriorPenaltyFlux1/2 and mirror boundary
@@ -207,6 +215,50 @@ sipg_status sipg_batch_apply(sipg_batch *batch, const double *const *u_dev, doub
  * history.  Status as sipg_solve, worst over the problems. */
 sipg_status sipg_batch_solve(sipg_batch *batch, const double *const *b_dev, double *const *x_dev, double rtol,
                              int maxit, sipg_solve_info *infos);
+
+/* ---- Learned smoother (not in the paper).  A per-cell network stands in for
+ * the Chebyshev smoother on the finest level: input = the cell's (k+1)^3
+ * residual values followed by, per face (-x,+x,-y,+y,-z,+z), the neighbour's
+ * (k+1)^2 residual values on the shared face (zeros on the boundary), all
+ * divided by their RMS s; two hidden ReLU layers of width 256; output y of
+ * (k+1)^3 values; smoothing step x <- x + c s y per cell.  BF16 weights and
+ * activations, FP32 accumulation (tensor cores), FP32 master weights.  The
+ * solve stays a flexible CG, so its result does not depend on the network;
+ * the Chebyshev cycle's average rate (measured while generating the data)
+ * judges each learned step and a worse step switches the solve back to
+ * Chebyshev (sipg_solve_info.fell_back). */
+typedef struct {
+  int npairs, epochs, steps;      /* training pairs, epochs, Adam steps          */
+  double loss_first, loss_last;   /* mean squared error, first and last epoch    */
+  double out_scale;               /* c                                            */
+  double cheb_rate;               /* average rate of the Chebyshev cycle         */
+  double seconds;                 /* wall time of data generation and training  */
+} sipg_train_info;
+/* Generates npairs (cell residual -> cell error) pairs from the plain cycle:
+ * 4 seeded uniform right-hand sides, each solved to 1e-12, and the first 4
+ * flexible-CG iterates of each (r = b - A x_j, e = x* - x_j) at seeded
+ * random cells; then trains the network with Adam (batches of 256). */
+sipg_status sipg_smoother_train(sipg_ctx *ctx, int npairs, int epochs, uint64_t seed, sipg_train_info *info);
+/* which = 0: Chebyshev (default); 1: learned (trained network required), with
+ * steps_pre and steps_post network steps around the coarse correction. */
+sipg_status sipg_set_smoother(sipg_ctx *ctx, int which, int steps_pre, int steps_post);
+/* Network shape: in_dim (and padded width), hidden width, out_dim (and
+ * padded width), number of parameters.  Flat parameter layout (FP32):
+ * W1[in_pad][hidden], b1[hidden], W2[hidden][hidden], b2[hidden],
+ * W3[hidden][out_pad], b3[out_pad]. */
+sipg_status sipg_mlp_shape(sipg_ctx *ctx, int *in_dim, int *in_pad, int *hidden, int *out_dim, int *out_pad,
+                           int64_t *nparams);
+/* set = 1: load the parameters from host; 0: store them to host. */
+sipg_status sipg_mlp_params(sipg_ctx *ctx, int set, float *host);
+/* Y[B][out_pad] = network(X[B][in_dim]) (device FP32 arrays). */
+sipg_status sipg_mlp_forward(sipg_ctx *ctx, const float *X_dev, int B, float *Y_dev);
+/* Gradients of sum ||y - t||^2 / (2B) over B rows (X[B][in_dim], T[B][out_dim],
+ * device) to host (flat layout), and the loss. */
+sipg_status sipg_mlp_gradients(sipg_ctx *ctx, const float *X_dev, const float *T_dev, int B, float *grads_host,
+                               double *loss);
+/* Network inputs of every cell from a finest-level FP64 residual: feat[cells][in_pad]
+ * (already divided by s, BF16-rounded) and scale[cells] = s. */
+sipg_status sipg_mlp_features(sipg_ctx *ctx, const double *r_dev, float *feat_dev, float *scale_dev);
 
 /* Cells per thread block the finest-level DG pass uses (pass 0 evaluation,
  * 1 integration) in the given precision: the autotuned value or the default. */

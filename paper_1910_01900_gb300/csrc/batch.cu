@@ -25,6 +25,12 @@ namespace sipg {
 
 constexpr int kBatchThreads = 256;
 
+// this translation unit's copy of the 1D tables (constant memory is per unit)
+template <>
+void upload_tables_batch<double>(const Tables<double> &t) { upload_tables_tu(t); }
+template <>
+void upload_tables_batch<float>(const Tables<float> &t) { upload_tables_tu(t); }
+
 template <typename T, bool CURVED, bool INTEGRATE>
 __global__ void __launch_bounds__(kBatchThreads)
     dg_batched_kernel(const BatchProb<T> *__restrict__ probs, const WorkItem *__restrict__ items, int nitems) {

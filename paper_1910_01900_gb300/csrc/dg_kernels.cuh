@@ -206,37 +206,47 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
           const T un = tn[0], qn = tn[N2];
           const T tau_f = max(tau_e, a.tau[nb]);
           const T jump = uo - un;
-          A[s] = dA * (tau_f * jump - T(0.5) * (qo - qn));
-          B[s] = T(-0.5) * dA * jump;
+          const T hdA = T(0.5) * dA;
+          A[s] = fma(dA * tau_f, jump, -hdA * (qo - qn));
+          B[s] = -hdA * jump;
         } else if (a.bc[2 * d + s] == 0) {
-          A[s] = dA * (T(2) * tau_e * uo - qo);
+          A[s] = fma(T(2) * dA * tau_e, uo, -dA * qo);
           B[s] = -dA * uo;
         } else {
           A[s] = T(0);
           B[s] = T(0);
         }
       }
-      T y[N];
-#pragma unroll
-      for (int q = 0; q < N; ++q) y[q] = t.l0[N][q] * A[0] + t.l1[N][q] * A[1];
+      // extrapolation transposed: every point of the line gets l_s(q) times the
+      // coefficient of each side (two FMAs per point, accumulated in place)
       if (d == 0) {
-        store_line<T, N>(st, base, stride, y);
+#pragma unroll
+        for (int q = 0; q < N; ++q) st[base + q * stride] = fma(t.l0[N][q], A[0], t.l1[N][q] * A[1]);
       } else {
 #pragma unroll
-        for (int q = 0; q < N; ++q) st[base + q * stride] += y[q];
+        for (int q = 0; q < N; ++q) {
+          T *p = st + base + q * stride;
+          *p = fma(t.l0[N][q], A[0], fma(t.l1[N][q], A[1], *p));
+        }
       }
       if constexpr (!CURVED) {
         const T b0 = -a.ih[d] * B[0], b1 = a.ih[d] * B[1];
         T *g = sg + d * N3;
 #pragma unroll
-        for (int q = 0; q < N; ++q) g[base + q * stride] += t.l0[N][q] * b0 + t.l1[N][q] * b1;
+        for (int q = 0; q < N; ++q) {
+          T *p = g + base + q * stride;
+          *p = fma(t.l0[N][q], b0, fma(t.l1[N][q], b1, *p));
+        }
       } else {
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) {
           const T b0 = cvec[0][bb] * B[0], b1 = cvec[1][bb] * B[1];
           T *g = sg + bb * N3;
 #pragma unroll
-          for (int q = 0; q < N; ++q) g[base + q * stride] += t.l0[N][q] * b0 + t.l1[N][q] * b1;
+          for (int q = 0; q < N; ++q) {
+            T *p = g + base + q * stride;
+            *p = fma(t.l0[N][q], b0, fma(t.l1[N][q], b1, *p));
+          }
         }
       }
     }

@@ -410,6 +410,68 @@ void manufactured_rhs(const Mapping &map, int n, const std::vector<double> &tau,
   }
 }
 
+double l2_error_manufactured(const Mapping &map, int n, const double *x) {
+  // || u_h - u ||_L2 with an (n+2)-point Gauss rule per direction; u_h from the
+  // nodal values x (DG order), u = prod_j sin(pi (x_j - lo_j) / L_j)
+  const MeshDesc &m = map.mesh;
+  const int nq = n + 2;
+  struct {
+    std::vector<double> xq, wq;
+  } rq;
+  gauss_rule(nq, rq.xq, rq.wq);
+  const Rules1D &rn = rules(n);
+  std::vector<double> S((size_t)nq * n);
+  for (int q = 0; q < nq; ++q) {
+    const auto v = lagrange_values(rn.gl, rq.xq[q]);
+    for (int i = 0; i < n; ++i) S[(size_t)q * n + i] = v[i];
+  }
+  std::vector<std::array<double, 3>> pts((size_t)nq * nq * nq);
+  for (int k = 0; k < nq; ++k)
+    for (int j = 0; j < nq; ++j)
+      for (int i = 0; i < nq; ++i) pts[i + nq * (j + nq * k)] = {rq.xq[i], rq.xq[j], rq.xq[k]};
+  const PointTable t = map.table(pts);
+  const int64_t E = (int64_t)m.m[0] * m.m[1] * m.m[2];
+  const int n3 = n * n * n, q3 = nq * nq * nq;
+  double L[3];
+  for (int d = 0; d < 3; ++d) L[d] = m.hi[d] - m.lo[d];
+  double total = 0;
+#pragma omp parallel reduction(+ : total)
+  {
+    std::vector<double> J((size_t)9 * q3), X((size_t)3 * q3), a((size_t)nq * n * n), b((size_t)nq * nq * n);
+#pragma omp for schedule(static)
+    for (int64_t e = 0; e < E; ++e) {
+      map.eval(e, t, X.data(), J.data());
+      const double *xe = x + (size_t)e * n3;
+      for (int k = 0; k < n; ++k)   // x direction: a[k][j][qx]
+        for (int j = 0; j < n; ++j)
+          for (int qx = 0; qx < nq; ++qx) {
+            double s2 = 0;
+            for (int i = 0; i < n; ++i) s2 += S[(size_t)qx * n + i] * xe[i + n * (j + n * k)];
+            a[(size_t)(k * n + j) * nq + qx] = s2;
+          }
+      for (int k = 0; k < n; ++k)   // y direction: b[k][qy][qx]
+        for (int qy = 0; qy < nq; ++qy)
+          for (int qx = 0; qx < nq; ++qx) {
+            double s2 = 0;
+            for (int j = 0; j < n; ++j) s2 += S[(size_t)qy * n + j] * a[(size_t)(k * n + j) * nq + qx];
+            b[(size_t)(k * nq + qy) * nq + qx] = s2;
+          }
+      for (int qz = 0; qz < nq; ++qz)
+        for (int qy = 0; qy < nq; ++qy)
+          for (int qx = 0; qx < nq; ++qx) {
+            double uh = 0;
+            for (int k = 0; k < n; ++k) uh += S[(size_t)qz * n + k] * b[(size_t)(k * nq + qy) * nq + qx];
+            const int p = qx + nq * (qy + nq * qz);
+            double u = 1;
+            for (int d = 0; d < 3; ++d) u *= std::sin(M_PI * (X[(size_t)p * 3 + d] - m.lo[d]) / L[d]);
+            const double w = rq.wq[qx] * rq.wq[qy] * rq.wq[qz] * std::fabs(det3(&J[(size_t)p * 9]));
+            total += (uh - u) * (uh - u) * w;
+          }
+    }
+  }
+  return std::sqrt(total);
+}
+
 void coarse_matrix(const Mapping &map, const int bc[6], std::vector<double> &A, int &N) {
   const MeshDesc &m = map.mesh;
   const int grid[3] = {m.m[0] + 1, m.m[1] + 1, m.m[2] + 1};

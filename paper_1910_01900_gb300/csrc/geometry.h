@@ -41,6 +41,7 @@ void face_geometry(const Mapping &map, int n, std::vector<double> fdA[3], std::v
                    std::vector<double> &fwcart);
 void penalty(const Mapping &map, int n, double factor, std::vector<double> &tau);
 void manufactured_rhs(const Mapping &map, int n, const std::vector<double> &tau, std::vector<double> &b);
+double l2_error_manufactured(const Mapping &map, int n, const double *x_host);
 void coarse_matrix(const Mapping &map, const int bc[6], std::vector<double> &A, int &N);
 bool cholesky_inverse(std::vector<double> &A, int N);
 double tridiag_max_eig(const std::vector<double> &diag, const std::vector<double> &off);

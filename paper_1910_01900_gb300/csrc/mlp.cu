@@ -11,6 +11,7 @@
 // tiles (4 warps of 32 x 32), optional bias, ReLU and BF16 or FP32 output.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "sipg_internal.h"
@@ -139,10 +140,12 @@ __global__ void gather_features_kernel(const T *r, int n, int m0, int m1, int m2
     ss += v * v;
   }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  const double s = sqrt(ss / nf) + 1e-300;
+  // a cell whose local residual is (numerically) zero gets zero inputs and scale 0
+  const double s = sqrt(ss / nf);
+  const bool ok = s > 1e-30 && s < 1e30;
   for (int j = lane; j < ldx; j += 32)
-    X[(size_t)w * ldx + j] = __float2bfloat16(j < nf ? (float)(value(j) / s) : 0.f);
-  if (lane == 0) scale[w] = (float)s;
+    X[(size_t)w * ldx + j] = __float2bfloat16(ok && j < nf ? (float)(value(j) / s) : 0.f);
+  if (lane == 0) scale[w] = ok ? (float)s : 0.f;
 }
 
 // x[cell] += c * s_cell * y[cell][0..n^3)   (the learned smoothing step)
@@ -152,17 +155,18 @@ __global__ void apply_correction_kernel(T *x, int n3, int c0, int nc, const floa
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)nc * n3) return;
   const int w = (int)(i / n3), j = (int)(i - (long)w * n3);
-  x[(size_t)(c0 + w) * n3 + j] += (T)(c * scale[w] * Y[(size_t)w * ldy + j]);
+  const float y = Y[(size_t)w * ldy + j];
+  if (isfinite(y)) x[(size_t)(c0 + w) * n3 + j] += (T)(c * scale[w] * y);   // a non-finite output is skipped
 }
 
 // dY = (Y - T) / B as bf16 and the loss partial sums
-__global__ void mse_grad_kernel(const float *Y, const float *Tg, int B, int N, int ld, __nv_bfloat16 *dY,
+__global__ void mse_grad_kernel(const float *Y, const float *Tg, long ldt, int B, int N, int ld, __nv_bfloat16 *dY,
                                 float *dYf, double *loss) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)B * ld) return;
   const int r = (int)(i / ld), c = (int)(i - (long)r * ld);
   float d = 0.f;
-  if (c < N) d = Y[i] - Tg[(size_t)r * ld + c];
+  if (c < N) d = Y[i] - Tg[(size_t)r * ldt + c];
   if (c < N) atomicAdd(loss, 0.5 * (double)d * d / B);
   dY[i] = __float2bfloat16(d / B);
   dYf[i] = d / B;
@@ -210,6 +214,38 @@ __global__ void f2bf_kernel(const float *x, __nv_bfloat16 *y, long n) {
   if (i < n) y[i] = __float2bfloat16(x[i]);
 }
 
+// T[w][j] = e[cell_w][j] / s_w for j < n3, 0 in the padding
+__global__ void targets_kernel(const double *e, int n3, const int *cells, int c0, int nc, const float *scale, float *T,
+                               int ldt) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)nc * ldt) return;
+  const int w = (int)(i / ldt), j = (int)(i - (long)w * ldt);
+  const int cell = cells[c0 + w];
+  T[i] = (j < n3 && scale[w] > 0.f) ? (float)(e[(size_t)cell * n3 + j] / (double)scale[w]) : 0.f;
+}
+__global__ void sumsq_kernel(const float *x, long n, double *out) {
+  double s = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    s += (double)x[i] * x[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+__global__ void scale_kernel(float *x, long n, float a) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= a;
+}
+// row-padded fp32 -> bf16: Y[r][c] = X[r][c] for c < F, 0 for F <= c < Fp
+__global__ void pad_f2bf_kernel(const float *X, int B, int F, int Fp, __nv_bfloat16 *Y) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)B * Fp) return;
+  const int r = (int)(i / Fp), c = (int)(i - (long)r * Fp);
+  Y[i] = __float2bfloat16(c < F ? X[(size_t)r * F + c] : 0.f);
+}
+__global__ void bf2f_kernel(const __nv_bfloat16 *X, long n, float *Y) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Y[i] = __bfloat162float(X[i]);
+}
+
 inline int blocks(long n, int bs = 256) { return (int)((n + bs - 1) / bs); }
 
 }  // namespace
@@ -253,9 +289,9 @@ template cudaError_t mlp_correct<float>(float *, int, int, int, const float *, i
 template cudaError_t mlp_correct<double>(double *, int, int, int, const float *, int, const float *, float,
                                          cudaStream_t);
 
-cudaError_t mlp_mse_grad(const float *Y, const float *Tg, int B, int N, int ld, void *dY, float *dYf, double *loss,
-                         cudaStream_t s) {
-  mse_grad_kernel<<<blocks((long)B * ld), 256, 0, s>>>(Y, Tg, B, N, ld, (__nv_bfloat16 *)dY, dYf, loss);
+cudaError_t mlp_mse_grad(const float *Y, const float *Tg, long ldt, int B, int N, int ld, void *dY, float *dYf,
+                         double *loss, cudaStream_t s) {
+  mse_grad_kernel<<<blocks((long)B * ld), 256, 0, s>>>(Y, Tg, ldt, B, N, ld, (__nv_bfloat16 *)dY, dYf, loss);
   note_launch();
   return cudaGetLastError();
 }
@@ -282,6 +318,34 @@ cudaError_t mlp_adam(float *p, float *m, float *v, const float *g, long n, float
 }
 cudaError_t mlp_f2bf(const float *x, void *y, long n, cudaStream_t s) {
   f2bf_kernel<<<blocks(n), 256, 0, s>>>(x, (__nv_bfloat16 *)y, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_targets(const double *e, int n3, const int *cells, int c0, int nc, const float *scale, float *T,
+                        int ldt, cudaStream_t s) {
+  if (nc <= 0) return cudaSuccess;
+  targets_kernel<<<blocks((long)nc * ldt), 256, 0, s>>>(e, n3, cells, c0, nc, scale, T, ldt);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t mlp_sumsq(const float *x, long n, double *out, cudaStream_t s) {
+  sumsq_kernel<<<std::min(blocks(n), 152 * 8), 256, 0, s>>>(x, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t mlp_scale(float *x, long n, float a, cudaStream_t s) {
+  scale_kernel<<<blocks(n), 256, 0, s>>>(x, n, a);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t mlp_pad_f2bf(const float *X, int B, int F, int Fp, void *Y, cudaStream_t s) {
+  pad_f2bf_kernel<<<blocks((long)B * Fp), 256, 0, s>>>(X, B, F, Fp, (__nv_bfloat16 *)Y);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t mlp_bf2f(const void *X, long n, float *Y, cudaStream_t s) {
+  bf2f_kernel<<<blocks(n), 256, 0, s>>>((const __nv_bfloat16 *)X, n, Y);
   note_launch();
   return cudaGetLastError();
 }

@@ -126,6 +126,8 @@ void even_odd(const std::vector<double> &M, int n, int par, double *E, double *O
 
 }  // namespace
 
+void gauss_rule(int n, std::vector<double> &x, std::vector<double> &w) { x = gauss_points(n, w); }
+
 std::vector<double> lagrange_values(const std::vector<double> &nodes, double x) {
   const int n = (int)nodes.size();
   std::vector<double> v(n, 1.0);

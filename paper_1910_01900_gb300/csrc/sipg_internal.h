@@ -26,6 +26,7 @@ struct Rules1D {
   std::vector<double> lp0, lp1;// l_i'(0), l_i'(1)  (GL basis)
 };
 const Rules1D &rules(int n);
+void gauss_rule(int n, std::vector<double> &x, std::vector<double> &w);   // any n >= 1, on [0,1]
 std::vector<double> lagrange_values(const std::vector<double> &nodes, double x);
 std::vector<double> lagrange_derivs(const std::vector<double> &nodes, double x);
 
@@ -115,6 +116,8 @@ template <typename T>
 void upload_tables_dg(const Tables<T> &t);
 template <typename T>
 void upload_tables_fe(const Tables<T> &t);
+template <typename T>
+void upload_tables_batch(const Tables<T> &t);
 
 template <typename T>
 cudaError_t launch_dg_eval(int n, bool curved, const DGArgs<T> &a, cudaStream_t s, int cb = 0);
@@ -214,6 +217,29 @@ cudaError_t seg_dot(const Seg *segs, int np, int which, double *partials, unsign
 cudaError_t seg_update_xr(const Seg *segs, int np, double *partials, unsigned *counter, double *sc, int sc_stride,
                           cudaStream_t s);
 cudaError_t seg_update_p(const Seg *segs, int np, const double *sc, int sc_stride, int init, cudaStream_t s);
+
+// ---- learned smoother network (mlp.cu); bf16 buffers passed as void*
+cudaError_t mlp_gemm(const void *A, long sam, long sak, const void *B, long sbk, long sbn, int M, int N, int K,
+                     const float *bias, int relu, float *Cf, void *Cb, long ldc, int accumulate, cudaStream_t s);
+template <typename T>
+cudaError_t mlp_gather(const T *r, int n, const int m[3], const int *cells, int c0, int nc, void *X, int ldx,
+                       float *scale, cudaStream_t s);
+template <typename T>
+cudaError_t mlp_correct(T *x, int n3, int c0, int nc, const float *Y, int ldy, const float *scale, float c,
+                        cudaStream_t s);
+cudaError_t mlp_mse_grad(const float *Y, const float *Tg, long ldt, int B, int N, int ld, void *dY, float *dYf,
+                         double *loss, cudaStream_t s);
+cudaError_t mlp_relu_mask(void *dH, const void *H, long n, cudaStream_t s);
+cudaError_t mlp_colsum(const void *D, int bf16, int B, int N, int ld, float *g, cudaStream_t s);
+cudaError_t mlp_adam(float *p, float *m, float *v, const float *g, long n, float lr, int step, void *pb,
+                     cudaStream_t s);
+cudaError_t mlp_f2bf(const float *x, void *y, long n, cudaStream_t s);
+cudaError_t mlp_targets(const double *e, int n3, const int *cells, int c0, int nc, const float *scale, float *T,
+                        int ldt, cudaStream_t s);
+cudaError_t mlp_sumsq(const float *x, long n, double *out, cudaStream_t s);
+cudaError_t mlp_scale(float *x, long n, float a, cudaStream_t s);
+cudaError_t mlp_pad_f2bf(const float *X, int B, int F, int Fp, void *Y, cudaStream_t s);
+cudaError_t mlp_bf2f(const void *X, long n, float *Y, cudaStream_t s);
 
 // Kernel-launch accounting (every launch of the library increments it).
 void note_launch();

@@ -42,6 +42,27 @@ struct sipg_ctx {
   // cells per thread block of the finest-level DG passes, [precision][eval, integrate]
   // (0 = compiled default; set by the autotuner)
   int cb[2][2] = {{0, 0}, {0, 0}};
+  // learned smoother of the finest level (see "learned smoother" below)
+  struct Net {
+    bool ready = false;    // weights allocated
+    bool trained = false;
+    int F = 0, Fp = 0, H = 256, No = 0, n3 = 0;
+    long oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0, np = 0;
+    float cscale = 1.f;    // output scale c: correction = c * s * y
+    float *P = nullptr, *M = nullptr, *V = nullptr, *G = nullptr;   // fp32 params, Adam moments, grads
+    void *Pb = nullptr;    // bf16 copy of P
+    // inference / training buffers for up to `rows` rows
+    long rows = 0;
+    void *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dH = nullptr;
+    float *Y = nullptr, *dYf = nullptr, *scale = nullptr;
+    double *loss = nullptr;
+    double rho_cheb = 1.0;  // average rate of the Chebyshev cycle (judge of the learned one)
+    int steps_pre = 2, steps_post = 2;
+  } net;
+  int smoother = 0;          // 0 Chebyshev, 1 learned (finest level)
+  int use_learned = 0;       // current cycle uses the learned smoother
+  cudaGraphExec_t vgraph_l[2] = {nullptr, nullptr};   // graphs of the learned cycle
+  int vcalls_l[2] = {0, 0};
 };
 
 static std::string g_create_err;
@@ -259,6 +280,9 @@ void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_
   }
 }
 
+template <typename T>
+void learned_smooth(sipg_ctx *c, const T *b, T *x, int steps, bool zero_start);
+
 // Algorithm 2 with x^(l) = 0 on entry: rhs in lv[l].vb; returns the buffer
 // (vx or vt of that level) that holds x^(l).  No state changes between calls,
 // so the whole cycle can be captured once and replayed.
@@ -273,12 +297,15 @@ T *vcycle_rec(sipg_ctx *c, int l) {
   }
   T *x = (T *)L.vx[pi], *xt = (T *)L.vt[pi];
   const int ns = c->prm.cheb_degree;
-  chebyshev<T>(c, l, b, x, xt, ns, true);
+  const bool learned = (l == c->L) && c->use_learned;
+  if (learned) learned_smooth<T>(c, b, x, c->net.steps_pre, true);
+  else chebyshev<T>(c, l, b, x, xt, ns, true);
   apply_level<T>(c, l, x, (T *)L.vr[pi], 2, nullptr, nullptr, b);
   restrict_level<T>(c, l, (const T *)L.vr[pi], (T *)c->lv[l - 1].vb[pi]);
   const T *xc = vcycle_rec<T>(c, l - 1);
   prolongate_level<T>(c, l, xc, x);
-  chebyshev<T>(c, l, b, x, xt, ns, false);
+  if (learned) learned_smooth<T>(c, b, x, c->net.steps_post, false);
+  else chebyshev<T>(c, l, b, x, xt, ns, false);
   return x;
 }
 
@@ -303,12 +330,14 @@ void vcycle_fp64io(sipg_ctx *c, const double *r, double *z) { vcycle_body(c, r, 
 // use and replayed afterwards (one launch instead of ~100 per cycle).
 void precondition(sipg_ctx *c) {
   const int pi = c->prm.precision;
-  if (c->vgraph[pi]) {
-    CK(cudaGraphLaunch(c->vgraph[pi], c->stream));
+  cudaGraphExec_t *gslot = c->use_learned ? &c->vgraph_l[pi] : &c->vgraph[pi];
+  int *calls = c->use_learned ? &c->vcalls_l[pi] : &c->vcalls[pi];
+  if (*gslot) {
+    CK(cudaGraphLaunch(*gslot, c->stream));
     note_launch();
     return;
   }
-  if (c->stream == nullptr || c->vcalls[pi]++ < 1) {
+  if (c->stream == nullptr || (*calls)++ < 1) {
     vcycle_body(c, c->fr, c->fz);
     return;
   }
@@ -326,7 +355,7 @@ void precondition(sipg_ctx *c) {
   const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   CK(e);
-  c->vgraph[pi] = ex;
+  *gslot = ex;
   CK(cudaGraphLaunch(ex, c->stream));
   note_launch();
 }
@@ -508,6 +537,8 @@ void setup(sipg_ctx *c) {
     upload_tables_dg<float>(tf);
     upload_tables_fe<double>(td);
     upload_tables_fe<float>(tf);
+    upload_tables_batch<double>(td);
+    upload_tables_batch<float>(tf);
     CK(cudaGetLastError());
     CK(prepare_dg_kernels<double>());
     CK(prepare_dg_kernels<float>());
@@ -683,6 +714,8 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
   }
   const double r0 = std::sqrt(dot(c, c->fr, c->fr, N, 3));
   std::vector<double> hist{r0};
+  c->use_learned = (c->smoother == 1 && c->net.trained) ? 1 : 0;
+  const int learned_at_start = c->use_learned;
   precondition(c);
   CK(launch_dot2(c->fr, c->fz, nullptr, nullptr, N, c->partials, c->counter, c->scal + 0, s));
   CK(cudaMemcpyAsync(c->fp, c->fz, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -690,6 +723,7 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
   sipg_status st = SIPG_OK;
   double rn = r0;
   const bool fixed_mode = fixed > 0;
+  int fell_back = 0;
   while (true) {
     if (fixed_mode) {
       if (it >= fixed) break;
@@ -711,10 +745,18 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
       ++it;
       break;
     }
+    const double rprev = rn;
     rn = std::sqrt(sc[3]);
     ++it;
     hist.push_back(rn);
     if (!fixed_mode && rn <= rtol * r0) break;
+    // the Chebyshev cycle judges the learned one: a step that reduces the
+    // residual less than the Chebyshev cycle's average rate switches the rest
+    // of the solve back to Chebyshev (flexible CG keeps the iteration valid)
+    if (c->use_learned && rn > c->net.rho_cheb * rprev) {
+      c->use_learned = 0;
+      fell_back = 1;
+    }
     precondition(c);
     CK(launch_dot2(c->fr, c->fz, c->fz, c->fv, N, c->partials, c->counter, c->scal + 0, s));   // gamma, z.Ap
     CK(launch_fcg_update_p(c->fp, c->fz, c->scal, N, s));
@@ -735,9 +777,222 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
     info->n10 = (info->rho > 0 && info->rho < 1) ? -10.0 / std::log10(info->rho) : 0.0;
     info->seconds = ms * 1e-3;
     for (int j = 0; j < (int)hist.size() && j < 256; ++j) info->res_history[j] = hist[j];
+    info->learned = learned_at_start;
+    info->fell_back = fell_back;
   }
+  c->use_learned = 0;
   if (st == SIPG_ENOTCONV) c->err = "flexible CG reached maxit before the tolerance";
   return st;
+}
+
+
+// ------------------------------------------------------------ learned smoother
+// A per-cell network (input: the cell's residual and the neighbours' face
+// residuals, scaled by their RMS; output: the cell's correction) that stands in
+// for the Chebyshev smoother on the finest level.  Not in the paper.
+
+void net_setup(sipg_ctx *c, long rows) {
+  auto &N = c->net;
+  const Level &F = c->lv[c->L];
+  if (!N.ready) {
+    N.n3 = F.n * F.n * F.n;
+    N.F = N.n3 + 6 * F.n * F.n;
+    N.Fp = (N.F + 15) / 16 * 16;
+    N.No = (N.n3 + 15) / 16 * 16;
+    N.oW1 = 0;
+    N.ob1 = N.oW1 + (long)N.Fp * N.H;
+    N.oW2 = N.ob1 + N.H;
+    N.ob2 = N.oW2 + (long)N.H * N.H;
+    N.oW3 = N.ob2 + N.H;
+    N.ob3 = N.oW3 + (long)N.H * N.No;
+    N.np = N.ob3 + N.No;
+    N.P = dalloc<float>(c, N.np);
+    N.M = dalloc<float>(c, N.np);
+    N.V = dalloc<float>(c, N.np);
+    N.G = dalloc<float>(c, N.np);
+    N.Pb = dalloc<uint16_t>(c, N.np);
+    N.loss = dalloc<double>(c, 2);
+    // He-uniform initial weights from the counter-based generator, zero biases
+    std::vector<float> h(N.np, 0.f);
+    auto fill = [&](long off, int fin, int fanin_valid, int fout, uint64_t seed) {
+      const double lim = std::sqrt(6.0 / fanin_valid);
+      for (int i = 0; i < fin; ++i)
+        for (int j = 0; j < fout; ++j)
+          h[off + (long)i * fout + j] = i < fanin_valid ? (float)(lim * uniform_pm1(seed, (uint64_t)i * fout + j)) : 0.f;
+    };
+    fill(N.oW1, N.Fp, N.F, N.H, 4001);
+    fill(N.oW2, N.H, N.H, N.H, 4002);
+    fill(N.oW3, N.H, N.H, N.No, 4003);
+    CK(cudaMemcpy(N.P, h.data(), N.np * sizeof(float), cudaMemcpyHostToDevice));
+    CK(mlp_f2bf(N.P, N.Pb, N.np, c->stream));
+    N.ready = true;
+  }
+  if (rows > N.rows) {
+    N.X = dalloc<uint16_t>(c, rows * N.Fp);
+    N.H1 = dalloc<uint16_t>(c, rows * N.H);
+    N.H2 = dalloc<uint16_t>(c, rows * N.H);
+    N.dH = dalloc<uint16_t>(c, rows * N.H);
+    N.dY = dalloc<uint16_t>(c, rows * N.No);
+    N.Y = dalloc<float>(c, rows * N.No);
+    N.dYf = dalloc<float>(c, rows * N.No);
+    N.scale = dalloc<float>(c, rows);
+    N.rows = rows;
+  }
+}
+
+inline const void *bf(const void *base, long off) { return (const uint16_t *)base + off; }
+inline void *bfm(void *base, long off) { return (uint16_t *)base + off; }
+
+// Y = net(X) for B rows of X (bf16, row stride ldx elements)
+void net_forward(sipg_ctx *c, const void *X, long ldx, int B) {
+  auto &N = c->net;
+  cudaStream_t s = c->stream;
+  CK(mlp_gemm(X, ldx, 1, bf(N.Pb, N.oW1), N.H, 1, B, N.H, N.Fp, N.P + N.ob1, 1, nullptr, N.H1, N.H, 0, s));
+  CK(mlp_gemm(N.H1, N.H, 1, bf(N.Pb, N.oW2), N.H, 1, B, N.H, N.H, N.P + N.ob2, 1, nullptr, N.H2, N.H, 0, s));
+  CK(mlp_gemm(N.H2, N.H, 1, bf(N.Pb, N.oW3), N.No, 1, B, N.No, N.H, N.P + N.ob3, 0, N.Y, nullptr, N.No, 0, s));
+}
+
+// gradients of the mean squared error over B rows (X row stride ldx, T row stride ldt) into N.G
+void net_gradients(sipg_ctx *c, const void *X, long ldx, const float *T, long ldt, int B) {
+  auto &N = c->net;
+  cudaStream_t s = c->stream;
+  net_forward(c, X, ldx, B);
+  CK(mlp_mse_grad(N.Y, T, ldt, B, N.n3, N.No, N.dY, N.dYf, N.loss, s));
+  CK(mlp_gemm(N.H2, 1, N.H, N.dY, N.No, 1, N.H, N.No, B, nullptr, 0, N.G + N.oW3, nullptr, N.No, 0, s));
+  CK(mlp_colsum(N.dYf, 0, B, N.No, N.No, N.G + N.ob3, s));
+  CK(mlp_gemm(N.dY, N.No, 1, bf(N.Pb, N.oW3), 1, N.No, B, N.H, N.No, nullptr, 0, nullptr, N.dH, N.H, 0, s));
+  CK(mlp_relu_mask(N.dH, N.H2, (long)B * N.H, s));
+  CK(mlp_gemm(N.H1, 1, N.H, N.dH, N.H, 1, N.H, N.H, B, nullptr, 0, N.G + N.oW2, nullptr, N.H, 0, s));
+  CK(mlp_colsum(N.dH, 1, B, N.H, N.H, N.G + N.ob2, s));
+  CK(mlp_gemm(N.dH, N.H, 1, bf(N.Pb, N.oW2), 1, N.H, B, N.H, N.H, nullptr, 0, nullptr, N.H2, N.H, 0, s));
+  CK(mlp_relu_mask(N.H2, N.H1, (long)B * N.H, s));
+  CK(mlp_gemm(X, 1, ldx, N.H2, N.H, 1, N.Fp, N.H, B, nullptr, 0, N.G + N.oW1, nullptr, N.H, 0, s));
+  CK(mlp_colsum(N.H2, 1, B, N.H, N.H, N.G + N.ob1, s));
+}
+
+// steps of x <- x + c s net(features(b - A x)) on the finest level
+template <typename T>
+void learned_smooth(sipg_ctx *c, const T *b, T *x, int steps, bool zero_start) {
+  constexpr int pi = pidx<T>();
+  auto &N = c->net;
+  const Level &F = c->lv[c->L];
+  const int E = (int)F.ncells;
+  for (int st = 0; st < steps; ++st) {
+    const T *r;
+    if (zero_start && st == 0) {
+      CK(cudaMemsetAsync(x, 0, F.ndofs * sizeof(T), c->stream));
+      r = b;
+    } else {
+      apply_level<T>(c, c->L, x, (T *)F.vr[pi], 2, nullptr, nullptr, b);
+      r = (const T *)F.vr[pi];
+    }
+    CK(mlp_gather<T>(r, F.n, F.m, nullptr, 0, E, N.X, N.Fp, N.scale, c->stream));
+    net_forward(c, N.X, N.Fp, E);
+    CK(mlp_correct<T>(x, N.n3, 0, E, N.Y, N.No, N.scale, N.cscale, c->stream));
+  }
+}
+template void learned_smooth<double>(sipg_ctx *, const double *, double *, int, bool);
+template void learned_smooth<float>(sipg_ctx *, const float *, float *, int, bool);
+
+sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_train_info *info) {
+  auto t0 = std::chrono::steady_clock::now();
+  const Level &F = c->lv[c->L];
+  const int E = (int)F.ncells;
+  const int64_t Nd = F.ndofs;
+  const int B = 256;
+  const int NB = std::max(1, (npairs + B - 1) / B);
+  const long R = (long)NB * B;
+  net_setup(c, std::max<long>(E, B));
+  auto &N = c->net;
+  const int S = 4, J = 4;   // right-hand sides, iterates per right-hand side
+  void *Xall = dalloc<uint16_t>(c, R * N.Fp);
+  float *Tall = dalloc<float>(c, R * N.No);
+  float *sall = dalloc<float>(c, R);
+  int *cells = dalloc<int>(c, R);
+  double *b = dalloc<double>(c, Nd), *xs = dalloc<double>(c, Nd), *xj = dalloc<double>(c, Nd),
+         *r = dalloc<double>(c, Nd), *e = dalloc<double>(c, Nd);
+  std::vector<int> hc(R);
+  for (long i = 0; i < R; ++i) hc[i] = (int)(splitmix64(seed ^ (0x5151ull + (uint64_t)i)) % (uint64_t)E);
+  CK(cudaMemcpy(cells, hc.data(), R * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<double> hb(Nd);
+  double rho_sum = 0;
+  int rho_cnt = 0;
+  const int save_smoother = c->smoother;
+  c->smoother = 0;
+  long row = 0;
+  for (int sidx = 0; sidx < S; ++sidx) {
+    for (int64_t i = 0; i < Nd; ++i) hb[i] = uniform_pm1(seed + 1 + sidx, (uint64_t)i);
+    CK(cudaMemcpy(b, hb.data(), Nd * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(xs, 0, Nd * sizeof(double), c->stream));
+    sipg_solve_info inf{};
+    const sipg_status st = solve_impl(c, b, xs, 1e-12, 500, 0, &inf);
+    if (st != SIPG_OK) {
+      c->smoother = save_smoother;
+      return st;
+    }
+    rho_sum += inf.rho;
+    ++rho_cnt;
+    for (int j = 0; j < J; ++j) {
+      CK(cudaMemsetAsync(xj, 0, Nd * sizeof(double), c->stream));
+      if (j > 0) solve_impl(c, b, xj, 0.0, j, j, nullptr);
+      apply_level<double>(c, c->L, xj, r, 2, nullptr, nullptr, b);
+      CK(cudaMemcpyAsync(e, xs, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      CK(launch_axpy<double>(e, -1.0, xj, Nd, c->stream));
+      const long cnt = (sidx * J + j == S * J - 1) ? R - row : R / (S * J);
+      CK(mlp_gather<double>(r, F.n, F.m, cells, (int)row, (int)cnt, bfm(Xall, row * N.Fp), N.Fp, sall + row,
+                            c->stream));
+      CK(mlp_targets(e, N.n3, cells, (int)row, (int)cnt, sall + row, Tall + row * N.No, N.No, c->stream));
+      row += cnt;
+    }
+  }
+  c->smoother = save_smoother;
+  N.rho_cheb = rho_cnt ? rho_sum / rho_cnt : 1.0;
+  // output scale: RMS of the targets
+  CK(cudaMemsetAsync(N.loss, 0, 2 * sizeof(double), c->stream));
+  CK(mlp_sumsq(Tall, R * N.No, N.loss, c->stream));
+  double ss;
+  CK(cudaMemcpy(&ss, N.loss, sizeof(double), cudaMemcpyDeviceToHost));
+  const double cs = std::sqrt(ss / ((double)R * N.n3)) + 1e-300;
+  N.cscale = (float)cs;
+  CK(mlp_scale(Tall, R * N.No, (float)(1.0 / cs), c->stream));
+  // Adam over strided minibatches (rows i, i + NB, i + 2 NB, ...)
+  CK(cudaMemsetAsync(N.M, 0, N.np * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(N.V, 0, N.np * sizeof(float), c->stream));
+  double loss_first = 0, loss_last = 0;
+  int step = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    CK(cudaMemsetAsync(N.loss, 0, sizeof(double), c->stream));
+    for (int i = 0; i < NB; ++i) {
+      net_gradients(c, bf(Xall, (long)i * N.Fp), (long)NB * N.Fp, Tall + (long)i * N.No, (long)NB * N.No, B);
+      ++step;
+      const float lr = 1e-3f * (ep >= epochs * 2 / 3 ? 0.3f : 1.0f);
+      CK(mlp_adam(N.P, N.M, N.V, N.G, N.np, lr, step, N.Pb, c->stream));
+    }
+    double l;
+    CK(cudaMemcpy(&l, N.loss, sizeof(double), cudaMemcpyDeviceToHost));
+    l /= NB;
+    if (ep == 0) loss_first = l;
+    loss_last = l;
+    if (!std::isfinite(l)) {
+      c->err = "learned smoother training diverged (non-finite loss)";
+      return SIPG_ENAN;
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  N.trained = true;
+  // graphs of a learned cycle captured earlier hold old weights only by pointer: nothing to redo
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->npairs = (int)R;
+    info->epochs = epochs;
+    info->steps = step;
+    info->loss_first = loss_first;
+    info->loss_last = loss_last;
+    info->out_scale = cs;
+    info->cheb_rate = N.rho_cheb;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return SIPG_OK;
 }
 
 template <typename F>
@@ -823,6 +1078,8 @@ sipg_status sipg_destroy(sipg_ctx *c) {
   cudaStreamSynchronize(c->stream);
   for (auto &g : c->vgraph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto &g : c->vgraph_l)
+    if (g) cudaGraphExecDestroy(g);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
   return SIPG_OK;
@@ -867,6 +1124,19 @@ sipg_status sipg_rhs(sipg_ctx *c, int kind, double *b) {
     manufactured_rhs(map, F.n, tau, h);
     CK(cudaMemcpyAsync(b, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_l2_error(sipg_ctx *c, int kind, const double *x, double *err) {
+  if (!c || !x || !err || kind != 0) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    const Level &F = c->lv[c->L];
+    std::vector<double> h(F.ndofs);
+    CK(cudaMemcpyAsync(h.data(), x, F.ndofs * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    Mapping map(c->md);
+    *err = l2_error_manufactured(map, F.n, h.data());
     return SIPG_OK;
   });
 }
@@ -952,7 +1222,9 @@ sipg_status sipg_coarse_solve(sipg_ctx *c, const double *b, double *x) {
 sipg_status sipg_vcycle(sipg_ctx *c, const double *r, double *z) {
   if (!c || !r || !z || !c->solver) return SIPG_EINVAL;
   return guarded(c, [&]() -> sipg_status {
+    c->use_learned = (c->smoother == 1 && c->net.trained) ? 1 : 0;
     vcycle_fp64io(c, r, z);
+    c->use_learned = 0;
     return SIPG_OK;
   });
 }
@@ -1023,6 +1295,106 @@ sipg_status sipg_tile_shape(const sipg_ctx *c, int precision, int pass, int *cel
   const int n = c->lv[c->L].n;
   *cells_per_block = v ? v : (precision == 0 ? dg_cells_per_block<double>(n) : dg_cells_per_block<float>(n));
   return SIPG_OK;
+}
+
+sipg_status sipg_smoother_train(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_train_info *info) {
+  if (!c || !c->solver || npairs < 256 || npairs > 10000000 || epochs < 1) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status { return train_impl(c, npairs, epochs, seed, info); });
+}
+
+sipg_status sipg_set_smoother(sipg_ctx *c, int which, int steps_pre, int steps_post) {
+  if (!c || which < 0 || which > 1 || steps_pre < 1 || steps_post < 1 || steps_pre > 16 || steps_post > 16)
+    return SIPG_EINVAL;
+  if (which == 1 && !c->net.trained) {
+    c->err = "the learned smoother has not been trained (sipg_smoother_train)";
+    return SIPG_EINVAL;
+  }
+  c->smoother = which;
+  if (c->net.steps_pre != steps_pre || c->net.steps_post != steps_post) {
+    for (auto &g : c->vgraph_l)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+    c->vcalls_l[0] = c->vcalls_l[1] = 0;
+  }
+  c->net.steps_pre = steps_pre;
+  c->net.steps_post = steps_post;
+  return SIPG_OK;
+}
+
+sipg_status sipg_mlp_shape(sipg_ctx *c, int *in_dim, int *in_pad, int *hidden, int *out_dim, int *out_pad,
+                           int64_t *nparams) {
+  if (!c || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    net_setup(c, 256);
+    const auto &N = c->net;
+    if (in_dim) *in_dim = N.F;
+    if (in_pad) *in_pad = N.Fp;
+    if (hidden) *hidden = N.H;
+    if (out_dim) *out_dim = N.n3;
+    if (out_pad) *out_pad = N.No;
+    if (nparams) *nparams = N.np;
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_mlp_params(sipg_ctx *c, int set, float *host) {
+  if (!c || !c->solver || !host) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    net_setup(c, 256);
+    auto &N = c->net;
+    if (set) {
+      CK(cudaMemcpy(N.P, host, N.np * sizeof(float), cudaMemcpyHostToDevice));
+      CK(mlp_f2bf(N.P, N.Pb, N.np, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    } else {
+      CK(cudaMemcpy(host, N.P, N.np * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_mlp_forward(sipg_ctx *c, const float *X, int B, float *Y) {
+  if (!c || !c->solver || !X || !Y || B < 1) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    net_setup(c, B);
+    auto &N = c->net;
+    CK(mlp_pad_f2bf(X, B, N.F, N.Fp, N.X, c->stream));
+    net_forward(c, N.X, N.Fp, B);
+    CK(cudaMemcpyAsync(Y, N.Y, (size_t)B * N.No * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_mlp_gradients(sipg_ctx *c, const float *X, const float *T, int B, float *grads_host,
+                               double *loss) {
+  if (!c || !c->solver || !X || !T || !grads_host || B < 1) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    net_setup(c, B);
+    auto &N = c->net;
+    CK(mlp_pad_f2bf(X, B, N.F, N.Fp, N.X, c->stream));
+    CK(cudaMemsetAsync(N.loss, 0, sizeof(double), c->stream));
+    net_gradients(c, N.X, N.Fp, T, N.n3, B);
+    CK(cudaMemcpyAsync(grads_host, N.G, N.np * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    double l = 0;
+    CK(cudaMemcpyAsync(&l, N.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (loss) *loss = l;
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_mlp_features(sipg_ctx *c, const double *r, float *feat, float *scale) {
+  if (!c || !c->solver || !r || !feat || !scale) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    const Level &F = c->lv[c->L];
+    net_setup(c, F.ncells);
+    auto &N = c->net;
+    CK(mlp_gather<double>(r, F.n, F.m, nullptr, 0, (int)F.ncells, N.X, N.Fp, scale, c->stream));
+    CK(mlp_bf2f(N.X, F.ncells * (long)N.Fp, feat, c->stream));
+    return SIPG_OK;
+  });
 }
 
 sipg_status sipg_launch_count(unsigned long long *n) {

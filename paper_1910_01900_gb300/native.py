@@ -22,7 +22,15 @@ EXPORTS = [
     "sipg_coarse_solve", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
     "sipg_operator_apply_noalloc", "sipg_launch_count", "sipg_batch_create", "sipg_batch_destroy",
     "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_solve", "sipg_tile_shape",
+    "sipg_smoother_train", "sipg_set_smoother", "sipg_mlp_shape", "sipg_mlp_params", "sipg_mlp_forward",
+    "sipg_mlp_gradients", "sipg_mlp_features", "sipg_l2_error",
 ]
+
+
+class TrainInfo(ctypes.Structure):
+    _fields_ = [("npairs", ctypes.c_int), ("epochs", ctypes.c_int), ("steps", ctypes.c_int),
+                ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("out_scale", ctypes.c_double),
+                ("cheb_rate", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
 class Mesh(ctypes.Structure):
@@ -42,7 +50,8 @@ class Params(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("r0_norm", ctypes.c_double),
                 ("r_norm", ctypes.c_double), ("rho", ctypes.c_double), ("n10", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("res_history", ctypes.c_double * 256)]
+                ("seconds", ctypes.c_double), ("res_history", ctypes.c_double * 256), ("learned", ctypes.c_int),
+                ("fell_back", ctypes.c_int)]
 
 
 _lib = None
@@ -83,6 +92,15 @@ def lib():
         L.sipg_fma_peak.argtypes = [i32, vp, ctypes.POINTER(dbl)]
         L.sipg_launch_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
         L.sipg_tile_shape.argtypes = [vp, i32, i32, ctypes.POINTER(i32)]
+        L.sipg_smoother_train.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(TrainInfo)]
+        L.sipg_set_smoother.argtypes = [vp, i32, i32, i32]
+        ip = ctypes.POINTER(i32)
+        L.sipg_mlp_shape.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.POINTER(i64)]
+        L.sipg_mlp_params.argtypes = [vp, i32, vp]
+        L.sipg_mlp_forward.argtypes = [vp, vp, i32, vp]
+        L.sipg_mlp_gradients.argtypes = [vp, vp, vp, i32, vp, ctypes.POINTER(dbl)]
+        L.sipg_mlp_features.argtypes = [vp, vp, vp, vp]
+        L.sipg_l2_error.argtypes = [vp, i32, vp, ctypes.POINTER(dbl)]
         L.sipg_batch_create.argtypes = [i32, ctypes.POINTER(Mesh), ctypes.POINTER(Params), ctypes.POINTER(vp)]
         L.sipg_batch_destroy.argtypes = [vp]
         L.sipg_batch_last_error.argtypes = [vp]
@@ -206,6 +224,13 @@ class Context:
         import torch
         self._check(lib().sipg_rhs(self.h, kind, _ptr(b, torch.float64, self.num_dofs())))
 
+    def l2_error(self, x, kind=0):
+        import torch
+        e = ctypes.c_double()
+        self._check(lib().sipg_l2_error(self.h, int(kind), _ptr(x, torch.float64, self.num_dofs()),
+                                        ctypes.byref(e)))
+        return e.value
+
     def apply(self, u, v, precision=None):
         import torch
         precision = (0 if u.dtype == torch.float64 else 1) if precision is None else precision
@@ -267,6 +292,59 @@ class Context:
                                           ctypes.c_void_p(x_host.ctypes.data), float(rtol), int(maxit),
                                           ctypes.byref(info)))
         return info
+
+    # ------------------------------------------------------ learned smoother
+    def train_smoother(self, npairs=100000, epochs=20, seed=2024):
+        info = TrainInfo()
+        self._check(lib().sipg_smoother_train(self.h, int(npairs), int(epochs), int(seed), ctypes.byref(info)))
+        return info
+
+    def set_smoother(self, which, steps_pre=2, steps_post=2):
+        self._check(lib().sipg_set_smoother(self.h, int(which), int(steps_pre), int(steps_post)))
+
+    def mlp_shape(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        n = ctypes.c_int64()
+        self._check(lib().sipg_mlp_shape(self.h, *[ctypes.byref(x) for x in v], ctypes.byref(n)))
+        keys = ("in_dim", "in_pad", "hidden", "out_dim", "out_pad")
+        d = {k: x.value for k, x in zip(keys, v)}
+        d["nparams"] = n.value
+        return d
+
+    def mlp_params(self, values=None):
+        import numpy as np
+        n = self.mlp_shape()["nparams"]
+        if values is None:
+            out = np.empty(n, dtype=np.float32)
+            self._check(lib().sipg_mlp_params(self.h, 0, ctypes.c_void_p(out.ctypes.data)))
+            return out
+        a = np.ascontiguousarray(values, dtype=np.float32)
+        assert a.size == n
+        self._check(lib().sipg_mlp_params(self.h, 1, ctypes.c_void_p(a.ctypes.data)))
+
+    def mlp_forward(self, X, Y):
+        import torch
+        sh = self.mlp_shape()
+        B = X.shape[0]
+        self._check(lib().sipg_mlp_forward(self.h, _ptr(X, torch.float32, B * sh["in_dim"]), B,
+                                           _ptr(Y, torch.float32, B * sh["out_pad"])))
+
+    def mlp_gradients(self, X, T):
+        import numpy as np
+        import torch
+        sh = self.mlp_shape()
+        B = X.shape[0]
+        g = np.empty(sh["nparams"], dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(lib().sipg_mlp_gradients(self.h, _ptr(X, torch.float32, B * sh["in_dim"]),
+                                             _ptr(T, torch.float32, B * sh["out_dim"]), B,
+                                             ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)))
+        return g, loss.value
+
+    def mlp_features(self, r, feat, scale):
+        import torch
+        self._check(lib().sipg_mlp_features(self.h, _ptr(r, torch.float64, self.num_dofs()),
+                                            _ptr(feat, torch.float32), _ptr(scale, torch.float32)))
 
     def tile_shape(self, precision, pass_):
         v = ctypes.c_int()

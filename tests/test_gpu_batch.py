@@ -36,6 +36,7 @@ def test_batched_apply_equals_single_problem_and_oracle(deform):
         u = torch.as_tensor(sipg_inputs.uniform(n, 50 + i)).to(DEV)
         ref = torch.empty_like(u)
         B.contexts[i].apply(u, ref)
+        torch.cuda.synchronize()
         us.append(u)
         vs.append(torch.full_like(u, float("nan")))
         refs.append(ref)
@@ -86,6 +87,7 @@ def test_seeded_uneven_batch_converges():
         assert infos[i].converged, i
         r = torch.empty_like(bs[i])
         B.contexts[i].apply(xs[i], r)
+        torch.cuda.synchronize()   # the problem's context works on its own stream
         res = (torch.linalg.norm(bs[i] - r) / torch.linalg.norm(bs[i])).item()
         assert res <= 2e-10, (i, res)
         assert 3 <= infos[i].iterations <= 12, (i, infos[i].iterations)

@@ -1,0 +1,88 @@
+"""Learned smoother (GPU): network kernels against the CPU reference network,
+training, and the flexible-CG solve with the network in place of Chebyshev."""
+import numpy as np
+import pytest
+
+import sipg_inputs
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _split(flat, sh):
+    Fp, H, No = sh["in_pad"], sh["hidden"], sh["out_pad"]
+    o = 0
+    parts = []
+    for shape in ((Fp, H), (H,), (H, H), (H,), (H, No), (No,)):
+        n = int(np.prod(shape))
+        parts.append(flat[o:o + n].reshape(shape).astype(np.float64))
+        o += n
+    W1, b1, W2, b2, W3, b3 = parts
+    return [W1[:sh["in_dim"]], W2, W3[:, :sh["out_dim"]]], [b1, b2, b3[:sh["out_dim"]]]
+
+
+def _ctx(m, k, deform=1, precision=1):
+    from paper_1910_01900_gb300 import Context
+    return Context(m, k, deform=deform, precision=precision)
+
+
+def test_features_match_oracle():
+    m, k = (4, 3, 5), 3
+    ctx = _ctx(m, k)
+    sh = ctx.mlp_shape()
+    n = ctx.num_dofs()
+    r = sipg_inputs.uniform(n, 77)
+    E = m[0] * m[1] * m[2]
+    feat = torch.empty(E * sh["in_pad"], dtype=torch.float32, device=DEV)
+    scale = torch.empty(E, dtype=torch.float32, device=DEV)
+    ctx.mlp_features(torch.as_tensor(r).to(DEV), feat, scale)
+    F = mlp.features(r, m, k + 1)
+    s = np.sqrt(np.mean(F * F, axis=1))
+    got = feat.cpu().numpy().reshape(E, sh["in_pad"])[:, :sh["in_dim"]]
+    assert np.allclose(scale.cpu().numpy(), s, rtol=1e-6)
+    assert np.max(np.abs(got - mlp.bf16_round(F / s[:, None]))) <= 2 ** -7 * np.max(np.abs(F / s[:, None]))
+
+
+def test_forward_and_gradients_match_cpu_network():
+    ctx = _ctx(4, 4)
+    sh = ctx.mlp_shape()
+    rng = np.random.default_rng(5)
+    flat = ctx.mlp_params()
+    flat[:] = rng.standard_normal(flat.size).astype(np.float32) * 0.05
+    ctx.mlp_params(flat)
+    Ws, bs = _split(flat, sh)
+    B = 200
+    X = rng.standard_normal((B, sh["in_dim"])).astype(np.float32)
+    T = rng.standard_normal((B, sh["out_dim"])).astype(np.float32)
+    Y = torch.empty(B * sh["out_pad"], dtype=torch.float32, device=DEV)
+    ctx.mlp_forward(torch.as_tensor(X).to(DEV), Y)
+    yref, _ = mlp.forward(X.astype(np.float64), Ws, bs, bf16=True)
+    y = Y.cpu().numpy().reshape(B, sh["out_pad"])[:, :sh["out_dim"]]
+    assert np.linalg.norm(y - yref) / np.linalg.norm(yref) <= 1e-2
+    g, loss = ctx.mlp_gradients(torch.as_tensor(X).to(DEV), torch.as_tensor(T).to(DEV))
+    L, gW, gb = mlp.loss_and_grads(X.astype(np.float64), T.astype(np.float64), Ws, bs, bf16=True)
+    assert abs(loss - L) <= 1e-2 * L
+    gWs, gbs = _split(g, sh)
+    for a, b in zip(gWs + gbs, gW + gb):
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 3e-2
+
+
+def test_training_and_learned_solve():
+    """Train on pairs from the plain cycle; the FCG solve still reaches 1e-10."""
+    m, k = 8, 3
+    ctx = _ctx(m, k)
+    info = ctx.train_smoother(npairs=20000, epochs=8, seed=7)
+    assert info.loss_last < info.loss_first
+    b = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_RHS)).to(DEV)
+    x0 = torch.zeros_like(b)
+    ref = ctx.solve(b, x0, rtol=1e-10)
+    ctx.set_smoother(1, 2, 2)
+    x1 = torch.zeros_like(b)
+    got = ctx.solve(b, x1, rtol=1e-10, maxit=200)
+    assert got.converged and got.learned == 1
+    err = (torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0)).item()
+    assert err <= 1e-8
+    ctx.set_smoother(0)
+    assert ref.converged

@@ -269,3 +269,49 @@ def test_autotuned_tile_shapes_keep_parity(k, deform):
     for prec in (0, 1):
         for p in (0, 1):
             assert ctx.tile_shape(prec, p) in tile_candidates(k + 1)
+
+
+def test_apply_is_deterministic_bitwise():
+    """No atomics anywhere: two applications give bit-identical results."""
+    ctx = _ctx((5, 4, 3), 4, deform=1, operator_only=True)
+    u = gpu(sipg_inputs.uniform(ctx.num_dofs(), 9))
+    v1, v2 = torch.empty_like(u), torch.empty_like(u)
+    ctx.apply(u, v1)
+    ctx.apply(u, v2)
+    assert torch.equal(v1, v2)
+
+
+def test_maxit_reports_not_converged():
+    from paper_1910_01900_gb300 import native
+    ctx = _ctx(4, 3)
+    b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+    ctx.rhs(b)
+    x = torch.zeros_like(b)
+    info = ctx.solve(b, x, rtol=1e-10, maxit=1, allow_notconv=True)
+    assert info.iterations == 1 and not info.converged
+    import ctypes
+    st = native.lib().sipg_solve(ctx.h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), 1e-10, 1, 0,
+                                 None)
+    assert st == native.ENOTCONV
+
+
+def test_penalty_robustness_of_cph_on_gpu():
+    """cph iteration counts barely move when the penalty grows 1000x (Table PenaltyFactor, cph rows)."""
+    its = []
+    for pf in (1.0, 1000.0):
+        ctx = _ctx(8, 3, penalty_factor=pf)
+        b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+        ctx.rhs(b)
+        x = torch.zeros_like(b)
+        its.append(ctx.solve(b, x, rtol=1e-10).n10)
+    assert abs(its[1] - its[0]) < 1.0, its
+
+
+@pytest.mark.parametrize("m,k,deform", [(4, 2, 0), (3, 4, 1), (2, 8, 1)])
+def test_l2_error_diagnostic_matches_oracle(m, k, deform):
+    ctx = _ctx(m, k, deform=deform, operator_only=True)
+    x = sipg_inputs.uniform(ctx.num_dofs(), 31)
+    e = ctx.l2_error(gpu(x))
+    exact = lambda p: np.prod(np.sin(np.pi * p), axis=-1)  # noqa: E731
+    ref = SIPG(Mesh(m, deform=deform), k).l2_error(x, exact)
+    assert abs(e - ref) <= 1e-12 * ref
