@@ -74,8 +74,9 @@ typedef struct {
   int precision;           /* V-cycle precision: 0 FP64, 1 FP32 (Section 4,
                               mixed-precision multigrid); the outer solver and
                               the coarse solve are always FP64              */
-  int p_coarsen;           /* 0: p_{l-1} = floor(p_l/2) (Section 3.2), the only
-                              sequence built                                 */
+  int p_coarsen;           /* p-sequence of the FE levels (Section 3.2):
+                              0 p_{l-1} = floor(p_l/2) (default, preferred by
+                              the paper), 1 p_{l-1} = p_l - 1, 2 straight to 1 */
   int cheb_degree;         /* n_s smoothing steps pre and post, default 5      */
   double cheb_lo, cheb_hi; /* smoothing range [lo, hi] * lambda_max: 0.06, 1.2 */
   int eig_iters;           /* CG iterations of the lambda_max estimate, 20     */
@@ -233,6 +234,8 @@ typedef struct {
   double out_scale;               /* c                                            */
   double cheb_rate;               /* average rate of the Chebyshev cycle         */
   double seconds;                 /* wall time of data generation and training  */
+  double target_max;              /* largest |e|/s of the data (before scaling)  */
+  double nonfinite;               /* number of non-finite targets (0 expected)   */
 } sipg_train_info;
 /* Generates npairs (cell residual -> cell error) pairs from the plain cycle:
  * 4 seeded uniform right-hand sides, each solved to 1e-12, and the first 4

@@ -30,7 +30,7 @@ import sipg_inputs
 from .dg import SIPG
 from .fe import FESpace
 from .mesh import Mesh
-from .transfer import c_transfer, fe_transfer
+from .transfer import c_transfer, dg_transfer, fe_transfer
 
 
 def chebyshev(apply_A, dinv, b, x, lam, ns, lo=0.06, hi=1.2, x_is_zero=False):
@@ -134,26 +134,54 @@ def p_sequence(k, rule="half"):
 
 
 class CPHMultigrid:
-    """The cph V-cycle preconditioner, levels stored coarse (0) to fine (L)."""
+    """Hybrid multigrid V-cycle preconditioner, levels stored coarse (0) to fine (L).
+
+    ``order`` lists the coarsening steps from the finest level (Section 3.2,
+    Table SummaryCoarseningStrategies): 'c' DG -> FE at equal h and p, 'p'
+    all polynomial levels down to degree 1, 'h' all geometric levels.  The
+    default 'cph' is the paper's preferred strategy.  The coarsest level is
+    solved directly (its space is DG when the order has no 'c').
+    """
 
     def __init__(self, mesh, k, penalty_factor=1.0, ns=5, cheb_lo=0.06, cheb_hi=1.2,
-                 eig_iters=20, lambdas=None, assemble_limit=6e7, p_rule="half"):
+                 eig_iters=20, lambdas=None, assemble_limit=6e7, p_rule="half", order="cph"):
         self.ns, self.cheb_lo, self.cheb_hi = ns, cheb_lo, cheb_hi
-        fine = []
-        dg = SIPG(mesh, k, penalty_factor)
-        n3 = dg.n ** 3
-        fine.append(Level("dg", dg, dg.assemble() if dg.n_dofs * n3 * 7 <= assemble_limit else None))
-        for p in p_sequence(k, p_rule):
-            fe = FESpace(mesh, p)
-            fine.append(Level("fe", fe, fe.assemble() if fe.n_dofs * (2 * p + 1) ** 3 <= assemble_limit else None))
-        for cm in coarse_meshes(mesh)[1:]:
-            fe = FESpace(cm, 1)
-            fine.append(Level("fe", fe, fe.assemble()))
+
+        def make(kind, p, msh):
+            if kind == "dg":
+                sp_ = SIPG(msh, p, penalty_factor)
+                big = sp_.n_dofs * sp_.n ** 3 * 7 > assemble_limit
+            else:
+                sp_ = FESpace(msh, p)
+                big = sp_.n_dofs * (2 * p + 1) ** 3 > assemble_limit
+            return Level(kind, sp_, None if big else sp_.assemble())
+
+        kind, p, msh = "dg", k, mesh
+        fine = [make(kind, p, msh)]
+        for step in order:
+            if step == "c":
+                kind = "fe"
+                fine.append(make(kind, p, msh))
+            elif step == "p":
+                for q in p_sequence(p, p_rule)[1:]:
+                    p = q
+                    fine.append(make(kind, p, msh))
+            elif step == "h":
+                for cm in coarse_meshes(msh)[1:]:
+                    msh = cm
+                    fine.append(make(kind, p, msh))
+            else:
+                raise ValueError("order letters are c, p, h")
         self.levels = fine[::-1]
         # transfers between consecutive levels
         for l in range(1, len(self.levels)):
             lf, lc = self.levels[l], self.levels[l - 1]
-            lf.P = c_transfer(lf.space.n, lc.space) if lf.kind == "dg" else fe_transfer(lf.space, lc.space)
+            if lf.kind == "dg" and lc.kind == "fe":
+                lf.P = c_transfer(lf.space.n, lc.space)
+            elif lf.kind == "dg":
+                lf.P = dg_transfer(lf.space, lc.space)
+            else:
+                lf.P = fe_transfer(lf.space, lc.space)
         # smoother data on levels l > 0, coarse factor on l = 0
         for l, lev in enumerate(self.levels):
             if l == 0:

@@ -97,3 +97,41 @@ def fe_transfer(fine, coarse):
     Zf = sp.diags((~fine.constrained).astype(np.float64))
     Zc = sp.diags((~coarse.constrained).astype(np.float64))
     return (Zf @ P @ Zc).tocsr()
+
+
+def dg_transfer(fine, coarse):
+    """P: coarse DG space -> fine DG space (p-transfer on one mesh or 2:1 h-transfer).
+
+    DG spaces share no nodes, so S_e has no multiplicity weights and P is block
+    diagonal over the fine cells: the block of a fine cell is the L2 projection
+    of its parent cell's basis (Section 3.2).
+    """
+    mf, mc = fine.mesh, coarse.mesh
+    if mf.m == mc.m:
+        kind = "p"
+    elif all(mf.m[d] == 2 * mc.m[d] for d in range(3)):
+        kind = "h"
+    else:
+        raise ValueError("fine mesh must equal or refine the coarse mesh 2:1")
+    nf3, nc3 = fine.n ** 3, coarse.n ** 3
+    rows, cols, vals = [], [], []
+    ijk = mf.cell_ijk(np.arange(mf.n_cells))
+    if kind == "p":
+        P1 = projection_1d(fine.nodes, coarse.nodes)
+        blocks = {None: _kron3(P1, P1, P1)}
+    else:
+        P1 = [projection_1d(fine.nodes, coarse.nodes, child=c) for c in (0, 1)]
+        blocks = {(cx, cy, cz): _kron3(P1[cx], P1[cy], P1[cz])
+                  for cz in (0, 1) for cy in (0, 1) for cx in (0, 1)}
+    for e in range(mf.n_cells):
+        if kind == "p":
+            parent, key = e, None
+        else:
+            parent = mc.cell_index(ijk[e, 0] // 2, ijk[e, 1] // 2, ijk[e, 2] // 2)
+            key = tuple(int(v) for v in ijk[e] % 2)
+        blk = blocks[key]
+        rows.append(np.repeat(e * nf3 + np.arange(nf3), nc3))
+        cols.append(np.tile(parent * nc3 + np.arange(nc3), nf3))
+        vals.append(blk.ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(fine.n_dofs, coarse.n_dofs))

@@ -65,10 +65,12 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
     }
   }
   __syncthreads();
-  T *gg = a.grad + (size_t)cell0 * 3 * N3;
-  for (int i = tid; i < ncta * 3 * N3; i += NT) {
-    const int c = i / (3 * N3);
-    gg[i] = sm[c * 4 * N3 + N3 + (i - c * 3 * N3)];
+  if (!a.recompute) {
+    T *gg = a.grad + (size_t)cell0 * 3 * N3;
+    for (int i = tid; i < ncta * 3 * N3; i += NT) {
+      const int c = i / (3 * N3);
+      gg[i] = sm[c * 4 * N3 + N3 + (i - c * 3 * N3)];
+    }
   }
   if (!act) return;
   const int cell = cell0 + cl;
@@ -140,10 +142,37 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
   T *st = sm + cl * 4 * N3;   // value accumulator, then the integrated tile
   T *sg = st + N3;            // three gradient components
 
-  const T *gg = a.grad + (size_t)cell0 * 3 * N3;
-  for (int i = tid; i < ncta * 3 * N3; i += NT) {
-    const int c = i / (3 * N3);
-    sm[c * 4 * N3 + N3 + (i - c * 3 * N3)] = gg[i];
+  if (a.recompute) {
+    // gradient at the Gauss points again from u: 3 interpolation and 3
+    // collocation-derivative sweeps (the value slot st is free until the faces)
+    const T *ug = a.u + (size_t)cell0 * N3;
+    for (int i = tid; i < ncta * N3; i += NT) {
+      const int c = i / N3;
+      sm[c * 4 * N3 + (i - c * N3)] = ug[i];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      if (act) sweep_inplace<T, N, MS>(st, d, l);
+      __syncthreads();
+    }
+    if (act) {
+#pragma unroll 1
+      for (int d = 0; d < 3; ++d) {
+        int base, stride;
+        line_of<N>(d, l, base, stride);
+        T x[N], y[N];
+        load_line<T, N>(st, base, stride, x);
+        apply_mat<T, N, MD>(x, y);
+        store_line<T, N>(sg + d * N3, base, stride, y);
+      }
+    }
+  } else {
+    const T *gg = a.grad + (size_t)cell0 * 3 * N3;
+    for (int i = tid; i < ncta * 3 * N3; i += NT) {
+      const int c = i / (3 * N3);
+      sm[c * 4 * N3 + N3 + (i - c * 3 * N3)] = gg[i];
+    }
   }
   __syncthreads();
   for (int i = tid; i < ncta * N3; i += NT) {

@@ -230,6 +230,18 @@ __global__ void sumsq_kernel(const float *x, long n, double *out) {
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
+// max |x| over the finite entries (as ordered bits) and the number of non-finite entries
+__global__ void stats_kernel(const float *x, long n, unsigned *maxbits, unsigned long long *bad) {
+  unsigned m = 0;
+  unsigned long long nb = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    if (!isfinite(v)) ++nb;
+    else m = max(m, __float_as_uint(fabsf(v)));
+  }
+  atomicMax(maxbits, m);
+  if (nb) atomicAdd(bad, nb);
+}
 __global__ void scale_kernel(float *x, long n, float a) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] *= a;
@@ -331,6 +343,11 @@ cudaError_t mlp_targets(const double *e, int n3, const int *cells, int c0, int n
 }
 cudaError_t mlp_sumsq(const float *x, long n, double *out, cudaStream_t s) {
   sumsq_kernel<<<std::min(blocks(n), 152 * 8), 256, 0, s>>>(x, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t mlp_stats(const float *x, long n, unsigned *maxbits, unsigned long long *bad, cudaStream_t s) {
+  stats_kernel<<<std::min(blocks(n), 152 * 8), 256, 0, s>>>(x, n, maxbits, bad);
   note_launch();
   return cudaGetLastError();
 }

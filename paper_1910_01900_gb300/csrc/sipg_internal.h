@@ -61,6 +61,9 @@ struct DGArgs {
   int m[3];
   int ncells;
   int bc[6];
+  // 1: the evaluation pass does not store the gradient and the integration
+  // pass recomputes it from u (less traffic, more arithmetic: used in FP32)
+  int recompute;
   // epilogue: mode 0 out = Au; 1 out = c1 x + c2 xp + c3 dinv (b - Au); 2 out = b - Au
   int mode;
   const T *x, *xp, *b, *dinv;
@@ -238,6 +241,7 @@ cudaError_t mlp_targets(const double *e, int n3, const int *cells, int c0, int n
                         int ldt, cudaStream_t s);
 cudaError_t mlp_sumsq(const float *x, long n, double *out, cudaStream_t s);
 cudaError_t mlp_scale(float *x, long n, float a, cudaStream_t s);
+cudaError_t mlp_stats(const float *x, long n, unsigned *maxbits, unsigned long long *bad, cudaStream_t s);
 cudaError_t mlp_pad_f2bf(const float *X, int B, int F, int Fp, void *Y, cudaStream_t s);
 cudaError_t mlp_bf2f(const void *X, long n, float *Y, cudaStream_t s);
 

@@ -148,6 +148,9 @@ DGArgs<T> dg_args(sipg_ctx *c, const Level &L) {
   a.tau = (const T *)L.tau[pi];
   a.ncells = (int)L.ncells;
   for (int s = 0; s < 6; ++s) a.bc[s] = c->mesh.bc[s];
+  // FP64 is bound by its arithmetic: store the gradient once; FP32 is bound
+  // by traffic: recompute it instead of a 24 B/DoF round trip
+  a.recompute = sizeof(T) == 4 ? 1 : 0;
   return a;
 }
 
@@ -569,9 +572,9 @@ void setup(sipg_ctx *c) {
   if (c->solver) {
     int p = P.degree;
     specs.push_back({1, p, md, -1});
-    while (p > 1) {
+    while (p > 1) {   // p-sequence: floor(p/2) (default), p-1, or straight to 1 (Section 3.2)
       specs.back().t_kind = 1;
-      p = std::max(1, p / 2);
+      p = P.p_coarsen == 0 ? std::max(1, p / 2) : (P.p_coarsen == 1 ? p - 1 : 1);
       specs.push_back({1, p, md, -1});
     }
     MeshDesc cm = md;
@@ -947,6 +950,17 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   }
   c->smoother = save_smoother;
   N.rho_cheb = rho_cnt ? rho_sum / rho_cnt : 1.0;
+  // data statistics (targets before scaling), for the training report
+  unsigned long long *bad = dalloc<unsigned long long>(c, 2);
+  unsigned *mx = (unsigned *)(bad + 1);
+  CK(cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned long long), c->stream));
+  CK(mlp_stats(Tall, R * N.No, mx, bad, c->stream));
+  unsigned long long hbad = 0;
+  unsigned hmx = 0;
+  CK(cudaMemcpy(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost));
+  float tmax;
+  std::memcpy(&tmax, &hmx, sizeof(tmax));
   // output scale: RMS of the targets
   CK(cudaMemsetAsync(N.loss, 0, 2 * sizeof(double), c->stream));
   CK(mlp_sumsq(Tall, R * N.No, N.loss, c->stream));
@@ -974,7 +988,9 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
     if (ep == 0) loss_first = l;
     loss_last = l;
     if (!std::isfinite(l)) {
-      c->err = "learned smoother training diverged (non-finite loss)";
+      c->err = "learned smoother training diverged (non-finite loss) at epoch " + std::to_string(ep) +
+               "; target max " + std::to_string(tmax) + ", non-finite targets " + std::to_string(hbad) +
+               ", output scale " + std::to_string(cs) + ", first loss " + std::to_string(loss_first);
       return SIPG_ENAN;
     }
   }
@@ -990,6 +1006,8 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
     info->loss_last = loss_last;
     info->out_scale = cs;
     info->cheb_rate = N.rho_cheb;
+    info->target_max = tmax;
+    info->nonfinite = (double)hbad;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return SIPG_OK;
@@ -1051,7 +1069,7 @@ sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_c
     if (M.deform && M.mapping_degree != 3) throw_inval("curved cells need mapping_degree 3");
     if (!(P.penalty_factor > 0)) throw_inval("penalty factor must be positive");
     if (P.precision != 0 && P.precision != 1) throw_inval("precision must be 0 or 1");
-    if (P.cheb_degree < 1 || P.eig_iters < 1 || P.p_coarsen != 0 || P.smoother != 0)
+    if (P.cheb_degree < 1 || P.eig_iters < 1 || P.p_coarsen < 0 || P.p_coarsen > 2 || P.smoother != 0)
       throw_inval("unsupported smoother parameters");
     for (int s = 0; s < 6; ++s)
       if (M.bc[s] != 0 && M.bc[s] != 1) throw_inval("bc must be 0 (Dirichlet) or 1 (Neumann)");

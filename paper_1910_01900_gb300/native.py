@@ -30,7 +30,8 @@ EXPORTS = [
 class TrainInfo(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int), ("epochs", ctypes.c_int), ("steps", ctypes.c_int),
                 ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("out_scale", ctypes.c_double),
-                ("cheb_rate", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("cheb_rate", ctypes.c_double), ("seconds", ctypes.c_double), ("target_max", ctypes.c_double),
+                ("nonfinite", ctypes.c_double)]
 
 
 class Mesh(ctypes.Structure):
@@ -147,13 +148,14 @@ def make_mesh(m, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(
 
 
 def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                operator_only=False, stream=None, autotune=False):
+                operator_only=False, stream=None, autotune=False, p_coarsen=0):
     prm = Params()
     lib().sipg_default_params(ctypes.byref(prm))
     prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
     prm.cheb_degree, prm.eig_iters = int(cheb_degree), int(eig_iters)
     prm.lambda_override, prm.operator_only = float(lambda_override), int(bool(operator_only))
     prm.autotune = int(bool(autotune))
+    prm.p_coarsen = int(p_coarsen)
     prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return prm
 
@@ -163,7 +165,7 @@ class Context:
 
     def __init__(self, m, degree, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
                  precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                 operator_only=False, stream=None, autotune=False, _handle=None):
+                 operator_only=False, stream=None, autotune=False, p_coarsen=0, _handle=None):
         L = lib()
         mesh, mm = make_mesh(m, deform, amp, lo, hi, bc)
         self.degree, self.precision = int(degree), int(precision)
@@ -174,7 +176,7 @@ class Context:
             self.h = _handle
             return
         prm = make_params(degree, precision, penalty_factor, cheb_degree, eig_iters, lambda_override,
-                          operator_only, stream, autotune)
+                          operator_only, stream, autotune, p_coarsen)
         h = ctypes.c_void_p()
         st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
         if st != OK:

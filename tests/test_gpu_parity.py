@@ -315,3 +315,20 @@ def test_l2_error_diagnostic_matches_oracle(m, k, deform):
     exact = lambda p: np.prod(np.sin(np.pi * p), axis=-1)  # noqa: E731
     ref = SIPG(Mesh(m, deform=deform), k).l2_error(x, exact)
     assert abs(e - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("rule,code", [("minus1", 1), ("one", 2)])
+def test_other_p_sequences_match_oracle(rule, code):
+    """p_{l-1} = p_l - 1 and p_{l-1} = 1 (Section 3.2): same levels, iterations and solution as the oracle."""
+    m, k = 4, 4
+    ctx = _ctx(m, k, p_coarsen=code)
+    mg = CPHMultigrid(Mesh(m), k, p_rule=rule)
+    assert ctx.num_levels == len(mg.levels)
+    b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+    ctx.rhs(b)
+    bo = b.cpu().numpy()
+    ref, it, _ = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
+    x = torch.zeros_like(b)
+    info = ctx.solve(b, x, rtol=1e-10)
+    assert info.iterations == it
+    assert rel(x.cpu().numpy(), ref) <= 1e-10

@@ -152,3 +152,23 @@ def test_cph_penalty_robustness(k):
         _, it, hist = fcg(fine.apply, b, np.zeros_like(b), mg.vcycle)
         n10.append(_n10(hist, it))
     assert abs(n10[1] - n10[0]) < 1.0, n10
+
+
+def test_dg_transfers_reproduce_coarse_polynomials():
+    from oracle.transfer import dg_transfer
+    mesh = Mesh((2, 2, 4))
+    f, c = SIPG(mesh, 4), SIPG(mesh, 2)
+    u = lambda x: 1 + x[..., 0] ** 2 - x[..., 1] * x[..., 2] ** 2  # noqa: E731  (degree <= 2 per direction)
+    P = dg_transfer(f, c)
+    assert np.max(np.abs(P @ c.interpolate(u) - f.interpolate(u))) < 1e-12
+    fh, ch = SIPG(Mesh(4), 2), SIPG(Mesh(2), 2)
+    assert np.max(np.abs(dg_transfer(fh, ch) @ ch.interpolate(u) - fh.interpolate(u))) < 1e-12
+
+
+@pytest.mark.parametrize("order", ["chp", "pch", "phc", "hpc"])
+def test_other_coarsening_orders_converge(order):
+    mg = CPHMultigrid(Mesh(6), 2, order=order)
+    fine = mg.levels[-1]
+    b = fine.space.rhs(lambda x: 3 * np.pi ** 2 * _exact(x))
+    _, it, hist = fcg(fine.apply, b, np.zeros_like(b), mg.vcycle)
+    assert hist[-1] <= 1e-10 * hist[0] and it <= 25
