@@ -84,6 +84,12 @@ typedef struct {
   int smoother;            /* 0: Chebyshev-Jacobi (Algorithm 3)               */
   int operator_only;       /* 1: build only the finest DG operator (for
                               operator_apply); the solver calls then fail   */
+  char coarsening[8];      /* order of the coarsening steps from the finest
+                              level (Section 3.2, Table SummaryCoarsening-
+                              Strategies): 'c' DG -> FE at equal h and p, 'p'
+                              polynomial levels down to 1, 'h' geometric
+                              levels; default "cph"; must contain 'c' and 'p'
+                              (the dense coarse solve works on FE_1)       */
   int autotune;            /* 1: at setup, time the compiled tile shapes
                               (cells per thread block) of both DG passes in
                               both precisions and keep the fastest; cached

@@ -12,6 +12,8 @@
 //
 // The same node pass, fed with a DG vector as the element buffer, is the
 // c-restriction (sum of the duplicated DG nodes, Section 3.2 c-coarsening).
+#include <algorithm>
+
 #include "sumfac.cuh"
 
 namespace sipg {
@@ -303,6 +305,88 @@ __global__ void fe_restrict_cells_kernel(const XferGeom G, const T *__restrict__
   for (int j = threadIdx.x; j < nc3; j += blockDim.x) ebuf[(size_t)cc * nc3 + j] = acc[j];
 }
 
+// Transfers between DG levels (p on one mesh, or 2:1 h): the spaces share no
+// nodes, so P is block diagonal over the fine cells with the parent's 1D
+// interpolation matrices (no multiplicity weights).  One thread block per
+// coarse cell and its fine cells (1 for p, 8 children for h), contracting
+// along x, y, z in shared memory.  PROLONG: x_f += P x_c; else r_c = P^T r_f.
+template <typename T, bool PROLONG>
+__global__ void dg_transfer_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ in,
+                                   T *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const int nf = G.pf + 1, nc = G.pc + 1;
+  const int nf3 = nf * nf * nf, nc3 = nc * nc * nc;
+  const int big = nf3 > nc3 ? nf3 : nc3;
+  T *A = sm, *B = A + big, *C = B + big, *acc = C + big;
+  const int cc = blockIdx.x;
+  const int cijk[3] = {cc % G.mc[0], (cc / G.mc[0]) % G.mc[1], cc / (G.mc[0] * G.mc[1])};
+  const int nch = G.kind == 4 ? 2 : 1;
+  if (!PROLONG)
+    for (int j = threadIdx.x; j < nc3; j += blockDim.x) acc[j] = T(0);
+  else
+    for (int j = threadIdx.x; j < nc3; j += blockDim.x) acc[j] = in[(size_t)cc * nc3 + j];
+  for (int ch = 0; ch < nch * nch * nch; ++ch) {
+    const int child[3] = {ch & (nch - 1), (ch / nch) & (nch - 1), ch / (nch * nch)};
+    int fijk[3];
+    for (int d = 0; d < 3; ++d) fijk[d] = G.kind == 4 ? 2 * cijk[d] + child[d] : cijk[d];
+    const size_t fcell = fijk[0] + (size_t)G.mf[0] * (fijk[1] + (size_t)G.mf[1] * fijk[2]);
+    const T *Px = P1 + (size_t)child[0] * nf * nc, *Py = P1 + (size_t)child[1] * nf * nc,
+            *Pz = P1 + (size_t)child[2] * nf * nc;
+    __syncthreads();
+    if (PROLONG) {
+      // B[jz][jy][ix] = sum_jx Px[ix][jx] acc[jz][jy][jx]; C[jz][iy][ix]; fine[iz][iy][ix]
+      for (int o = threadIdx.x; o < nc * nc * nf; o += blockDim.x) {
+        const int ix = o % nf, r = o / nf;
+        T s = T(0);
+        for (int jx = 0; jx < nc; ++jx) s += Px[ix * nc + jx] * acc[r * nc + jx];
+        B[o] = s;
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < nc * nf * nf; o += blockDim.x) {
+        const int ix = o % nf, iy = (o / nf) % nf, jz = o / (nf * nf);
+        T s = T(0);
+        for (int jy = 0; jy < nc; ++jy) s += Py[iy * nc + jy] * B[(jz * nc + jy) * nf + ix];
+        C[o] = s;
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < nf3; o += blockDim.x) {
+        const int ixy = o % (nf * nf), iz = o / (nf * nf);
+        T s = T(0);
+        for (int jz = 0; jz < nc; ++jz) s += Pz[iz * nc + jz] * C[jz * nf * nf + ixy];
+        out[fcell * nf3 + o] += s;
+      }
+    } else {
+      for (int i = threadIdx.x; i < nf3; i += blockDim.x) A[i] = in[fcell * nf3 + i];
+      __syncthreads();
+      for (int o = threadIdx.x; o < nf * nf * nc; o += blockDim.x) {   // B[iz][iy][jx]
+        const int jx = o % nc, r = o / nc;
+        T s = T(0);
+        for (int ix = 0; ix < nf; ++ix) s += Px[ix * nc + jx] * A[r * nf + ix];
+        B[o] = s;
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < nf * nc * nc; o += blockDim.x) {   // C[iz][jy][jx]
+        const int jx = o % nc, jy = (o / nc) % nc, iz = o / (nc * nc);
+        T s = T(0);
+        for (int iy = 0; iy < nf; ++iy) s += Py[iy * nc + jy] * B[(iz * nf + iy) * nc + jx];
+        C[o] = s;
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < nc3; o += blockDim.x) {
+        const int jxy = o % (nc * nc), jz = o / (nc * nc);
+        T s = T(0);
+        for (int iz = 0; iz < nf; ++iz) s += Pz[iz * nc + jz] * C[iz * nc * nc + jxy];
+        acc[o] += s;
+      }
+    }
+  }
+  if (!PROLONG) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc3; j += blockDim.x) out[(size_t)cc * nc3 + j] = acc[j];
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename T, int N, bool CURVED>
 static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s) {
@@ -417,6 +501,21 @@ cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_dg_transfer(const XferGeom &g, const T *P1, const T *in, T *out, bool prolong, cudaStream_t s) {
+  const int nf = g.pf + 1, nc = g.pc + 1;
+  const int big = std::max(nf * nf * nf, nc * nc * nc);
+  const size_t smem = (size_t)(3 * big + nc * nc * nc) * sizeof(T);
+  const long ncc = (long)g.mc[0] * g.mc[1] * g.mc[2];
+  if (ncc == 0) return cudaSuccess;
+  if (prolong)
+    dg_transfer_kernel<T, true><<<(int)ncc, 128, smem, s>>>(g, P1, in, out);
+  else
+    dg_transfer_kernel<T, false><<<(int)ncc, 128, smem, s>>>(g, P1, in, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 #define SIPG_FE_INST(T)                                                                                   \
   template cudaError_t launch_fe_cells<T>(int, bool, const FEArgs<T> &, bool, cudaStream_t);            \
   template cudaError_t launch_fe_gather<T>(const FEArgs<T> &, cudaStream_t);                            \
@@ -424,7 +523,8 @@ cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf
   template cudaError_t launch_fe_prolongate_add<T>(const XferGeom &, const T *, const T *, T *,         \
                                                    cudaStream_t);                                       \
   template cudaError_t launch_fe_restrict_cells<T>(const XferGeom &, const T *, const T *, T *,         \
-                                                   cudaStream_t);
+                                                   cudaStream_t);                                       \
+  template cudaError_t launch_dg_transfer<T>(const XferGeom &, const T *, const T *, T *, bool, cudaStream_t);
 SIPG_FE_INST(double)
 SIPG_FE_INST(float)
 

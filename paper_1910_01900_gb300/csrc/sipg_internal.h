@@ -107,7 +107,7 @@ struct Level {
   void *dinv[2] = {nullptr, nullptr};
   double lambda = 0;
   // transfer from level l-1 (coarser) to this level
-  int t_kind = -1;      // 0 c-transfer, 1 p-transfer, 2 h-transfer
+  int t_kind = -1;      // 0 c-transfer, 1 FE p, 2 FE h, 3 DG p, 4 DG h
   void *P1[2] = {nullptr, nullptr};   // [2 children][nf][nc] interpolation tables
   // V-cycle work vectors in the V-cycle precision (and FP64 for setup)
   void *vb[2] = {nullptr, nullptr}, *vx[2] = {nullptr, nullptr}, *vr[2] = {nullptr, nullptr},
@@ -141,7 +141,7 @@ cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_c_prolongate_add(const FEArgs<T> &fe, const T *xc, T *xdg, cudaStream_t s);
 struct XferGeom {
-  int kind;             // 1 p, 2 h
+  int kind;             // 1 FE p, 2 FE h, 3 DG p, 4 DG h
   int mf[3], mc[3];     // cells of fine and coarse mesh
   int pf, pc;           // degrees
   int gf[3], gc[3];     // node grids
@@ -151,6 +151,9 @@ template <typename T>
 cudaError_t launch_fe_prolongate_add(const XferGeom &g, const T *P1, const T *xc, T *xf, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf, T *ebuf_c, cudaStream_t s);
+// DG -> DG transfers (kind 3 p, 4 h): prolong: out += P in; else out = P^T in
+template <typename T>
+cudaError_t launch_dg_transfer(const XferGeom &g, const T *P1, const T *in, T *out, bool prolong, cudaStream_t s);
 
 // Vector kernels.
 template <typename T>

@@ -229,6 +229,10 @@ template <typename T>
 void restrict_level(sipg_ctx *c, int l, const T *r, T *rc) {
   constexpr int pi = pidx<T>();
   const Level &F = c->lv[l];
+  if (F.t_kind >= 3) {   // DG -> DG: cell-local transpose
+    CK(launch_dg_transfer<T>(xfer(c, l), (const T *)F.P1[pi], r, rc, false, c->stream));
+    return;
+  }
   FEArgs<T> a = fe_args<T>(c, c->lv[l - 1]);
   a.mode = 3;
   a.out = rc;
@@ -245,7 +249,9 @@ template <typename T>
 void prolongate_level(sipg_ctx *c, int l, const T *xc, T *x) {
   constexpr int pi = pidx<T>();
   const Level &F = c->lv[l];
-  if (F.t_kind == 0) {
+  if (F.t_kind >= 3) {
+    CK(launch_dg_transfer<T>(xfer(c, l), (const T *)F.P1[pi], xc, x, true, c->stream));
+  } else if (F.t_kind == 0) {
     FEArgs<T> a = fe_args<T>(c, c->lv[l - 1]);
     CK(launch_c_prolongate_add<T>(a, xc, x, c->stream));
   } else {
@@ -382,6 +388,7 @@ double estimate_lambda(sipg_ctx *c, int l) {
   std::vector<double> r0(n);
   for (int64_t i = 0; i < n; ++i) r0[i] = uniform_pm1(1910, (uint64_t)i);
   double *r = (double *)L.vb[0], *z = (double *)L.vx[0], *p = (double *)L.vr[0], *Ap = (double *)L.vt[0];
+  CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(r, r0.data(), n * sizeof(double), cudaMemcpyHostToDevice));
   if (L.kind == 1) {   // the start vector is zero on constrained FE nodes
     std::vector<double> h(n);
@@ -568,27 +575,43 @@ void setup(sipg_ctx *c) {
     int t_kind;   // transfer to the next coarser level
   };
   std::vector<Spec> specs;
-  specs.push_back({0, P.degree, md, 0});
+  specs.push_back({0, P.degree, md, -1});
   if (c->solver) {
-    int p = P.degree;
-    specs.push_back({1, p, md, -1});
-    while (p > 1) {   // p-sequence: floor(p/2) (default), p-1, or straight to 1 (Section 3.2)
-      specs.back().t_kind = 1;
-      p = P.p_coarsen == 0 ? std::max(1, p / 2) : (P.p_coarsen == 1 ? p - 1 : 1);
-      specs.push_back({1, p, md, -1});
-    }
+    // coarsening steps in the order of params.coarsening (Section 3.2): 'c' DG -> FE
+    // at equal h and p, 'p' all polynomial levels down to 1, 'h' all geometric
+    // levels (halve while every m is even and m/2 >= 3); the coarsest level is FE
+    int kind = 0, p = P.degree;
     MeshDesc cm = md;
-    while (cm.m[0] % 2 == 0 && cm.m[1] % 2 == 0 && cm.m[2] % 2 == 0 && cm.m[0] / 2 >= 3 && cm.m[1] / 2 >= 3 &&
-           cm.m[2] / 2 >= 3) {
-      for (int d = 0; d < 3; ++d) cm.m[d] /= 2;
-      specs.back().t_kind = 2;
-      specs.push_back({1, 1, cm, -1});
+    for (const char *o = P.coarsening; *o; ++o) {
+      if (*o == 'c') {
+        if (kind == 1) throw_inval("coarsening: 'c' twice");
+        specs.back().t_kind = 0;
+        kind = 1;
+        specs.push_back({1, p, cm, -1});
+      } else if (*o == 'p') {
+        while (p > 1) {   // floor(p/2) (default), p-1, or straight to 1
+          specs.back().t_kind = kind ? 1 : 3;
+          p = P.p_coarsen == 0 ? std::max(1, p / 2) : (P.p_coarsen == 1 ? p - 1 : 1);
+          specs.push_back({kind, p, cm, -1});
+        }
+      } else if (*o == 'h') {
+        while (cm.m[0] % 2 == 0 && cm.m[1] % 2 == 0 && cm.m[2] % 2 == 0 && cm.m[0] / 2 >= 3 &&
+               cm.m[1] / 2 >= 3 && cm.m[2] / 2 >= 3) {
+          for (int d = 0; d < 3; ++d) cm.m[d] /= 2;
+          specs.back().t_kind = kind ? 2 : 4;
+          specs.push_back({kind, p, cm, -1});
+        }
+      } else {
+        throw_inval("coarsening letters are c, p and h");
+      }
     }
+    if (kind != 1) throw_inval("coarsening must contain 'c' (the coarse solve works on an FE level)");
+    if (p != 1) throw_inval("coarsening must contain 'p' (the coarse matrix is assembled for degree 1)");
   }
   const int nl = (int)specs.size();
   c->lv.assign(nl, Level());
   c->L = nl - 1;
-  int64_t ebuf_len = 0;
+  int64_t ebuf_len = 0, dg_grad_len = 0, dg_trace_len = 0;
   for (int i = 0; i < nl; ++i) {
     const Spec &s = specs[i];
     Level &L = c->lv[nl - 1 - i];
@@ -605,6 +628,10 @@ void setup(sipg_ctx *c) {
     L.ndofs = s.kind == 0 ? L.ncells * n3 : (int64_t)L.grid[0] * L.grid[1] * L.grid[2];
     build_level_geometry(c, L, s.md, s.kind == 0);
     if (s.kind == 1) ebuf_len = std::max(ebuf_len, L.ncells * n3);
+    if (s.kind == 0) {
+      dg_grad_len = std::max(dg_grad_len, L.ncells * 3 * n3);
+      dg_trace_len = std::max(dg_trace_len, L.ncells * 12 * (int64_t)L.n * L.n);
+    }
     if (c->solver) alloc_work(c, L);
   }
   // transfer tables: level l (fine) from l-1 (coarse)
@@ -616,26 +643,24 @@ void setup(sipg_ctx *c) {
     const Level &C = c->lv[l - 1];
     const int nf = F.n, nc = C.n;
     const Rules1D &rf = rules(nf), &rc = rules(nc);
-    const int nch = F.t_kind == 2 ? 2 : 1;
+    const bool hk = F.t_kind == 2 || F.t_kind == 4;
+    const int nch = hk ? 2 : 1;
     std::vector<double> P1((size_t)nch * nf * nc);
     for (int ch = 0; ch < nch; ++ch)
       for (int i = 0; i < nf; ++i) {
-        const double x = F.t_kind == 2 ? 0.5 * (ch + rf.gl[i]) : rf.gl[i];
+        const double x = hk ? 0.5 * (ch + rf.gl[i]) : rf.gl[i];
         const auto v = lagrange_values(rc.gl, x);
         for (int j = 0; j < nc; ++j) P1[((size_t)ch * nf + i) * nc + j] = v[j];
       }
     upload2(c, P1, F.P1);
     ebuf_len = std::max(ebuf_len, C.ncells * (int64_t)nc * nc * nc);
   }
-  // DG scratch (both precisions)
-  {
-    const Level &F = c->lv[c->L];
-    const int64_t n3 = (int64_t)F.n * F.n * F.n, n2 = (int64_t)F.n * F.n;
-    c->dg_grad[0] = dalloc<double>(c, F.ncells * 3 * n3);
-    c->dg_trace[0] = dalloc<double>(c, F.ncells * 12 * n2);
-    c->dg_grad[1] = dalloc<float>(c, F.ncells * 3 * n3);
-    c->dg_trace[1] = dalloc<float>(c, F.ncells * 12 * n2);
-  }
+  // DG scratch (both precisions), shared by all DG levels (used one at a time)
+  c->dg_grad[0] = dalloc<double>(c, dg_grad_len);
+  c->dg_trace[0] = dalloc<double>(c, dg_trace_len);
+  c->dg_grad[1] = dalloc<float>(c, dg_grad_len);
+  c->dg_trace[1] = dalloc<float>(c, dg_trace_len);
+  CK(cudaDeviceSynchronize());   // geometry uploads (legacy stream) complete before stream work
   if (P.autotune) {
     for (int pass = 0; pass < 2; ++pass) {
       autotune_pass<double>(c, pass);
@@ -826,8 +851,9 @@ void net_setup(sipg_ctx *c, long rows) {
     fill(N.oW1, N.Fp, N.F, N.H, 4001);
     fill(N.oW2, N.H, N.H, N.H, 4002);
     fill(N.oW3, N.H, N.H, N.No, 4003);
-    CK(cudaMemcpy(N.P, h.data(), N.np * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(N.P, h.data(), N.np * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CK(mlp_f2bf(N.P, N.Pb, N.np, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     N.ready = true;
   }
   if (rows > N.rows) {
@@ -916,7 +942,10 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
          *r = dalloc<double>(c, Nd), *e = dalloc<double>(c, Nd);
   std::vector<int> hc(R);
   for (long i = 0; i < R; ++i) hc[i] = (int)(splitmix64(seed ^ (0x5151ull + (uint64_t)i)) % (uint64_t)E);
-  CK(cudaMemcpy(cells, hc.data(), R * sizeof(int), cudaMemcpyHostToDevice));
+  // every copy below is ordered on the context stream (which may be a
+  // non-blocking stream that the legacy default stream does not wait for)
+  CK(cudaMemcpyAsync(cells, hc.data(), R * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   std::vector<double> hb(Nd);
   double rho_sum = 0;
   int rho_cnt = 0;
@@ -925,7 +954,8 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   long row = 0;
   for (int sidx = 0; sidx < S; ++sidx) {
     for (int64_t i = 0; i < Nd; ++i) hb[i] = uniform_pm1(seed + 1 + sidx, (uint64_t)i);
-    CK(cudaMemcpy(b, hb.data(), Nd * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaStreamSynchronize(c->stream));   // the previous right-hand side is no longer read
+    CK(cudaMemcpyAsync(b, hb.data(), Nd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(xs, 0, Nd * sizeof(double), c->stream));
     sipg_solve_info inf{};
     const sipg_status st = solve_impl(c, b, xs, 1e-12, 500, 0, &inf);
@@ -957,15 +987,17 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   CK(mlp_stats(Tall, R * N.No, mx, bad, c->stream));
   unsigned long long hbad = 0;
   unsigned hmx = 0;
-  CK(cudaMemcpy(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   float tmax;
   std::memcpy(&tmax, &hmx, sizeof(tmax));
   // output scale: RMS of the targets
   CK(cudaMemsetAsync(N.loss, 0, 2 * sizeof(double), c->stream));
   CK(mlp_sumsq(Tall, R * N.No, N.loss, c->stream));
   double ss;
-  CK(cudaMemcpy(&ss, N.loss, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&ss, N.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   const double cs = std::sqrt(ss / ((double)R * N.n3)) + 1e-300;
   N.cscale = (float)cs;
   CK(mlp_scale(Tall, R * N.No, (float)(1.0 / cs), c->stream));
@@ -983,7 +1015,8 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
       CK(mlp_adam(N.P, N.M, N.V, N.G, N.np, lr, step, N.Pb, c->stream));
     }
     double l;
-    CK(cudaMemcpy(&l, N.loss, sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(&l, N.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     l /= NB;
     if (ep == 0) loss_first = l;
     loss_last = l;
@@ -1050,6 +1083,7 @@ void sipg_default_params(sipg_params *p) {
   p->lambda_override = 0.0;
   p->smoother = 0;
   p->operator_only = 0;
+  std::strcpy(p->coarsening, "cph");
   p->stream = nullptr;
 }
 
@@ -1363,12 +1397,12 @@ sipg_status sipg_mlp_params(sipg_ctx *c, int set, float *host) {
     net_setup(c, 256);
     auto &N = c->net;
     if (set) {
-      CK(cudaMemcpy(N.P, host, N.np * sizeof(float), cudaMemcpyHostToDevice));
+      CK(cudaMemcpyAsync(N.P, host, N.np * sizeof(float), cudaMemcpyHostToDevice, c->stream));
       CK(mlp_f2bf(N.P, N.Pb, N.np, c->stream));
-      CK(cudaStreamSynchronize(c->stream));
     } else {
-      CK(cudaMemcpy(host, N.P, N.np * sizeof(float), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpyAsync(host, N.P, N.np * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     }
+    CK(cudaStreamSynchronize(c->stream));
     return SIPG_OK;
   });
 }

@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("penalty_factor", ctypes.c_double), ("precision", ctypes.c_int),
                 ("p_coarsen", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("lambda_override", ctypes.c_double),
-                ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("coarsening", ctypes.c_char * 8),
+                ("autotune", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -148,7 +149,7 @@ def make_mesh(m, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(
 
 
 def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                operator_only=False, stream=None, autotune=False, p_coarsen=0):
+                operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph"):
     prm = Params()
     lib().sipg_default_params(ctypes.byref(prm))
     prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
@@ -156,6 +157,7 @@ def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iter
     prm.lambda_override, prm.operator_only = float(lambda_override), int(bool(operator_only))
     prm.autotune = int(bool(autotune))
     prm.p_coarsen = int(p_coarsen)
+    prm.coarsening = coarsening.encode()
     prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return prm
 
@@ -165,7 +167,7 @@ class Context:
 
     def __init__(self, m, degree, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
                  precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                 operator_only=False, stream=None, autotune=False, p_coarsen=0, _handle=None):
+                 operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", _handle=None):
         L = lib()
         mesh, mm = make_mesh(m, deform, amp, lo, hi, bc)
         self.degree, self.precision = int(degree), int(precision)
@@ -176,7 +178,7 @@ class Context:
             self.h = _handle
             return
         prm = make_params(degree, precision, penalty_factor, cheb_degree, eig_iters, lambda_override,
-                          operator_only, stream, autotune, p_coarsen)
+                          operator_only, stream, autotune, p_coarsen, coarsening)
         h = ctypes.c_void_p()
         st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
         if st != OK:

@@ -332,3 +332,29 @@ def test_other_p_sequences_match_oracle(rule, code):
     info = ctx.solve(b, x, rtol=1e-10)
     assert info.iterations == it
     assert rel(x.cpu().numpy(), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("order,m,k", [("chp", 6, 2), ("pch", 6, 3), ("phc", 6, 2), ("hpc", 6, 2), ("cp", 4, 3),
+                                       ("pc", 4, 4)])
+def test_other_coarsening_orders_match_oracle(order, m, k):
+    """Orders of Table SummaryCoarseningStrategies that end on FE_1: levels, iterations, solution."""
+    ctx = _ctx(m, k, coarsening=order)
+    mg = CPHMultigrid(Mesh(m), k, order=order)
+    assert ctx.num_levels == len(mg.levels)
+    for l, lev in enumerate(mg.levels):
+        kind, deg, mm = ctx.level_info(l)
+        assert (kind == 0) == (lev.kind == "dg") and deg == lev.space.n - 1 and ctx.num_dofs(l) == lev.n
+    b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+    ctx.rhs(b)
+    bo = b.cpu().numpy()
+    ref, it, _ = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
+    x = torch.zeros_like(b)
+    info = ctx.solve(b, x, rtol=1e-10)
+    assert info.iterations == it
+    assert rel(x.cpu().numpy(), ref) <= 1e-10
+
+
+def test_coarsening_without_c_is_rejected():
+    from paper_1910_01900_gb300 import SipgError
+    with pytest.raises(SipgError):
+        _ctx(4, 2, coarsening="ph")
