@@ -36,16 +36,16 @@ namespace sipg {
 // shared memory at sm.  Shared by the per-problem and the batched kernels.
 template <typename T, int N, bool CURVED>
 __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0, const int ncta, T *sm) {
-  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const bool act = cl < ncta;
-  T *su = sm + cl * 4 * N3;
+  T *su = sm + cl * 4 * TT;
 
   const T *ug = a.u + (size_t)cell0 * N3;
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3;
-    sm[c * 4 * N3 + (i - c * N3)] = ug[i];
+    sm[c * 4 * TT + Tile<N>::idx(i - c * N3)] = ug[i];
   }
   __syncthreads();
 #pragma unroll 1
@@ -61,15 +61,15 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
       T x[N], y[N];
       load_line<T, N>(su, base, stride, x);
       apply_mat<T, N, MD>(x, y);
-      store_line<T, N>(su + (1 + d) * N3, base, stride, y);
+      store_line<T, N>(su + (1 + d) * TT, base, stride, y);
     }
   }
   __syncthreads();
   if (!a.recompute) {
     T *gg = a.grad + (size_t)cell0 * 3 * N3;
     for (int i = tid; i < ncta * 3 * N3; i += NT) {
-      const int c = i / (3 * N3);
-      gg[i] = sm[c * 4 * N3 + N3 + (i - c * 3 * N3)];
+      const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
+      gg[i] = sm[c * 4 * TT + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)];
     }
   }
   if (!act) return;
@@ -91,7 +91,7 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
     T q0, q1;
     if constexpr (!CURVED) {
       T g[N];
-      load_line<T, N>(su + (1 + d) * N3, base, stride, g);
+      load_line<T, N>(su + (1 + d) * TT, base, stride, g);
       T g0 = t.l0[N][0] * g[0], g1 = t.l1[N][0] * g[0];
 #pragma unroll
       for (int q = 1; q < N; ++q) {
@@ -105,7 +105,7 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         T g[N];
-        load_line<T, N>(su + (1 + b) * N3, base, stride, g);
+        load_line<T, N>(su + (1 + b) * TT, base, stride, g);
         T g0 = t.l0[N][0] * g[0], g1 = t.l1[N][0] * g[0];
 #pragma unroll
         for (int q = 1; q < N; ++q) {
@@ -135,12 +135,12 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
 // Integration pass (same thread and shared-memory contract as the evaluation).
 template <typename T, int N, bool CURVED>
 __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int cell0, const int ncta, T *sm) {
-  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const bool act = cl < ncta;
-  T *st = sm + cl * 4 * N3;   // value accumulator, then the integrated tile
-  T *sg = st + N3;            // three gradient components
+  T *st = sm + cl * 4 * TT;   // value accumulator, then the integrated tile
+  T *sg = st + TT;            // three gradient components
 
   if (a.recompute) {
     // gradient at the Gauss points again from u: 3 interpolation and 3
@@ -148,7 +148,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
     const T *ug = a.u + (size_t)cell0 * N3;
     for (int i = tid; i < ncta * N3; i += NT) {
       const int c = i / N3;
-      sm[c * 4 * N3 + (i - c * N3)] = ug[i];
+      sm[c * 4 * TT + Tile<N>::idx(i - c * N3)] = ug[i];
     }
     __syncthreads();
 #pragma unroll 1
@@ -164,31 +164,31 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
         T x[N], y[N];
         load_line<T, N>(st, base, stride, x);
         apply_mat<T, N, MD>(x, y);
-        store_line<T, N>(sg + d * N3, base, stride, y);
+        store_line<T, N>(sg + d * TT, base, stride, y);
       }
     }
   } else {
     const T *gg = a.grad + (size_t)cell0 * 3 * N3;
     for (int i = tid; i < ncta * 3 * N3; i += NT) {
-      const int c = i / (3 * N3);
-      sm[c * 4 * N3 + N3 + (i - c * 3 * N3)] = gg[i];
+      const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
+      sm[c * 4 * TT + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)] = gg[i];
     }
   }
   __syncthreads();
   for (int i = tid; i < ncta * N3; i += NT) {
-    const int c = i / N3, p = i - c * N3;
-    T *s = sm + c * 4 * N3 + N3;
-    const T g0 = s[p], g1 = s[N3 + p], g2 = s[2 * N3 + p];
+    const int c = i / N3, p = i - c * N3, tp = Tile<N>::idx(p);
+    T *s = sm + c * 4 * TT + TT + tp;
+    const T g0 = s[0], g1 = s[TT], g2 = s[2 * TT];
     if constexpr (!CURVED) {
-      s[p] = g0 * a.wcart[p];
-      s[N3 + p] = g1 * a.wcart[N3 + p];
-      s[2 * N3 + p] = g2 * a.wcart[2 * N3 + p];
+      s[0] = g0 * a.wcart[p];
+      s[TT] = g1 * a.wcart[N3 + p];
+      s[2 * TT] = g2 * a.wcart[2 * N3 + p];
     } else {
       const T *M = a.metric + (size_t)(cell0 + c) * 6 * N3 + p;
       const T xx = M[0], yy = M[N3], zz = M[2 * N3], xy = M[3 * N3], xz = M[4 * N3], yz = M[5 * N3];
-      s[p] = xx * g0 + xy * g1 + xz * g2;
-      s[N3 + p] = xy * g0 + yy * g1 + yz * g2;
-      s[2 * N3 + p] = xz * g0 + yz * g1 + zz * g2;
+      s[0] = xx * g0 + xy * g1 + xz * g2;
+      s[TT] = xy * g0 + yy * g1 + yz * g2;
+      s[2 * TT] = xz * g0 + yz * g1 + zz * g2;
     }
   }
   __syncthreads();
@@ -260,7 +260,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
       }
       if constexpr (!CURVED) {
         const T b0 = -a.ih[d] * B[0], b1 = a.ih[d] * B[1];
-        T *g = sg + d * N3;
+        T *g = sg + d * TT;
 #pragma unroll
         for (int q = 0; q < N; ++q) {
           T *p = g + base + q * stride;
@@ -270,7 +270,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) {
           const T b0 = cvec[0][bb] * B[0], b1 = cvec[1][bb] * B[1];
-          T *g = sg + bb * N3;
+          T *g = sg + bb * TT;
 #pragma unroll
           for (int q = 0; q < N; ++q) {
             T *p = g + base + q * stride;
@@ -287,7 +287,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
       int base, stride;
       line_of<N>(d, l, base, stride);
       T x[N], y[N];
-      load_line<T, N>(sg + d * N3, base, stride, x);
+      load_line<T, N>(sg + d * TT, base, stride, x);
       apply_mat<T, N, MDt>(x, y);
 #pragma unroll
       for (int q = 0; q < N; ++q) st[base + q * stride] += y[q];
@@ -301,7 +301,11 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
   }
   if (!act) return;
   T x[N], y[N];
-  load_line<T, N>(st, l, N2, x);
+  {
+    int base, stride;
+    line_of<N>(2, l, base, stride);
+    load_line<T, N>(st, base, stride, x);
+  }
   apply_mat<T, N, MSt>(x, y);
   const size_t g0 = (size_t)cell * N3 + l;
   if (a.mode == 0) {

@@ -7,8 +7,7 @@ namespace sipg {
 
 template <typename T, int N, bool CURVED, int CB>
 static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s) {
-  constexpr int N3 = N * N * N;
-  const size_t smem = (size_t)CB * 4 * N3 * sizeof(T);
+  const size_t smem = (size_t)CB * 4 * Tile<N>::T3 * sizeof(T);
   const int grid = (a.ncells + CB - 1) / CB;
   if (grid == 0) return cudaSuccess;
   if (integrate)
@@ -23,7 +22,7 @@ static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s) {
 // device, before any launch or stream capture).
 template <typename T, int N, bool CURVED, int CB>
 static cudaError_t prep_dg() {
-  const int smem = CB * 4 * N * N * N * (int)sizeof(T);
+  const int smem = CB * 4 * Tile<N>::T3 * (int)sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(dg_integrate_kernel<T, N, CURVED, CB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -31,21 +31,21 @@ __device__ __forceinline__ bool node_constrained(const int g[3], const int grid[
 
 template <typename T, int N, bool CURVED, int CB>
 __global__ void __launch_bounds__(CB *N *N) fe_cell_kernel(const FEArgs<T> a) {
-  constexpr int N2 = N * N, N3 = N2 * N, NT = CB * N2;
+  constexpr int N2 = N * N, N3 = N2 * N, NT = CB * N2, TT = Tile<N>::T3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const int cell0 = blockIdx.x * CB;
   const int ncta = min(CB, a.ncells - cell0);
   const bool act = cl < ncta;
-  T *su = sm + cl * 4 * N3;
+  T *su = sm + cl * 4 * TT;
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3, p = i - c * N3;
     const int cell = cell0 + c;
     const int g[3] = {(cell % a.m[0]) * a.deg + p % N, ((cell / a.m[0]) % a.m[1]) * a.deg + (p / N) % N,
                       (cell / (a.m[0] * a.m[1])) * a.deg + p / N2};
     const size_t gi = g[0] + (size_t)a.grid[0] * (g[1] + (size_t)a.grid[1] * g[2]);
-    sm[c * 4 * N3 + p] = node_constrained(g, a.grid, a.bc) ? T(0) : a.u[gi];
+    sm[c * 4 * TT + Tile<N>::idx(p)] = node_constrained(g, a.grid, a.bc) ? T(0) : a.u[gi];
   }
   __syncthreads();
 #pragma unroll 1
@@ -61,24 +61,24 @@ __global__ void __launch_bounds__(CB *N *N) fe_cell_kernel(const FEArgs<T> a) {
       T x[N], y[N];
       load_line<T, N>(su, base, stride, x);
       apply_mat<T, N, MD>(x, y);
-      store_line<T, N>(su + (1 + d) * N3, base, stride, y);
+      store_line<T, N>(su + (1 + d) * TT, base, stride, y);
     }
   }
   __syncthreads();
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3, p = i - c * N3;
-    T *s = sm + c * 4 * N3 + N3;
-    const T g0 = s[p], g1 = s[N3 + p], g2 = s[2 * N3 + p];
+    T *s = sm + c * 4 * TT + TT + Tile<N>::idx(p);
+    const T g0 = s[0], g1 = s[TT], g2 = s[2 * TT];
     if constexpr (!CURVED) {
-      s[p] = g0 * a.wcart[p];
-      s[N3 + p] = g1 * a.wcart[N3 + p];
-      s[2 * N3 + p] = g2 * a.wcart[2 * N3 + p];
+      s[0] = g0 * a.wcart[p];
+      s[TT] = g1 * a.wcart[N3 + p];
+      s[2 * TT] = g2 * a.wcart[2 * N3 + p];
     } else {
       const T *M = a.metric + (size_t)(cell0 + c) * 6 * N3 + p;
       const T xx = M[0], yy = M[N3], zz = M[2 * N3], xy = M[3 * N3], xz = M[4 * N3], yz = M[5 * N3];
-      s[p] = xx * g0 + xy * g1 + xz * g2;
-      s[N3 + p] = xy * g0 + yy * g1 + yz * g2;
-      s[2 * N3 + p] = xz * g0 + yz * g1 + zz * g2;
+      s[0] = xx * g0 + xy * g1 + xz * g2;
+      s[TT] = xy * g0 + yy * g1 + yz * g2;
+      s[2 * TT] = xz * g0 + yz * g1 + zz * g2;
     }
   }
   __syncthreads();
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(CB *N *N) fe_cell_kernel(const FEArgs<T> a) {
       int base, stride;
       line_of<N>(d, l, base, stride);
       T x[N], y[N];
-      load_line<T, N>(su + (1 + d) * N3, base, stride, x);
+      load_line<T, N>(su + (1 + d) * TT, base, stride, x);
       apply_mat<T, N, MDt>(x, y);
       if (d == 0) {
         store_line<T, N>(su, base, stride, y);
@@ -106,7 +106,11 @@ __global__ void __launch_bounds__(CB *N *N) fe_cell_kernel(const FEArgs<T> a) {
   }
   if (!act) return;
   T x[N], y[N];
-  load_line<T, N>(su, l, N2, x);
+  {
+    int base, stride;
+    line_of<N>(2, l, base, stride);
+    load_line<T, N>(su, base, stride, x);
+  }
   apply_mat<T, N, MSt>(x, y);
   T *eb = a.ebuf + (size_t)(cell0 + cl) * N3 + l;
 #pragma unroll
@@ -390,8 +394,8 @@ __global__ void dg_transfer_kernel(const XferGeom G, const T *__restrict__ P1, c
 // ---------------------------------------------------------------- launchers
 template <typename T, int N, bool CURVED>
 static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s) {
-  constexpr int CB = default_cb(N), N3 = N * N * N;
-  const size_t smem = (size_t)CB * 4 * N3 * sizeof(T);
+  constexpr int CB = default_cb(N);
+  const size_t smem = (size_t)CB * 4 * Tile<N>::T3 * sizeof(T);
   const int grid = (a.ncells + CB - 1) / CB;
   if (grid == 0) return cudaSuccess;
   fe_cell_kernel<T, N, CURVED, CB><<<grid, CB * N * N, smem, s>>>(a);
@@ -402,7 +406,7 @@ static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s) {
 template <typename T, int N>
 static cudaError_t prep_fe_n() {
   constexpr int CB = default_cb(N);
-  const int smem = CB * 4 * N * N * N * (int)sizeof(T);
+  const int smem = CB * 4 * Tile<N>::T3 * (int)sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(fe_cell_kernel<T, N, false, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(fe_cell_kernel<T, N, true, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

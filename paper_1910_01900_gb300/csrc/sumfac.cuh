@@ -97,21 +97,33 @@ __device__ __forceinline__ void apply_mat(const T (&x)[N], T (&y)[N]) {
   if constexpr (M == MDt) mv<T, N, -1>(t.Dt[N], t.DtE[N], t.DtO[N], x, y);
 }
 
-// Offset and stride of line l (0 <= l < N^2) along direction d in an N^3 tile.
+// Shared-memory tile of N^3 values, x fastest, with the x pitch padded to an
+// odd number for even N: a warp walking lines along x then hits distinct
+// banks (an even pitch like 8 puts 4-8 threads on one bank).
+template <int N>
+struct Tile {
+  static constexpr int XP = (N % 2 == 0) ? N + 1 : N;   // pitch of a y step
+  static constexpr int T3 = XP * N * N;                  // values per tile array
+  // tile position of the node or point with linear index p = x + N (y + N z)
+  static __device__ __forceinline__ int idx(int p) { return XP == N ? p : p + p / N; }
+};
+
+// Offset and stride of line l (0 <= l < N^2) along direction d in a tile.
 // The line index l = a + N*b runs over the two other directions in increasing
 // order, so it equals the face-point index of the faces normal to d.
 template <int N>
 __device__ __forceinline__ void line_of(int d, int l, int &base, int &stride) {
+  constexpr int XP = Tile<N>::XP;
   const int a = l % N, b = l / N;
   if (d == 0) {
-    base = a * N + b * N * N;
+    base = XP * (a + N * b);
     stride = 1;
   } else if (d == 1) {
-    base = a + b * N * N;
-    stride = N;
+    base = a + XP * N * b;
+    stride = XP;
   } else {
-    base = a + b * N;
-    stride = N * N;
+    base = a + XP * b;
+    stride = XP * N;
   }
 }
 
@@ -136,6 +148,9 @@ __device__ __forceinline__ void sweep_inplace(T *s, int d, int l) {
   apply_mat<T, N, M>(x, y);
   store_line<T, N>(s, base, stride, y);
 }
+
+// Values of one padded tile array for n points per direction (host and device).
+__host__ __device__ constexpr int tile_values(int n) { return ((n % 2 == 0) ? n + 1 : n) * n * n; }
 
 // Cells per thread block for a tile size n (about 256 threads, n^2 threads per cell).
 __host__ __device__ constexpr int default_cb(int n) {
