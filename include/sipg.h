@@ -243,10 +243,13 @@ typedef struct {
   double target_max;              /* largest |e|/s of the data (before scaling)  */
   double nonfinite;               /* number of non-finite targets (0 expected)   */
 } sipg_train_info;
-/* Generates npairs (cell residual -> cell error) pairs from the plain cycle:
- * 4 seeded uniform right-hand sides, each solved to 1e-12, and the first 4
- * flexible-CG iterates of each (r = b - A x_j, e = x* - x_j) at seeded
- * random cells; then trains the network with Adam (batches of 256). */
+/* Generates npairs (cell residual -> cell error) pairs from the plain cycle
+ * and trains the network with Adam (batches of 256).  For the first 4
+ * flexible-CG iterates of 4 seeded uniform right-hand sides, the cycle's input
+ * b_v = r_j and its exact correction x* = A^-1 b_v (solved to 1e-12) give
+ * pairs at seeded random cells of two kinds: before smoothing (b_v, x*) and
+ * after pre-smoothing and the coarse-grid correction (b_v - A x, x* - x),
+ * the state a post-smoother works on. */
 sipg_status sipg_smoother_train(sipg_ctx *ctx, int npairs, int epochs, uint64_t seed, sipg_train_info *info);
 /* which = 0: Chebyshev (default); 1: learned (trained network required), with
  * steps_pre and steps_post network steps around the coarse correction. */

@@ -951,31 +951,52 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   int rho_cnt = 0;
   const int save_smoother = c->smoother;
   c->smoother = 0;
+  double *bv = dalloc<double>(c, Nd), *xv = dalloc<double>(c, Nd), *xx = dalloc<double>(c, Nd),
+         *xt2 = dalloc<double>(c, Nd);
   long row = 0;
+  auto add_pairs = [&](const double *res, const double *err, long cnt) {
+    CK(mlp_gather<double>(res, F.n, F.m, cells, (int)row, (int)cnt, bfm(Xall, row * N.Fp), N.Fp, sall + row,
+                          c->stream));
+    CK(mlp_targets(err, N.n3, cells, (int)row, (int)cnt, sall + row, Tall + row * N.No, N.No, c->stream));
+    row += cnt;
+  };
+  // Snapshots of the plain cycle at work: for FCG iterate j of a seeded random
+  // right-hand side, the cycle's input b_v = r_j; its exact correction
+  // x*_v = A^-1 b_v (solved to 1e-12); pairs of two kinds at random cells:
+  //  - before smoothing (x = 0): residual b_v, error x*_v;
+  //  - after pre-smoothing and the coarse-grid correction (the state the
+  //    post-smoother starts from): residual b_v - A x, error x*_v - x.
   for (int sidx = 0; sidx < S; ++sidx) {
     for (int64_t i = 0; i < Nd; ++i) hb[i] = uniform_pm1(seed + 1 + sidx, (uint64_t)i);
     CK(cudaStreamSynchronize(c->stream));   // the previous right-hand side is no longer read
     CK(cudaMemcpyAsync(b, hb.data(), Nd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(xs, 0, Nd * sizeof(double), c->stream));
-    sipg_solve_info inf{};
-    const sipg_status st = solve_impl(c, b, xs, 1e-12, 500, 0, &inf);
-    if (st != SIPG_OK) {
-      c->smoother = save_smoother;
-      return st;
-    }
-    rho_sum += inf.rho;
-    ++rho_cnt;
     for (int j = 0; j < J; ++j) {
       CK(cudaMemsetAsync(xj, 0, Nd * sizeof(double), c->stream));
       if (j > 0) solve_impl(c, b, xj, 0.0, j, j, nullptr);
-      apply_level<double>(c, c->L, xj, r, 2, nullptr, nullptr, b);
-      CK(cudaMemcpyAsync(e, xs, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      CK(launch_axpy<double>(e, -1.0, xj, Nd, c->stream));
-      const long cnt = (sidx * J + j == S * J - 1) ? R - row : R / (S * J);
-      CK(mlp_gather<double>(r, F.n, F.m, cells, (int)row, (int)cnt, bfm(Xall, row * N.Fp), N.Fp, sall + row,
-                            c->stream));
-      CK(mlp_targets(e, N.n3, cells, (int)row, (int)cnt, sall + row, Tall + row * N.No, N.No, c->stream));
-      row += cnt;
+      apply_level<double>(c, c->L, xj, bv, 2, nullptr, nullptr, b);           // b_v = r_j
+      CK(cudaMemsetAsync(xv, 0, Nd * sizeof(double), c->stream));
+      sipg_solve_info inf{};
+      const sipg_status st = solve_impl(c, bv, xv, 1e-12, 500, 0, &inf);     // x*_v
+      if (st != SIPG_OK) {
+        c->smoother = save_smoother;
+        return st;
+      }
+      rho_sum += inf.rho;
+      ++rho_cnt;
+      const long snaps = (long)S * J, cnt = (sidx * J + j == snaps - 1) ? R - row : R / snaps;
+      const long c1 = cnt / 2;
+      add_pairs(bv, xv, c1);
+      // the cycle up to the post-smoother, in FP64
+      double *x = xx, *xt = xt2;
+      chebyshev<double>(c, c->L, bv, x, xt, c->prm.cheb_degree, true);
+      apply_level<double>(c, c->L, x, r, 2, nullptr, nullptr, bv);
+      restrict_level<double>(c, c->L, r, (double *)c->lv[c->L - 1].vb[0]);
+      const double *xc = vcycle_rec<double>(c, c->L - 1);
+      prolongate_level<double>(c, c->L, xc, x);
+      apply_level<double>(c, c->L, x, r, 2, nullptr, nullptr, bv);
+      CK(cudaMemcpyAsync(e, xv, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      CK(launch_axpy<double>(e, -1.0, x, Nd, c->stream));
+      add_pairs(r, e, cnt - c1);
     }
   }
   c->smoother = save_smoother;
