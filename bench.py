@@ -41,16 +41,19 @@ METRIC = "SIPG apply DoF/s & %roofline; solve s/MDoF to 1e-10 rel. res. vs plain
 # Iterations of this workload's FP64 solve to 1e-10 (measured on the GB300; the
 # GPU path and the oracle reach equal counts in the parity tests).  The oracle
 # arm scales one timed fine-level operator apply by the number of fine-level
-# applies one solve performs: (ITERATIONS + 1) V-cycles with 2 n_s + 1 DG
-# applies each plus ITERATIONS outer applies (a lower bound of the oracle's
-# solve time: FE levels, transfers and vector updates are left out).
+# applies the oracle's solve performs: ITERATIONS V-cycles (flexible CG
+# preconditions once before its loop and once after every non-final
+# iteration) with 2 n_s DG applies each (n_s - 1 pre-smoothing from x = 0, one
+# residual, n_s post-smoothing), ITERATIONS outer applies and the initial
+# residual: a lower bound of the oracle's solve time (FE levels, transfers and
+# vector updates are left out).
 ITERATIONS = 6
 NS = 5
 # DRAM bytes per DoF of the FP64 curved k=5 integration pass, from the ncu
 # capture summarised in profiles/dg_kernels_curved32_k5_fp64.md (32^3 cells,
 # scaled to this workload by the number of cells it processes).
 INTEGRATE_DRAM_BYTES_PER_DOF = 126.2
-DG_APPLIES_PER_SOLVE = (ITERATIONS + 1) * (2 * NS + 1) + ITERATIONS
+DG_APPLIES_PER_SOLVE = ITERATIONS * 2 * NS + ITERATIONS + 1
 
 
 def clocks_sampler(stop, out):
@@ -123,13 +126,15 @@ def run_gb300(args):
         x.zero_()
         return ctx.solve(b, x, rtol=1e-10, maxit=100)
 
+    # the clock sampler runs from before the warm-up, so that starting it costs
+    # the timed steps nothing; it covers the whole timed region
+    samples, stop = [], threading.Event()
+    th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
+    th.start()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             info = step()
     torch.cuda.synchronize()
-    samples, stop = [], threading.Event()
-    th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
-    th.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()

@@ -90,10 +90,23 @@ typedef struct {
                               polynomial levels down to 1, 'h' geometric
                               levels; default "cph"; must contain 'c' and 'p'
                               (the dense coarse solve works on FE_1)       */
-  int autotune;            /* 1: at setup, time the compiled tile shapes
-                              (cells per thread block) of both DG passes in
-                              both precisions and keep the fastest; cached
-                              per (degree, geometry) for the process       */
+  int autotune;            /* 1: at setup, time a few tile shapes (cells per
+                              thread block) of every cell kernel of every
+                              level (both DG passes, the FE cell pass) in
+                              both precisions and keep the fastest; the
+                              candidates are the widths whose last wave of
+                              blocks leaves the fewest cell slots idle;
+                              cached per (degree, geometry, cells) for the
+                              process                                      */
+  int fe_assemble;         /* FE levels of degree <= fe_assemble (0, 1 or 2;
+                              default 1) apply an assembled (2p+1)^3-point
+                              stencil built at setup from the same element
+                              integrals instead of the matrix-free cell and
+                              node passes (27 points at degree 1: one
+                              node-centric launch instead of two); 0 = all
+                              levels matrix-free.  Degree 2 (125 points) is
+                              slower than matrix-free on GB300 and is kept
+                              for comparison only                          */
   void *stream;            /* cudaStream_t or NULL                             */
 } sipg_params;
 
@@ -188,6 +201,27 @@ sipg_status sipg_vcycle(sipg_ctx *ctx, const double *r_dev, double *z_dev);
 sipg_status sipg_solve(sipg_ctx *ctx, const double *b_dev, double *x_dev, double rtol,
                        int maxit, int fixed_iters, sipg_solve_info *info);
 
+/* Several right-hand sides of the context's problem solved together (not in
+ * the paper, whose solver takes one right-hand side per run): B_dev and
+ * X_dev hold nrhs device vectors of num_dofs values one after another (vector
+ * r at r * num_dofs, the oracle's DoF order in each), X_dev is the initial
+ * guess and the result.  One flexible CG per right-hand side, all in lockstep:
+ * every operator application and every V-cycle runs on all nrhs vectors with
+ * one launch per kernel (block b of a cell kernel = cell group b / nrhs of
+ * vector b % nrhs, so the vectors share each group's geometry reads).  Each
+ * right-hand side stops on its own at rtol (or maxit); the iterates of each
+ * equal those of sipg_solve on it alone up to rounding.  infos: nrhs entries
+ * (may be NULL).  1 <= nrhs <= 4096; device memory for nrhs vectors of every
+ * level is allocated on first use and kept.  Errors: EINVAL, ENAN (a right-hand
+ * side not finite), ENOTCONV, EBREAKDOWN as for sipg_solve. */
+sipg_status sipg_solve_multi(sipg_ctx *ctx, int nrhs, const double *B_dev, double *X_dev, double rtol, int maxit,
+                             sipg_solve_info *infos);
+
+/* V = A U for nv vectors at once (same layout as sipg_solve_multi), in the
+ * given precision (0 FP64, 1 FP32); the same kernels as sipg_operator_apply
+ * with one launch per pass for all vectors.  Needs a solver context. */
+sipg_status sipg_operator_apply_multi(sipg_ctx *ctx, int precision, int nv, const void *U_dev, void *V_dev);
+
 /* The same solve from and to HOST memory: copies b_host to the device, solves
  * with x0 = 0, copies x back to x_host (both FP64, length = finest dofs). */
 sipg_status sipg_solve_host(sipg_ctx *ctx, const double *b_host, double *x_host, double rtol,
@@ -272,9 +306,17 @@ sipg_status sipg_mlp_gradients(sipg_ctx *ctx, const float *X_dev, const float *T
  * (already divided by s, BF16-rounded) and scale[cells] = s. */
 sipg_status sipg_mlp_features(sipg_ctx *ctx, const double *r_dev, float *feat_dev, float *scale_dev);
 
-/* Cells per thread block the finest-level DG pass uses (pass 0 evaluation,
- * 1 integration) in the given precision: the autotuned value or the default. */
-sipg_status sipg_tile_shape(const sipg_ctx *ctx, int precision, int pass, int *cells_per_block);
+/* Cells per thread block a cell kernel of a level uses in the given
+ * precision (pass 0 DG evaluation, 1 DG integration on a DG level; 2 the FE
+ * cell pass on an FE level): the autotuned or set value, else the default.
+ * EINVAL for a pass that does not exist on the level. */
+sipg_status sipg_tile_shape(const sipg_ctx *ctx, int level, int precision, int pass, int *cells_per_block);
+
+/* Sets that width (0 = the compiled default; at most 768 threads and 227 KB
+ * of shared memory per block, else EINVAL).  The results do not depend on
+ * it: every cell is computed by the same threads in the same order.  Drops
+ * the context's captured V-cycle graphs (they hold the old launch shapes). */
+sipg_status sipg_set_tile_shape(sipg_ctx *ctx, int level, int precision, int pass, int cells_per_block);
 
 /* Number of kernel launches (and CUDA-graph launches) the library has issued
  * in this process so far, all contexts together.  For launch accounting. */

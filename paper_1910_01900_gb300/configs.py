@@ -6,7 +6,8 @@ cube4_k3        4^3 Cartesian, k=3, manufactured RHS: FP64 multigrid and mixed p
 cube32_k4       32^3 Cartesian, k=4 (4.1 MDoF), manufactured RHS: mixed precision vs plain FP64 multigrid.
 batch16         the 16 seeded problems (m in 8..24 even, k in 2..6), FP32 cycle / FP64 FCG:
                 one batch (persistent launches, lockstep FCG) vs the 16 solves one after another.
-rhs32           32 seeded right-hand sides on 16^3 k=4: batch vs one after another.
+rhs32           32 seeded right-hand sides on 16^3 k=4: batch, one N x 32 block on one
+                context (sipg_solve_multi) and one after another.
 curved32_k4     32^3 curved, k=4: learned smoother (trained on 10^5 pairs) vs Chebyshev,
                 iterations and time to 1e-10.
 
@@ -113,11 +114,29 @@ def run_batch(name, problems, steps, stream):
         return its
     with torch.cuda.stream(stream):
         ms_s, its = _timed(solve_seq, steps, stream)
-    return {"workload": name, "problems": len(problems), "dofs_total": total, "setup_s": setup,
-            "batch_ms": ms_b, "sequential_ms": ms_s, "speedup_batch_vs_sequential": ms_s / ms_b,
-            "batch_s_per_mdof": ms_b * 1e-3 * 1e6 / total,
-            "iterations": [i.iterations for i in infos], "sequential_iterations": its,
-            "all_converged": all(i.converged for i in infos)}
+    res = {"workload": name, "problems": len(problems), "dofs_total": total, "setup_s": setup,
+           "batch_ms": ms_b, "sequential_ms": ms_s, "speedup_batch_vs_sequential": ms_s / ms_b,
+           "batch_s_per_mdof": ms_b * 1e-3 * 1e6 / total,
+           "iterations": [i.iterations for i in infos], "sequential_iterations": its,
+           "all_converged": all(i.converged for i in infos)}
+    if name == "rhs32":
+        # the same right-hand sides as one N x 32 block on one context (sipg_solve_multi)
+        c = ctxs[0]
+        Bm = torch.stack(bs)
+        Xm = torch.zeros_like(Bm)
+
+        def solve_multi():
+            Xm.zero_()
+            return c.solve_multi(Bm, Xm, rtol=1e-10)
+        with torch.cuda.stream(stream):
+            ms_m, minfos = _timed(solve_multi, steps, stream)
+        res.update({"multi_ms": ms_m, "multi_s_per_mdof": ms_m * 1e-3 * 1e6 / total,
+                    "speedup_multi_vs_sequential": ms_s / ms_m,
+                    "multi_iterations": [i.iterations for i in minfos],
+                    "multi_all_converged": all(i.converged for i in minfos),
+                    "multi_rel_diff_vs_sequential": float(torch.linalg.norm(Xm - torch.stack(xs)) /
+                                                     torch.linalg.norm(torch.stack(xs)))})
+    return res
 
 
 def run_learned(steps, stream, npairs=100000, epochs=20):

@@ -43,9 +43,9 @@ __global__ void __launch_bounds__(kBatchThreads)
 #define SIPG_BATCH_CASE(NN)                                              \
   case NN:                                                               \
     if (INTEGRATE)                                                       \
-      dg_integrate_body<T, NN, CURVED>(P.a, w.cell0, w.ncta, sm);        \
+      dg_integrate_body<T, NN, CURVED>(P.a, vec_ptrs(P.a, 0), w.cell0, w.ncta, sm); \
     else                                                                 \
-      dg_eval_body<T, NN, CURVED>(P.a, w.cell0, w.ncta, sm);             \
+      dg_eval_body<T, NN, CURVED>(P.a, vec_ptrs(P.a, 0), w.cell0, w.ncta, sm); \
     break;
       switch (P.n) {
         SIPG_BATCH_CASE(2)
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kBatchThreads)
   }
 }
 
-constexpr int kSegBlocks = 32;   // blocks per problem in the batched reductions
+constexpr int kSegBlocks = kSegBlocksHost;   // blocks per system in the batched reductions
 
 __device__ void seg_reduce2(double a, double b, double *partials, unsigned *counter, double *out) {
   // blocks (p, j), j < kSegBlocks: partial sums per block, the last block of

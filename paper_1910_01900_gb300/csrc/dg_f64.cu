@@ -7,14 +7,20 @@ template <>
 void upload_tables_dg<double>(const Tables<double> &t) { upload_tables_tu(t); }
 template <>
 cudaError_t launch_dg_eval<double>(int n, bool curved, const DGArgs<double> &a, cudaStream_t s, int cb) {
-  return dispatch_dg<double>(false, n, curved, a, s, cb);
+  return dispatch_dg<double>(0, 0, n, curved, &a, s, cb);
 }
 template <>
 cudaError_t launch_dg_integrate<double>(int n, bool curved, const DGArgs<double> &a, cudaStream_t s, int cb) {
-  return dispatch_dg<double>(true, n, curved, a, s, cb);
+  return dispatch_dg<double>(1, 0, n, curved, &a, s, cb);
 }
 template <>
 int dg_cells_per_block<double>(int n) { return default_cb(n); }
+template <>
+int dg_max_cells_per_block<double>(int n) { return max_cb(n, sizeof(double)); }
+template <>
+cudaError_t dg_blocks_per_sm<double>(int n, bool curved, int pass, int cb, int *blocks) {
+  return dispatch_dg<double>(pass, 1, n, curved, nullptr, nullptr, cb, blocks);
+}
 template <>
 cudaError_t prepare_dg_kernels<double>() { return prep_dg_all<double>(); }
 

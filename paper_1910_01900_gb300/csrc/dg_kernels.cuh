@@ -31,18 +31,26 @@
 
 namespace sipg {
 
+template <typename T>
+struct VecPtrs {
+  const T *u;
+  T *out;
+  const T *x, *xp, *b;
+  T *grad, *trace;
+};
+
 // Evaluation pass for the cells cell0 .. cell0+ncta-1 of one problem, on a
 // thread block of blockDim.x >= ncta * N^2 threads with 4 ncta N^3 values of
 // shared memory at sm.  Shared by the per-problem and the batched kernels.
 template <typename T, int N, bool CURVED>
-__device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0, const int ncta, T *sm) {
+__device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T> &v, const int cell0, const int ncta, T *sm) {
   constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const bool act = cl < ncta;
   T *su = sm + cl * 4 * TT;
 
-  const T *ug = a.u + (size_t)cell0 * N3;
+  const T *ug = v.u + (size_t)cell0 * N3;
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3;
     sm[c * 4 * TT + Tile<N>::idx(i - c * N3)] = ug[i];
@@ -66,7 +74,7 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
   }
   __syncthreads();
   if (!a.recompute) {
-    T *gg = a.grad + (size_t)cell0 * 3 * N3;
+    T *gg = v.grad + (size_t)cell0 * 3 * N3;
     for (int i = tid; i < ncta * 3 * N3; i += NT) {
       const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
       gg[i] = sm[c * 4 * TT + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)];
@@ -124,7 +132,7 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
       q0 = c0[0] * gr0[0] + c0[N2] * gr0[1] + c0[2 * N2] * gr0[2];
       q1 = c1[0] * gr1[0] + c1[N2] * gr1[1] + c1[2 * N2] * gr1[2];
     }
-    T *tr = a.trace + ((size_t)cell * 6 + 2 * d) * 2 * N2 + l;
+    T *tr = v.trace + ((size_t)cell * 6 + 2 * d) * 2 * N2 + l;
     tr[0] = v0;
     tr[N2] = q0;
     tr[2 * N2] = v1;
@@ -134,7 +142,8 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const int cell0
 
 // Integration pass (same thread and shared-memory contract as the evaluation).
 template <typename T, int N, bool CURVED>
-__device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int cell0, const int ncta, T *sm) {
+__device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecPtrs<T> &v, const int cell0, const int ncta,
+                                                  T *sm) {
   constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
@@ -145,7 +154,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
   if (a.recompute) {
     // gradient at the Gauss points again from u: 3 interpolation and 3
     // collocation-derivative sweeps (the value slot st is free until the faces)
-    const T *ug = a.u + (size_t)cell0 * N3;
+    const T *ug = v.u + (size_t)cell0 * N3;
     for (int i = tid; i < ncta * N3; i += NT) {
       const int c = i / N3;
       sm[c * 4 * TT + Tile<N>::idx(i - c * N3)] = ug[i];
@@ -168,7 +177,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
       }
     }
   } else {
-    const T *gg = a.grad + (size_t)cell0 * 3 * N3;
+    const T *gg = v.grad + (size_t)cell0 * 3 * N3;
     for (int i = tid; i < ncta * 3 * N3; i += NT) {
       const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
       sm[c * 4 * TT + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)] = gg[i];
@@ -215,7 +224,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
       const size_t ftan = ijk[t1] + (size_t)a.m[t1] * ijk[t2];
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        const T *tr = a.trace + ((size_t)cell * 6 + 2 * d + s) * 2 * N2 + l;
+        const T *tr = v.trace + ((size_t)cell * 6 + 2 * d + s) * 2 * N2 + l;
         const T uo = tr[0], qo = tr[N2];
         T dA;
         const size_t face = (size_t)(ijk[d] + s) * nfp + ftan;
@@ -231,7 +240,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
         const bool has_nb = s ? (ijk[d] < a.m[d] - 1) : (ijk[d] > 0);
         if (has_nb) {
           const int nb = cell + (s ? cstride[d] : -cstride[d]);
-          const T *tn = a.trace + ((size_t)nb * 6 + 2 * d + (1 - s)) * 2 * N2 + l;
+          const T *tn = v.trace + ((size_t)nb * 6 + 2 * d + (1 - s)) * 2 * N2 + l;
           const T un = tn[0], qn = tn[N2];
           const T tau_f = max(tau_e, a.tau[nb]);
           const T jump = uo - un;
@@ -310,34 +319,59 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const int 
   const size_t g0 = (size_t)cell * N3 + l;
   if (a.mode == 0) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) a.out[g0 + q * N2] = y[q];
+    for (int q = 0; q < N; ++q) v.out[g0 + q * N2] = y[q];
   } else if (a.mode == 2) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) a.out[g0 + q * N2] = a.b[g0 + q * N2] - y[q];
+    for (int q = 0; q < N; ++q) v.out[g0 + q * N2] = v.b[g0 + q * N2] - y[q];
   } else {
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       const size_t i = g0 + q * N2;
-      T v = a.c3 * a.dinv[i] * (a.b[i] - y[q]);
-      if (a.x) v = fma(a.c1, a.x[i], v);
-      if (a.xp) v = fma(a.c2, a.xp[i], v);
-      a.out[i] = v;
+      T z = a.c3 * a.dinv[i] * (v.b[i] - y[q]);
+      if (v.x) z = fma(a.c1, v.x[i], z);
+      if (v.xp) z = fma(a.c2, v.xp[i], z);
+      v.out[i] = z;
     }
   }
 }
 
-template <typename T, int N, bool CURVED, int CB>
-__global__ void __launch_bounds__(CB *N *N) dg_eval_kernel(const DGArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int cell0 = blockIdx.x * CB;
-  dg_eval_body<T, N, CURVED>(a, cell0, min(CB, a.ncells - cell0), reinterpret_cast<T *>(smem_raw));
+// Per-vector pointers of a multi-vector launch: vector r of u, out, x, xp, b
+// and its scratch (geometry and inverse diagonal are shared).  A small
+// struct of pointers only, so it stays in registers.
+template <typename T>
+__device__ __forceinline__ VecPtrs<T> vec_ptrs(const DGArgs<T> &a, const int r) {
+  const int64_t o = r * a.vs;
+  VecPtrs<T> v;
+  v.u = a.u + o;
+  v.out = a.out + o;
+  v.x = a.x ? a.x + o : nullptr;
+  v.xp = a.xp ? a.xp + o : nullptr;
+  v.b = a.b ? a.b + o : nullptr;
+  v.grad = a.grad ? a.grad + r * a.gs : nullptr;
+  v.trace = a.trace + r * a.ts;
+  return v;
 }
 
-template <typename T, int N, bool CURVED, int CB>
-__global__ void __launch_bounds__(CB *N *N) dg_integrate_kernel(const DGArgs<T> a) {
+// One thread block handles cb consecutive cells of one vector with cb N^2
+// threads; block b is cell group b / nv of vector b % nv, so the vectors of
+// one group run side by side and share its geometry in L2.  cb is a launch
+// parameter (picked per level and size by the tile-shape autotuner): one
+// compiled kernel serves every block width up to kCellThreads threads.
+template <typename T, int N, bool CURVED>
+__global__ void __launch_bounds__(kCellThreads) dg_eval_kernel(const DGArgs<T> a, const int cb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int cell0 = blockIdx.x * CB;
-  dg_integrate_body<T, N, CURVED>(a, cell0, min(CB, a.ncells - cell0), reinterpret_cast<T *>(smem_raw));
+  const int grp = blockIdx.x / a.nv, vec = blockIdx.x - grp * a.nv;
+  const int cell0 = grp * cb;
+  dg_eval_body<T, N, CURVED>(a, vec_ptrs(a, vec), cell0, min(cb, a.ncells - cell0), reinterpret_cast<T *>(smem_raw));
+}
+
+template <typename T, int N, bool CURVED>
+__global__ void __launch_bounds__(kCellThreads) dg_integrate_kernel(const DGArgs<T> a, const int cb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int grp = blockIdx.x / a.nv, vec = blockIdx.x - grp * a.nv;
+  const int cell0 = grp * cb;
+  dg_integrate_body<T, N, CURVED>(a, vec_ptrs(a, vec), cell0, min(cb, a.ncells - cell0),
+                                  reinterpret_cast<T *>(smem_raw));
 }
 
 // Diagonal of the DG operator (setup, FP64), one thread per DoF: the cell

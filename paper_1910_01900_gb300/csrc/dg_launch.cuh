@@ -5,37 +5,43 @@
 
 namespace sipg {
 
-template <typename T, int N, bool CURVED, int CB>
-static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s) {
-  const size_t smem = (size_t)CB * 4 * Tile<N>::T3 * sizeof(T);
-  const int grid = (a.ncells + CB - 1) / CB;
+template <typename T, int N, bool CURVED>
+static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s, int cb) {
+  if (cb <= 0) cb = default_cb(N);
+  if (cb > max_cb(N, sizeof(T))) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)cb * 4 * Tile<N>::T3 * sizeof(T);
+  const int64_t grid = (int64_t)((a.ncells + cb - 1) / cb) * a.nv;
   if (grid == 0) return cudaSuccess;
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
   if (integrate)
-    dg_integrate_kernel<T, N, CURVED, CB><<<grid, CB * N * N, smem, s>>>(a);
+    dg_integrate_kernel<T, N, CURVED><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
   else
-    dg_eval_kernel<T, N, CURVED, CB><<<grid, CB * N * N, smem, s>>>(a);
+    dg_eval_kernel<T, N, CURVED><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
   note_launch();
   return cudaGetLastError();
 }
 
-// Opt every compiled tile shape into its dynamic shared memory size (once per
-// device, before any launch or stream capture).
-template <typename T, int N, bool CURVED, int CB>
-static cudaError_t prep_dg() {
-  const int smem = CB * 4 * Tile<N>::T3 * (int)sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(dg_integrate_kernel<T, N, CURVED, CB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(dg_eval_kernel<T, N, CURVED, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+// Resident thread blocks per SM of one pass at cb cells per block.
+template <typename T, int N, bool CURVED>
+static cudaError_t occ_dg(bool integrate, int cb, int *blocks) {
+  const size_t smem = (size_t)cb * 4 * Tile<N>::T3 * sizeof(T);
+  return integrate ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_integrate_kernel<T, N, CURVED>,
+                                                                   cb * N * N, smem)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_eval_kernel<T, N, CURVED>,
+                                                                   cb * N * N, smem);
 }
 
+// Opt every kernel into the shared memory of its widest block (once per
+// device, before any launch or stream capture).
 template <typename T, int N>
 static cudaError_t prep_dg_n() {
-  constexpr int D = default_cb(N);
+  const int smem = max_cb(N, sizeof(T)) * 4 * Tile<N>::T3 * (int)sizeof(T);
   cudaError_t e = cudaSuccess;
-  for (cudaError_t r : {prep_dg<T, N, false, D>(), prep_dg<T, N, true, D>(), prep_dg<T, N, false, 1>(),
-                        prep_dg<T, N, true, 1>(), prep_dg<T, N, false, 2 * D>(), prep_dg<T, N, true, 2 * D>(),
-                        prep_dg<T, N, false, (D + 1) / 2>(), prep_dg<T, N, true, (D + 1) / 2>()})
+  for (cudaError_t r :
+       {cudaFuncSetAttribute(dg_integrate_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_integrate_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_eval_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_eval_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)})
     if (r != cudaSuccess) e = r;
   return e;
 }
@@ -49,23 +55,15 @@ static cudaError_t prep_dg_all() {
   return e;
 }
 
-template <typename T, int N, bool CURVED>
-static cudaError_t run_dg_cb(bool integrate, const DGArgs<T> &a, cudaStream_t s, int cb) {
-  // a few tile widths per n for the autotuner; 0 = default
-  constexpr int D = default_cb(N);
-  if (cb == 0 || cb == D) return run_dg<T, N, CURVED, D>(integrate, a, s);
-  if (cb == 1) return run_dg<T, N, CURVED, 1>(integrate, a, s);
-  if (cb == 2 * D) return run_dg<T, N, CURVED, 2 * D>(integrate, a, s);
-  if (cb == (D + 1) / 2) return run_dg<T, N, CURVED, (D + 1) / 2>(integrate, a, s);
-  return cudaErrorInvalidValue;
-}
-
+// pass 0 evaluation, 1 integration; op 0 launch, 1 occupancy query into *blocks
 template <typename T>
-static cudaError_t dispatch_dg(bool integrate, int n, bool curved, const DGArgs<T> &a, cudaStream_t s, int cb) {
-#define SIPG_DG_CASE(NN)                                                        \
-  case NN:                                                                      \
-    return curved ? run_dg_cb<T, NN, true>(integrate, a, s, cb)                 \
-                  : run_dg_cb<T, NN, false>(integrate, a, s, cb);
+static cudaError_t dispatch_dg(int pass, int op, int n, bool curved, const DGArgs<T> *a, cudaStream_t s, int cb,
+                               int *blocks = nullptr) {
+#define SIPG_DG_CASE(NN)                                                                            \
+  case NN:                                                                                          \
+    if (op == 1)                                                                                    \
+      return curved ? occ_dg<T, NN, true>(pass == 1, cb, blocks) : occ_dg<T, NN, false>(pass == 1, cb, blocks); \
+    return curved ? run_dg<T, NN, true>(pass == 1, *a, s, cb) : run_dg<T, NN, false>(pass == 1, *a, s, cb);
   switch (n) {
     SIPG_DG_CASE(2)
     SIPG_DG_CASE(3)

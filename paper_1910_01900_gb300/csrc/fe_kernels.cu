@@ -29,14 +29,19 @@ __device__ __forceinline__ bool node_constrained(const int g[3], const int grid[
          (g[2] == 0 && bc[4] == 0) || (g[2] == grid[2] - 1 && bc[5] == 0);
 }
 
-template <typename T, int N, bool CURVED, int CB>
-__global__ void __launch_bounds__(CB *N *N) fe_cell_kernel(const FEArgs<T> a) {
-  constexpr int N2 = N * N, N3 = N2 * N, NT = CB * N2, TT = Tile<N>::T3;
+// cb cells per thread block (a launch parameter, cb N^2 threads)
+template <typename T, int N, bool CURVED>
+__global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a, const int cb) {
+  constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
+  const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
-  const int cell0 = blockIdx.x * CB;
-  const int ncta = min(CB, a.ncells - cell0);
+  // block -> (cell group, vector); the vectors of one group are neighbours
+  const int grp = blockIdx.x / a.nv, vec = blockIdx.x - grp * a.nv;
+  const int cell0 = grp * cb;
+  const int ncta = min(cb, a.ncells - cell0);
+  const T *__restrict__ ug = a.u + vec * a.vs;
   const bool act = cl < ncta;
   T *su = sm + cl * 4 * TT;
   for (int i = tid; i < ncta * N3; i += NT) {
@@ -45,7 +50,7 @@ __global__ void __launch_bounds__(CB *N *N) fe_cell_kernel(const FEArgs<T> a) {
     const int g[3] = {(cell % a.m[0]) * a.deg + p % N, ((cell / a.m[0]) % a.m[1]) * a.deg + (p / N) % N,
                       (cell / (a.m[0] * a.m[1])) * a.deg + p / N2};
     const size_t gi = g[0] + (size_t)a.grid[0] * (g[1] + (size_t)a.grid[1] * g[2]);
-    sm[c * 4 * TT + Tile<N>::idx(p)] = node_constrained(g, a.grid, a.bc) ? T(0) : a.u[gi];
+    sm[c * 4 * TT + Tile<N>::idx(p)] = node_constrained(g, a.grid, a.bc) ? T(0) : ug[gi];
   }
   __syncthreads();
 #pragma unroll 1
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(CB *N *N) fe_cell_kernel(const FEArgs<T> a) {
     load_line<T, N>(su, base, stride, x);
   }
   apply_mat<T, N, MSt>(x, y);
-  T *eb = a.ebuf + (size_t)(cell0 + cl) * N3 + l;
+  T *eb = a.ebuf + vec * a.es + (size_t)(cell0 + cl) * N3 + l;
 #pragma unroll
   for (int q = 0; q < N; ++q) eb[q * N2] = y[q];
 }
@@ -143,60 +148,220 @@ __global__ void fe_diag_cells_kernel(const FEArgs<double> a, const double *S, co
   a.ebuf[idx] = sum;
 }
 
+// ------------------------------------------------- assembled low-degree levels
+// On FE levels of degree p <= 2 the operator is applied from an assembled
+// stencil instead of by sum factorisation: those levels are small and their
+// matrix-free apply (a cell pass with a dozen barriers plus a node pass) is
+// bound by latency, not by arithmetic or bytes.  The stencil holds, for every
+// node g and offset o in [-p, p]^3, the matrix entry A[g][g + o] = the sum of
+// the element-matrix entries of the cells containing both nodes, with the
+// same quadrature and metric as the matrix-free cell pass (so both give the
+// same operator up to rounding); constrained rows are identity rows and
+// constrained columns are zero, as in the matrix-free pass.
+
+// Element matrices K[cell][i][j] = sum_q grad phi_i^T M_q grad phi_j (setup, FP64).
+template <int N, bool CURVED>
+__global__ void fe_elem_matrix_kernel(const FEArgs<double> a, const double *S, const double *Sd, double *K) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int cell = blockIdx.x;
+  for (int ij = threadIdx.x; ij < N3 * N3; ij += blockDim.x) {
+    const int i = ij / N3, j = ij - i * N3;
+    const int ii[3] = {i % N, (i / N) % N, i / N2}, jj[3] = {j % N, (j / N) % N, j / N2};
+    double sum = 0;
+    for (int qz = 0; qz < N; ++qz)
+      for (int qy = 0; qy < N; ++qy)
+        for (int qx = 0; qx < N; ++qx) {
+          const int q = qx + N * qy + N2 * qz;
+          const double si[3] = {S[qx * N + ii[0]], S[qy * N + ii[1]], S[qz * N + ii[2]]};
+          const double sj[3] = {S[qx * N + jj[0]], S[qy * N + jj[1]], S[qz * N + jj[2]]};
+          const double gi[3] = {Sd[qx * N + ii[0]] * si[1] * si[2], si[0] * Sd[qy * N + ii[1]] * si[2],
+                                si[0] * si[1] * Sd[qz * N + ii[2]]};
+          const double gj[3] = {Sd[qx * N + jj[0]] * sj[1] * sj[2], sj[0] * Sd[qy * N + jj[1]] * sj[2],
+                                sj[0] * sj[1] * Sd[qz * N + jj[2]]};
+          if (!CURVED) {
+            sum += a.wcart[q] * gi[0] * gj[0] + a.wcart[N3 + q] * gi[1] * gj[1] + a.wcart[2 * N3 + q] * gi[2] * gj[2];
+          } else {
+            const double *M = a.metric + (size_t)cell * 6 * N3 + q;
+            const double xx = M[0], yy = M[N3], zz = M[2 * N3], xy = M[3 * N3], xz = M[4 * N3], yz = M[5 * N3];
+            sum += gi[0] * (xx * gj[0] + xy * gj[1] + xz * gj[2]) + gi[1] * (xy * gj[0] + yy * gj[1] + yz * gj[2]) +
+                   gi[2] * (xz * gj[0] + yz * gj[1] + zz * gj[2]);
+          }
+        }
+    K[(size_t)cell * N3 * N3 + ij] = sum;
+  }
+}
+
+// Stencil of the level: coef[o][g], one thread per (node, offset) (setup, FP64).
+__global__ void fe_stencil_assemble_kernel(const FEArgs<double> a, const double *__restrict__ K,
+                                           double *__restrict__ coef) {
+  const int p = a.deg, n = p + 1, n3 = n * n * n, w = 2 * p + 1;
+  const long ng = (long)a.grid[0] * a.grid[1] * a.grid[2];
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ng * w * w * w) return;
+  const int o = (int)(idx / ng);
+  const long gid = idx - (long)o * ng;
+  const int g[3] = {(int)(gid % a.grid[0]), (int)((gid / a.grid[0]) % a.grid[1]),
+                    (int)(gid / ((long)a.grid[0] * a.grid[1]))};
+  const int off[3] = {o % w - p, (o / w) % w - p, o / (w * w) - p};
+  if (node_constrained(g, a.grid, a.bc)) {
+    coef[idx] = (off[0] == 0 && off[1] == 0 && off[2] == 0) ? 1.0 : 0.0;
+    return;
+  }
+  int h[3];
+  for (int d = 0; d < 3; ++d) h[d] = g[d] + off[d];
+  for (int d = 0; d < 3; ++d)
+    if (h[d] < 0 || h[d] >= a.grid[d]) {
+      coef[idx] = 0.0;
+      return;
+    }
+  if (node_constrained(h, a.grid, a.bc)) {
+    coef[idx] = 0.0;
+    return;
+  }
+  // cells containing both nodes: per direction c with c p <= min, max <= c p + p
+  int cs[3][2], cn[3];
+  for (int d = 0; d < 3; ++d) {
+    cn[d] = 0;
+    const int lo = min(g[d], h[d]), hi = max(g[d], h[d]);
+    for (int c = lo / p - 1; c <= lo / p; ++c)
+      if (c >= 0 && c < a.m[d] && c * p <= lo && hi <= c * p + p) cs[d][cn[d]++] = c;
+  }
+  double sum = 0;
+  for (int z = 0; z < cn[2]; ++z)
+    for (int y = 0; y < cn[1]; ++y)
+      for (int x = 0; x < cn[0]; ++x) {
+        const int c[3] = {cs[0][x], cs[1][y], cs[2][z]};
+        const size_t cell = c[0] + (size_t)a.m[0] * (c[1] + (size_t)a.m[1] * c[2]);
+        const int li = (g[0] - c[0] * p) + n * ((g[1] - c[1] * p) + n * (g[2] - c[2] * p));
+        const int lj = (h[0] - c[0] * p) + n * ((h[1] - c[1] * p) + n * (h[2] - c[2] * p));
+        sum += K[cell * n3 * n3 + (size_t)li * n3 + lj];
+      }
+  coef[idx] = sum;
+}
+
+// Stencil apply with the gather's epilogue (modes 0, 1, 2), one thread per
+// node, vector blockIdx.y.  Neighbours outside the grid or on a Dirichlet
+// plane are skipped (their coefficients are zero).
+template <typename T, int P>
+__global__ void fe_stencil_apply_kernel(const FEArgs<T> a, const T *__restrict__ coef) {
+  constexpr int W = 2 * P + 1;
+  const long ng = (long)a.grid[0] * a.grid[1] * a.grid[2];
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ng) return;
+  const int64_t vo = blockIdx.y * a.vs;
+  const T *__restrict__ u = a.u + vo;
+  const int g[3] = {(int)(gid % a.grid[0]), (int)((gid / a.grid[0]) % a.grid[1]),
+                    (int)(gid / ((long)a.grid[0] * a.grid[1]))};
+  bool ok[3][W];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const int h = g[d] + k - P;
+      ok[d][k] = h >= 0 && h < a.grid[d] && !(h == 0 && a.bc[2 * d] == 0) &&
+                 !(h == a.grid[d] - 1 && a.bc[2 * d + 1] == 0);
+    }
+  const long sy = a.grid[0], sz = (long)a.grid[0] * a.grid[1];
+  // all loads first, unconditionally (a skipped neighbour reads the node
+  // itself), so that they are in flight together; then the sum, skipping by
+  // selection
+  constexpr int W3 = W * W * W;
+  T cf[W3], uv[W3];
+#pragma unroll
+  for (int o = 0; o < W3; ++o) {
+    const int x = o % W, yy = (o / W) % W, z = o / (W * W);
+    const bool take = ok[0][x] && ok[1][yy] && ok[2][z];
+    cf[o] = coef[(long)o * ng + gid];
+    uv[o] = u[take ? gid + (x - P) + (yy - P) * sy + (z - P) * sz : gid];
+  }
+  T y = T(0);
+#pragma unroll
+  for (int o = 0; o < W3; ++o) {
+    const int x = o % W, yy = (o / W) % W, z = o / (W * W);
+    y = (ok[0][x] && ok[1][yy] && ok[2][z]) ? fma(cf[o], uv[o], y) : y;
+  }
+  if (node_constrained(g, a.grid, a.bc)) y = u[gid];   // identity row
+  const long gv = vo + gid;
+  if (a.mode == 0) {
+    a.out[gv] = y;
+  } else if (a.mode == 2) {
+    a.out[gv] = a.b[gv] - y;
+  } else {
+    T v = a.c3 * a.dinv[gid] * (a.b[gv] - y);
+    if (a.x) v = fma(a.c1, a.x[gv], v);
+    if (a.xp) v = fma(a.c2, a.xp[gv], v);
+    a.out[gv] = v;
+  }
+}
+
 // Node pass: out[g] = sum over the cells sharing node g of ebuf, then the epilogue.
 template <typename T>
 __global__ void fe_gather_kernel(const FEArgs<T> a) {
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= total) return;
+  // vector blockIdx.y
+  const T *__restrict__ ebuf = a.ebuf + blockIdx.y * a.es;
+  const int64_t vo = blockIdx.y * a.vs;
   const int n = a.deg + 1, n2 = n * n, n3 = n2 * n;
   const int g[3] = {(int)(gid % a.grid[0]), (int)((gid / a.grid[0]) % a.grid[1]),
                     (int)(gid / ((long)a.grid[0] * a.grid[1]))};
   const bool cons = node_constrained(g, a.grid, a.bc);
   T y;
   if (cons) {
-    y = (a.mode == 3) ? T(0) : (a.mode == 4 ? T(1) : a.u[gid]);
+    y = (a.mode == 3) ? T(0) : (a.mode == 4 ? T(1) : a.u[vo + gid]);
   } else {
-    // per direction: (cell, local index) pairs containing this node
-    int cc[3][2], ll[3][2], cnt[3];
+    // per direction the two candidate cells containing this node: the one
+    // below (when the node is on its upper face) and the one it starts
+    int cc[3][2], ll[3][2];
+    bool ok[3][2];
     for (int d = 0; d < 3; ++d) {
       const int c = g[d] / a.deg, r = g[d] - c * a.deg;
-      cnt[d] = 0;
-      if (r == 0 && c > 0) {
-        cc[d][cnt[d]] = c - 1;
-        ll[d][cnt[d]++] = a.deg;
-      }
-      if (c < a.m[d]) {
-        cc[d][cnt[d]] = c;
-        ll[d][cnt[d]++] = r;
-      }
+      ok[d][0] = r == 0 && c > 0;
+      cc[d][0] = c - 1;
+      ll[d][0] = a.deg;
+      ok[d][1] = c < a.m[d];
+      cc[d][1] = c;
+      ll[d][1] = r;
+    }
+    // all eight loads issued unconditionally (a missing cell reads entry 0),
+    // then summed in a fixed order over the cells that exist
+    T e[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = q & 1, yy = (q >> 1) & 1, z = q >> 2;
+      const bool take = ok[0][x] && ok[1][yy] && ok[2][z];
+      const size_t cell = take ? cc[0][x] + (size_t)a.m[0] * (cc[1][yy] + (size_t)a.m[1] * cc[2][z]) : 0;
+      e[q] = ebuf[take ? cell * n3 + ll[0][x] + n * ll[1][yy] + n2 * ll[2][z] : 0];
     }
     y = T(0);
-    for (int z = 0; z < cnt[2]; ++z)
-      for (int yy = 0; yy < cnt[1]; ++yy)
-        for (int x = 0; x < cnt[0]; ++x) {
-          const size_t cell = cc[0][x] + (size_t)a.m[0] * (cc[1][yy] + (size_t)a.m[1] * cc[2][z]);
-          y += a.ebuf[cell * n3 + ll[0][x] + n * ll[1][yy] + n2 * ll[2][z]];
-        }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = q & 1, yy = (q >> 1) & 1, z = q >> 2;
+      if (ok[0][x] && ok[1][yy] && ok[2][z]) y += e[q];
+    }
   }
+  const long gv = vo + gid;
   if (a.mode == 0 || a.mode >= 3) {
-    a.out[gid] = y;
+    a.out[gv] = y;
   } else if (a.mode == 2) {
-    a.out[gid] = a.b[gid] - y;
+    a.out[gv] = a.b[gv] - y;
   } else {
-    T v = a.c3 * a.dinv[gid] * (a.b[gid] - y);
-    if (a.x) v = fma(a.c1, a.x[gid], v);
-    if (a.xp) v = fma(a.c2, a.xp[gid], v);
-    a.out[gid] = v;
+    T v = a.c3 * a.dinv[gid] * (a.b[gv] - y);
+    if (a.x) v = fma(a.c1, a.x[gv], v);
+    if (a.xp) v = fma(a.c2, a.xp[gv], v);
+    a.out[gv] = v;
   }
 }
 
 // c-transfer prolongation: x_dg[cell][i] += x_fe[node(cell, i)]  (injection).
 template <typename T>
-__global__ void c_prolongate_add_kernel(const FEArgs<T> a, const T *xc, T *xdg) {
+__global__ void c_prolongate_add_kernel(const FEArgs<T> a, const T *xc, T *xdg, const int64_t dg_stride) {
   const int n = a.deg + 1, n2 = n * n, n3 = n2 * n;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long)a.ncells * n3) return;
+  xc += blockIdx.y * a.vs;   // vector blockIdx.y
+  xdg += blockIdx.y * dg_stride;
   const int cell = (int)(idx / n3), p = (int)(idx - (long)cell * n3);
   const int g[3] = {(cell % a.m[0]) * a.deg + p % n, ((cell / a.m[0]) % a.m[1]) * a.deg + (p / n) % n,
                     (cell / (a.m[0] * a.m[1])) * a.deg + p / n2};
@@ -210,7 +375,9 @@ __global__ void c_prolongate_add_kernel(const FEArgs<T> a, const T *xc, T *xdg) 
 // same value and the multiplicity-weighted scatter of Section 3.2 reduces to
 // one evaluation.  P1 holds the 1D interpolation matrices l^c_j(x^f_i)
 // ([child][nf][nc]; child 0 only for the p-transfer).
-template <typename T>
+// NC: coarse points per direction at compile time (unrolled, all loads in
+// flight together), 0 = runtime
+template <typename T, int NC>
 __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ xc,
                                          T *__restrict__ xf) {
   const long total = (long)G.gf[0] * G.gf[1] * G.gf[2];
@@ -218,7 +385,9 @@ __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__
   if (gid >= total) return;
   const int g[3] = {(int)(gid % G.gf[0]), (int)((gid / G.gf[0]) % G.gf[1]), (int)(gid / ((long)G.gf[0] * G.gf[1]))};
   if (node_constrained(g, G.gf, G.bc)) return;
-  const int nf = G.pf + 1, nc = G.pc + 1;
+  xc += blockIdx.y * G.sc;   // vector blockIdx.y
+  xf += blockIdx.y * G.sf;
+  const int nf = G.pf + 1, nc = NC > 0 ? NC : G.pc + 1;
   const T *row[3];
   int base[3];
   for (int d = 0; d < 3; ++d) {
@@ -233,13 +402,78 @@ __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__
     base[d] = cc * G.pc;
   }
   T sum = T(0);
-  for (int jz = 0; jz < nc; ++jz)
-    for (int jy = 0; jy < nc; ++jy) {
+#pragma unroll
+  for (int jz = 0; jz < (NC > 0 ? NC : nc); ++jz)
+#pragma unroll
+    for (int jy = 0; jy < (NC > 0 ? NC : nc); ++jy) {
       const T wyz = row[1][jy] * row[2][jz];
       const size_t off = (size_t)G.gc[0] * ((base[1] + jy) + (size_t)G.gc[1] * (base[2] + jz));
-      for (int jx = 0; jx < nc; ++jx) sum += row[0][jx] * wyz * xc[off + base[0] + jx];
+#pragma unroll
+      for (int jx = 0; jx < (NC > 0 ? NC : nc); ++jx) sum += row[0][jx] * wyz * xc[off + base[0] + jx];
     }
   xf[gid] += sum;
+}
+
+// p/h restriction node by node for the two small transfers of the hierarchy
+// (degree 2 -> 1 on one mesh, degree 1 across a 2:1 refinement): coarse node
+// J sums the fine nodal values weighted by its coarse basis function at the
+// fine nodes, r_c[J] = sum_i phi_J(x_i) r_f[i] over the unconstrained fine
+// nodes i (R = P^T with the interpolation P of the prolongation), one launch
+// instead of a cell pass and a node pass.  In both cases coarse node J sits
+// at fine index 2 J per direction and its support there is 2J-1 .. 2J+1 (the
+// fine nodes 2J +- 2 are the neighbouring coarse nodes, where phi_J = 0); the
+// weights come from the prolongation's 1D tables.  27 loads per node, issued
+// unconditionally (a missing entry reads fine node 2J) and summed by
+// selection in a fixed order.
+template <typename T>
+__global__ void fe_restrict_nodes_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ rf,
+                                         T *__restrict__ rc) {
+  const long total = (long)G.gc[0] * G.gc[1] * G.gc[2];
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  rf += blockIdx.y * G.sf;   // vector blockIdx.y
+  rc += blockIdx.y * G.sc;
+  const int J[3] = {(int)(gid % G.gc[0]), (int)((gid / G.gc[0]) % G.gc[1]), (int)(gid / ((long)G.gc[0] * G.gc[1]))};
+  if (node_constrained(J, G.gc, G.bc)) {
+    rc[gid] = T(0);
+    return;
+  }
+  const int nf = G.pf + 1, nc = G.pc + 1;
+  int idx[3][3];
+  T w[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int i = 2 * J[d] + e - 1;   // fine index
+      const int C = e == 0 ? J[d] - 1 : (J[d] < G.mc[d] ? J[d] : J[d] - 1);   // coarse cell holding i and J
+      const int a = J[d] - C;
+      int ch = 0, b;
+      if (G.kind == 2) {
+        ch = min(i - 2 * C, 1);
+        b = i - (2 * C + ch);
+      } else {
+        b = i - C * G.pf;
+      }
+      const bool ok = i >= 0 && i < G.gf[d] && C >= 0 && C < G.mc[d] && !(i == 0 && G.bc[2 * d] == 0) &&
+                      !(i == G.gf[d] - 1 && G.bc[2 * d + 1] == 0);
+      idx[d][e] = ok ? i : 2 * J[d];
+      const size_t t = ok ? ((size_t)ch * nf + b) * nc + a : 0;   // in the table even when unused
+      w[d][e] = ok ? P1[t] : T(0);
+    }
+  const long sy = G.gf[0], sz = (long)G.gf[0] * G.gf[1];
+  T sum = T(0);
+#pragma unroll
+  for (int z = 0; z < 3; ++z)
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const T wt = w[0][x] * w[1][y] * w[2][z];
+        const T v = rf[idx[0][x] + sy * idx[1][y] + sz * idx[2][z]];
+        sum = wt != T(0) ? fma(wt, v, sum) : sum;
+      }
+  rc[gid] = sum;
 }
 
 // p/h restriction, cell part, by sum factorisation: one thread block per
@@ -261,6 +495,8 @@ __global__ void fe_restrict_cells_kernel(const XferGeom G, const T *__restrict__
   T *C = B + nf * nf * nc;          // nf nc^2   [iz][jy][jx]
   T *acc = C + nf * nc * nc;        // nc^3
   const int cc = blockIdx.x;
+  rf += blockIdx.y * G.sf;   // vector blockIdx.y
+  ebuf += blockIdx.y * G.se;
   const int cijk[3] = {cc % G.mc[0], (cc / G.mc[0]) % G.mc[1], cc / (G.mc[0] * G.mc[1])};
   const int nch = G.kind == 2 ? 2 : 1;
   for (int j = threadIdx.x; j < nc3; j += blockDim.x) acc[j] = T(0);
@@ -324,6 +560,8 @@ __global__ void dg_transfer_kernel(const XferGeom G, const T *__restrict__ P1, c
   const int big = nf3 > nc3 ? nf3 : nc3;
   T *A = sm, *B = A + big, *C = B + big, *acc = C + big;
   const int cc = blockIdx.x;
+  in += blockIdx.y * (PROLONG ? G.sc : G.sf);   // vector blockIdx.y
+  out += blockIdx.y * (PROLONG ? G.sf : G.sc);
   const int cijk[3] = {cc % G.mc[0], (cc / G.mc[0]) % G.mc[1], cc / (G.mc[0] * G.mc[1])};
   const int nch = G.kind == 4 ? 2 : 1;
   if (!PROLONG)
@@ -393,23 +631,30 @@ __global__ void dg_transfer_kernel(const XferGeom G, const T *__restrict__ P1, c
 
 // ---------------------------------------------------------------- launchers
 template <typename T, int N, bool CURVED>
-static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s) {
-  constexpr int CB = default_cb(N);
-  const size_t smem = (size_t)CB * 4 * Tile<N>::T3 * sizeof(T);
-  const int grid = (a.ncells + CB - 1) / CB;
+static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s, int cb) {
+  if (cb <= 0) cb = default_cb(N);
+  if (cb > max_cb(N, sizeof(T))) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)cb * 4 * Tile<N>::T3 * sizeof(T);
+  const int64_t grid = (int64_t)((a.ncells + cb - 1) / cb) * a.nv;
   if (grid == 0) return cudaSuccess;
-  fe_cell_kernel<T, N, CURVED, CB><<<grid, CB * N * N, smem, s>>>(a);
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  fe_cell_kernel<T, N, CURVED><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
   note_launch();
   return cudaGetLastError();
 }
 
+template <typename T, int N, bool CURVED>
+static cudaError_t occ_fe_cells(int cb, int *blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fe_cell_kernel<T, N, CURVED>, cb * N * N,
+                                                       (size_t)cb * 4 * Tile<N>::T3 * sizeof(T));
+}
+
 template <typename T, int N>
 static cudaError_t prep_fe_n() {
-  constexpr int CB = default_cb(N);
-  const int smem = CB * 4 * Tile<N>::T3 * (int)sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(fe_cell_kernel<T, N, false, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem = max_cb(N, sizeof(T)) * 4 * Tile<N>::T3 * (int)sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(fe_cell_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fe_cell_kernel<T, N, true, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(fe_cell_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t prepare_fe_kernels() {
@@ -442,7 +687,7 @@ static cudaError_t run_fe_diag(const FEArgs<double> &a, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_fe_cells(int n, bool curved, const FEArgs<T> &a, bool diag_only, cudaStream_t s) {
+cudaError_t launch_fe_cells(int n, bool curved, const FEArgs<T> &a, bool diag_only, cudaStream_t s, int cb) {
 #define SIPG_FE_CASE(NN)                                                                     \
   case NN:                                                                                   \
     if (diag_only) {                                                                         \
@@ -450,7 +695,7 @@ cudaError_t launch_fe_cells(int n, bool curved, const FEArgs<T> &a, bool diag_on
         return curved ? run_fe_diag<NN, true>(a, s) : run_fe_diag<NN, false>(a, s);          \
       return cudaErrorInvalidValue;                                                          \
     }                                                                                        \
-    return curved ? run_fe_cells<T, NN, true>(a, s) : run_fe_cells<T, NN, false>(a, s);
+    return curved ? run_fe_cells<T, NN, true>(a, s, cb) : run_fe_cells<T, NN, false>(a, s, cb);
   switch (n) {
     SIPG_FE_CASE(2)
     SIPG_FE_CASE(3)
@@ -466,21 +711,100 @@ cudaError_t launch_fe_cells(int n, bool curved, const FEArgs<T> &a, bool diag_on
 #undef SIPG_FE_CASE
 }
 
+template <int N, bool CURVED>
+static cudaError_t run_fe_stencil_setup(const FEArgs<double> &a, double *coef, cudaStream_t s) {
+  constexpr int N3 = N * N * N;
+  const Rules1D &r = rules(N);
+  double *tabs = nullptr, *K = nullptr;
+  cudaError_t e = cudaMalloc(&tabs, 2 * N * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&K, std::max<size_t>(1, (size_t)a.ncells * N3 * N3) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tabs, r.S.data(), N * N * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tabs + N * N, r.Sd.data(), N * N * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && a.ncells > 0) {
+    fe_elem_matrix_kernel<N, CURVED><<<a.ncells, 128, 0, s>>>(a, tabs, tabs + N * N, K);
+    note_launch();
+    const long w = 2 * (N - 1) + 1;
+    const long total = (long)a.grid[0] * a.grid[1] * a.grid[2] * w * w * w;
+    fe_stencil_assemble_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a, K, coef);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(K);
+  cudaFree(tabs);
+  return e;
+}
+
+cudaError_t launch_fe_stencil_setup(bool curved, const FEArgs<double> &a, double *coef, cudaStream_t s) {
+  switch (a.deg) {
+    case 1:
+      return curved ? run_fe_stencil_setup<2, true>(a, coef, s) : run_fe_stencil_setup<2, false>(a, coef, s);
+    case 2:
+      return curved ? run_fe_stencil_setup<3, true>(a, coef, s) : run_fe_stencil_setup<3, false>(a, coef, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
-cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s) {
+cudaError_t launch_fe_stencil_apply(const FEArgs<T> &a, const T *coef, cudaStream_t s) {
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
-  const int bs = 256;
-  fe_gather_kernel<T><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(a);
+  const int bs = 128;
+  if (total == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((total + bs - 1) / bs), a.nv);
+  if (a.deg == 1)
+    fe_stencil_apply_kernel<T, 1><<<grid, bs, 0, s>>>(a, coef);
+  else if (a.deg == 2)
+    fe_stencil_apply_kernel<T, 2><<<grid, bs, 0, s>>>(a, coef);
+  else
+    return cudaErrorInvalidValue;
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_c_prolongate_add(const FEArgs<T> &a, const T *xc, T *xdg, cudaStream_t s) {
+int fe_max_cells_per_block(int n) {
+  return max_cb(n, sizeof(T));
+}
+
+template <typename T>
+cudaError_t fe_blocks_per_sm(int n, bool curved, int cb, int *blocks) {
+#define SIPG_FE_OCC(NN) \
+  case NN:              \
+    return curved ? occ_fe_cells<T, NN, true>(cb, blocks) : occ_fe_cells<T, NN, false>(cb, blocks);
+  switch (n) {
+    SIPG_FE_OCC(2)
+    SIPG_FE_OCC(3)
+    SIPG_FE_OCC(4)
+    SIPG_FE_OCC(5)
+    SIPG_FE_OCC(6)
+    SIPG_FE_OCC(7)
+    SIPG_FE_OCC(8)
+    SIPG_FE_OCC(9)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SIPG_FE_OCC
+}
+
+template <typename T>
+cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s) {
+  const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
+  const int bs = 256;
+  if (total == 0) return cudaSuccess;
+  fe_gather_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), a.nv), bs, 0, s>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_c_prolongate_add(const FEArgs<T> &a, const T *xc, T *xdg, cudaStream_t s, int64_t dg_stride) {
   const int n = a.deg + 1;
   const long total = (long)a.ncells * n * n * n;
   const int bs = 256;
-  c_prolongate_add_kernel<T><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(a, xc, xdg);
+  if (total == 0) return cudaSuccess;
+  c_prolongate_add_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), a.nv), bs, 0, s>>>(a, xc, xdg, dg_stride);
   note_launch();
   return cudaGetLastError();
 }
@@ -489,7 +813,35 @@ template <typename T>
 cudaError_t launch_fe_prolongate_add(const XferGeom &g, const T *P1, const T *xc, T *xf, cudaStream_t s) {
   const long total = (long)g.gf[0] * g.gf[1] * g.gf[2];
   const int bs = 256;
-  fe_prolongate_add_kernel<T><<<(int)((total + bs - 1) / bs), bs, 0, s>>>(g, P1, xc, xf);
+  if (total == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((total + bs - 1) / bs), g.nv);
+  switch (g.pc + 1) {
+    case 2:
+      fe_prolongate_add_kernel<T, 2><<<grid, bs, 0, s>>>(g, P1, xc, xf);
+      break;
+    case 3:
+      fe_prolongate_add_kernel<T, 3><<<grid, bs, 0, s>>>(g, P1, xc, xf);
+      break;
+    case 4:
+      fe_prolongate_add_kernel<T, 4><<<grid, bs, 0, s>>>(g, P1, xc, xf);
+      break;
+    case 5:
+      fe_prolongate_add_kernel<T, 5><<<grid, bs, 0, s>>>(g, P1, xc, xf);
+      break;
+    default:
+      fe_prolongate_add_kernel<T, 0><<<grid, bs, 0, s>>>(g, P1, xc, xf);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fe_restrict_nodes(const XferGeom &g, const T *P1, const T *rf, T *rc, cudaStream_t s) {
+  if (!fe_restrict_nodes_ok(g)) return cudaErrorInvalidValue;
+  const long total = (long)g.gc[0] * g.gc[1] * g.gc[2];
+  const int bs = 128;
+  if (total == 0) return cudaSuccess;
+  fe_restrict_nodes_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), g.nv), bs, 0, s>>>(g, P1, rf, rc);
   note_launch();
   return cudaGetLastError();
 }
@@ -500,7 +852,7 @@ cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf
   const long ncc = (long)g.mc[0] * g.mc[1] * g.mc[2];
   const size_t smem = (size_t)(nf * nf * nf + nf * nf * nc + nf * nc * nc + nc * nc * nc) * sizeof(T);
   if (ncc == 0) return cudaSuccess;
-  fe_restrict_cells_kernel<T><<<(int)ncc, 128, smem, s>>>(g, P1, rf, ebuf);
+  fe_restrict_cells_kernel<T><<<dim3((unsigned)ncc, g.nv), 128, smem, s>>>(g, P1, rf, ebuf);
   note_launch();
   return cudaGetLastError();
 }
@@ -513,18 +865,23 @@ cudaError_t launch_dg_transfer(const XferGeom &g, const T *P1, const T *in, T *o
   const long ncc = (long)g.mc[0] * g.mc[1] * g.mc[2];
   if (ncc == 0) return cudaSuccess;
   if (prolong)
-    dg_transfer_kernel<T, true><<<(int)ncc, 128, smem, s>>>(g, P1, in, out);
+    dg_transfer_kernel<T, true><<<dim3((unsigned)ncc, g.nv), 128, smem, s>>>(g, P1, in, out);
   else
-    dg_transfer_kernel<T, false><<<(int)ncc, 128, smem, s>>>(g, P1, in, out);
+    dg_transfer_kernel<T, false><<<dim3((unsigned)ncc, g.nv), 128, smem, s>>>(g, P1, in, out);
   note_launch();
   return cudaGetLastError();
 }
 
 #define SIPG_FE_INST(T)                                                                                   \
-  template cudaError_t launch_fe_cells<T>(int, bool, const FEArgs<T> &, bool, cudaStream_t);            \
+  template cudaError_t launch_fe_cells<T>(int, bool, const FEArgs<T> &, bool, cudaStream_t, int);       \
+  template int fe_max_cells_per_block<T>(int);                                                          \
+  template cudaError_t fe_blocks_per_sm<T>(int, bool, int, int *);                                      \
   template cudaError_t launch_fe_gather<T>(const FEArgs<T> &, cudaStream_t);                            \
-  template cudaError_t launch_c_prolongate_add<T>(const FEArgs<T> &, const T *, T *, cudaStream_t);     \
+  template cudaError_t launch_fe_stencil_apply<T>(const FEArgs<T> &, const T *, cudaStream_t);          \
+  template cudaError_t launch_c_prolongate_add<T>(const FEArgs<T> &, const T *, T *, cudaStream_t, int64_t); \
   template cudaError_t launch_fe_prolongate_add<T>(const XferGeom &, const T *, const T *, T *,         \
+                                                   cudaStream_t);                                       \
+  template cudaError_t launch_fe_restrict_nodes<T>(const XferGeom &, const T *, const T *, T *,         \
                                                    cudaStream_t);                                       \
   template cudaError_t launch_fe_restrict_cells<T>(const XferGeom &, const T *, const T *, T *,         \
                                                    cudaStream_t);                                       \

@@ -68,6 +68,11 @@ struct DGArgs {
   int mode;
   const T *x, *xp, *b, *dinv;
   T c1, c2, c3;
+  // nv vectors of one operator at once (right-hand sides): vector r of u,
+  // out, x, xp, b starts at r * vs, its scratch at r * gs (grad) and r * ts
+  // (trace); dinv and the geometry are shared
+  int nv = 1;
+  int64_t vs = 0, gs = 0, ts = 0;
 };
 
 // Arguments of the FE cell pass and the node gather pass.
@@ -87,6 +92,10 @@ struct FEArgs {
                        //         4 diagonal (sum, constrained -> 1)
   const T *x, *xp, *b, *dinv;
   T c1, c2, c3;
+  // nv vectors at once: vector r of u, out, x, xp, b starts at r * vs, its
+  // element buffer at r * es
+  int nv = 1;
+  int64_t vs = 0, es = 0;
 };
 
 // One multigrid level.
@@ -106,6 +115,12 @@ struct Level {
   void *tau[2] = {nullptr, nullptr};
   void *dinv[2] = {nullptr, nullptr};
   double lambda = 0;
+  // cells per thread block of the cell kernels, [precision][DG evaluation,
+  // DG integration, FE cells]; 0 = compiled default (set by the autotuner)
+  int cb[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  // FE levels of low degree: assembled stencil [(2p+1)^3][nodes] in both
+  // precisions (nullptr: matrix-free)
+  void *stencil[2] = {nullptr, nullptr};
   // transfer from level l-1 (coarser) to this level
   int t_kind = -1;      // 0 c-transfer, 1 FE p, 2 FE h, 3 DG p, 4 DG h
   void *P1[2] = {nullptr, nullptr};   // [2 children][nf][nc] interpolation tables
@@ -128,29 +143,58 @@ template <typename T>
 cudaError_t launch_dg_integrate(int n, bool curved, const DGArgs<T> &a, cudaStream_t s, int cb = 0);
 template <typename T>
 int dg_cells_per_block(int n);
+template <typename T>
+int dg_max_cells_per_block(int n);
+// resident blocks per SM of a DG pass (0 evaluation, 1 integration) at cb cells per block
+template <typename T>
+cudaError_t dg_blocks_per_sm(int n, bool curved, int pass, int cb, int *blocks);
 
 cudaError_t launch_dg_diag(int n, bool curved, const DGArgs<double> &a, double *diag, cudaStream_t s);
 
+// FE cell pass at cb cells per block (0 = default); diag_only: the cell-local
+// diagonal (setup, FP64)
 template <typename T>
-cudaError_t launch_fe_cells(int n, bool curved, const FEArgs<T> &a, bool diag_only, cudaStream_t s);
+cudaError_t launch_fe_cells(int n, bool curved, const FEArgs<T> &a, bool diag_only, cudaStream_t s, int cb = 0);
+template <typename T>
+int fe_max_cells_per_block(int n);
+template <typename T>
+cudaError_t fe_blocks_per_sm(int n, bool curved, int cb, int *blocks);
 template <typename T>
 cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s);
+// Assembled stencil of an FE level of degree 1 or 2 (setup, FP64):
+// coef[o][node], o over the (2p+1)^3 offsets, x fastest
+cudaError_t launch_fe_stencil_setup(bool curved, const FEArgs<double> &a, double *coef, cudaStream_t s);
+// the level operator from its stencil with the gather's epilogue (modes 0-2)
+template <typename T>
+cudaError_t launch_fe_stencil_apply(const FEArgs<T> &a, const T *coef, cudaStream_t s);
 
 // Transfers.  For the c-transfer the coarse space is the FE space on the same
 // mesh with the same degree: prolongation injects, restriction sums duplicates.
+// (nv vectors: xc at r * fe.vs, xdg at r * dg_stride)
 template <typename T>
-cudaError_t launch_c_prolongate_add(const FEArgs<T> &fe, const T *xc, T *xdg, cudaStream_t s);
+cudaError_t launch_c_prolongate_add(const FEArgs<T> &fe, const T *xc, T *xdg, cudaStream_t s, int64_t dg_stride = 0);
 struct XferGeom {
   int kind;             // 1 FE p, 2 FE h, 3 DG p, 4 DG h
   int mf[3], mc[3];     // cells of fine and coarse mesh
   int pf, pc;           // degrees
   int gf[3], gc[3];     // node grids
   int bc[6];
+  // nv vectors at once: vector r of the fine / coarse vector starts at r * sf
+  // / r * sc, of the coarse element buffer at r * se
+  int nv = 1;
+  int64_t sf = 0, sc = 0, se = 0;
 };
 template <typename T>
 cudaError_t launch_fe_prolongate_add(const XferGeom &g, const T *P1, const T *xc, T *xf, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf, T *ebuf_c, cudaStream_t s);
+// node-by-node restriction r_c = P^T r_f in one launch, for the transfers
+// degree 2 -> 1 on one mesh and degree 1 across a 2:1 refinement
+inline bool fe_restrict_nodes_ok(const XferGeom &g) {
+  return (g.kind == 1 && g.pf == 2 && g.pc == 1) || (g.kind == 2 && g.pf == 1 && g.pc == 1);
+}
+template <typename T>
+cudaError_t launch_fe_restrict_nodes(const XferGeom &g, const T *P1, const T *rf, T *rc, cudaStream_t s);
 // DG -> DG transfers (kind 3 p, 4 h): prolong: out += P in; else out = P^T in
 template <typename T>
 cudaError_t launch_dg_transfer(const XferGeom &g, const T *P1, const T *in, T *out, bool prolong, cudaStream_t s);
@@ -164,7 +208,8 @@ template <typename T>
 cudaError_t launch_axpy(T *y, T a, const T *x, int64_t n, cudaStream_t s);   // y += a x
 cudaError_t launch_invert(double *d, int64_t n, cudaStream_t s);
 template <typename T>
-cudaError_t launch_xdb(T *x, T c, const T *dinv, const T *b, int64_t n, cudaStream_t s);   // x = c dinv b
+cudaError_t launch_xdb(T *x, T c, const T *dinv, const T *b, int64_t n, cudaStream_t s,
+                      int nv = 1);   // x = c dinv b, nv vectors of length n (dinv shared)
 template <typename T>
 cudaError_t launch_xpby(T *p, const T *z, T beta, int64_t n, cudaStream_t s);              // p = z + beta p
 // deterministic dot products into device scalars: out[0] = x.y (and out[1] = z.w if z)
@@ -176,7 +221,7 @@ cudaError_t launch_fcg_update_xr(double *x, double *r, const double *p, const do
                                  cudaStream_t s);
 cudaError_t launch_fcg_update_p(double *p, const double *z, const double *sc, int64_t n, cudaStream_t s);
 template <typename Tb, typename Tx>
-cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cudaStream_t s);
+cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cudaStream_t s, int nv = 1);
 
 cudaError_t fma_peak(int precision, cudaStream_t s, double *flops);
 
@@ -217,6 +262,7 @@ template <typename T>
 void batch_plan_free(BatchPlan<T> &P);
 template <typename T>
 cudaError_t batch_apply(BatchPlan<T> &P, cudaStream_t s);
+constexpr int kSegBlocksHost = 32;   // blocks per system in the batched reductions (batch.cu)
 constexpr int kSegSlots = 8;   // scalar slots per problem (FCG layout of solver.cu, 4: b.b, 5: r0.r0)
 cudaError_t seg_dot(const Seg *segs, int np, int which, double *partials, unsigned *counter, double *sc,
                     int sc_stride, int slot, cudaStream_t s);

@@ -39,9 +39,6 @@ struct sipg_ctx {
   // fr and writing fz; captured on the second use, replayed afterwards
   cudaGraphExec_t vgraph[2] = {nullptr, nullptr};
   int vcalls[2] = {0, 0};
-  // cells per thread block of the finest-level DG passes, [precision][eval, integrate]
-  // (0 = compiled default; set by the autotuner)
-  int cb[2][2] = {{0, 0}, {0, 0}};
   // learned smoother of the finest level (see "learned smoother" below)
   struct Net {
     bool ready = false;    // weights allocated
@@ -59,6 +56,23 @@ struct sipg_ctx {
     double rho_cheb = 1.0;  // average rate of the Chebyshev cycle (judge of the learned one)
     int steps_pre = 2, steps_post = 2;
   } net;
+  // Several right-hand sides at once (sipg_solve_multi, sipg_operator_apply_multi):
+  // nv vectors of every level's V-cycle data and of the cell-kernel scratch,
+  // vector r of a level at r * (that level's length).  nv = 1 uses the
+  // single-vector buffers above.
+  int nv = 1;
+  struct Multi {
+    int cap = 0;                               // vectors allocated
+    std::vector<void *> v;                     // [level][vb, vx, vr, vt], V-cycle precision
+    void *grad[2] = {nullptr, nullptr}, *trace[2] = {nullptr, nullptr}, *ebuf[2] = {nullptr, nullptr};
+    double *r = nullptr, *z = nullptr, *p = nullptr, *v_ = nullptr;   // flexible-CG vectors
+    std::vector<Seg> segs;
+    Seg *d_segs = nullptr;
+    double *sc = nullptr, *partials = nullptr;
+    unsigned *counters = nullptr;
+    cudaGraphExec_t graph = nullptr;           // V-cycle of graph_nv vectors
+    int graph_nv = 0, calls = 0;
+  } mv;
   int smoother = 0;          // 0 Chebyshev, 1 learned (finest level)
   int use_learned = 0;       // current cycle uses the learned smoother
   cudaGraphExec_t vgraph_l[2] = {nullptr, nullptr};   // graphs of the learned cycle
@@ -134,8 +148,12 @@ template <typename T>
 DGArgs<T> dg_args(sipg_ctx *c, const Level &L) {
   constexpr int pi = pidx<T>();
   DGArgs<T> a{};
-  a.grad = (T *)c->dg_grad[pi];
-  a.trace = (T *)c->dg_trace[pi];
+  a.grad = (T *)(c->nv > 1 ? c->mv.grad[pi] : c->dg_grad[pi]);
+  a.trace = (T *)(c->nv > 1 ? c->mv.trace[pi] : c->dg_trace[pi]);
+  a.nv = c->nv;
+  a.vs = L.ndofs;
+  a.gs = L.ncells * 3 * (int64_t)L.n * L.n * L.n;
+  a.ts = L.ncells * 12 * (int64_t)L.n * L.n;
   a.metric = (const T *)L.metric[pi];
   a.wcart = (const T *)L.wcart[pi];
   for (int d = 0; d < 3; ++d) {
@@ -158,7 +176,10 @@ template <typename T>
 FEArgs<T> fe_args(sipg_ctx *c, const Level &L) {
   constexpr int pi = pidx<T>();
   FEArgs<T> a{};
-  a.ebuf = (T *)c->ebuf[pi];
+  a.ebuf = (T *)(c->nv > 1 ? c->mv.ebuf[pi] : c->ebuf[pi]);
+  a.nv = c->nv;
+  a.vs = L.ndofs;
+  a.es = L.ncells * (int64_t)L.n * L.n * L.n;
   a.metric = (const T *)L.metric[pi];
   a.wcart = (const T *)L.wcart[pi];
   a.deg = L.deg;
@@ -188,9 +209,8 @@ void apply_level(sipg_ctx *c, int l, const T *u, T *out, int mode, const T *x = 
     a.c1 = c1;
     a.c2 = c2;
     a.c3 = c3;
-    const int fine = (l == c->L);
-    CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, fine ? c->cb[pidx<T>()][0] : 0));
-    CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream, fine ? c->cb[pidx<T>()][1] : 0));
+    CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, L.cb[pidx<T>()][0]));
+    CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream, L.cb[pidx<T>()][1]));
   } else {
     FEArgs<T> a = fe_args<T>(c, L);
     a.u = u;
@@ -203,8 +223,12 @@ void apply_level(sipg_ctx *c, int l, const T *u, T *out, int mode, const T *x = 
     a.c1 = c1;
     a.c2 = c2;
     a.c3 = c3;
-    CK(launch_fe_cells<T>(L.n, L.curved, a, false, c->stream));
-    CK(launch_fe_gather<T>(a, c->stream));
+    if (L.stencil[pidx<T>()]) {
+      CK(launch_fe_stencil_apply<T>(a, (const T *)L.stencil[pidx<T>()], c->stream));
+    } else {
+      CK(launch_fe_cells<T>(L.n, L.curved, a, false, c->stream, L.cb[pidx<T>()][2]));
+      CK(launch_fe_gather<T>(a, c->stream));
+    }
   }
 }
 
@@ -221,6 +245,10 @@ XferGeom xfer(sipg_ctx *c, int l) {
   g.pf = F.deg;
   g.pc = C.deg;
   for (int s = 0; s < 6; ++s) g.bc[s] = c->mesh.bc[s];
+  g.nv = c->nv;
+  g.sf = F.ndofs;
+  g.sc = C.ndofs;
+  g.se = C.ncells * (int64_t)C.n * C.n * C.n;
   return g;
 }
 
@@ -233,13 +261,18 @@ void restrict_level(sipg_ctx *c, int l, const T *r, T *rc) {
     CK(launch_dg_transfer<T>(xfer(c, l), (const T *)F.P1[pi], r, rc, false, c->stream));
     return;
   }
+  if (F.t_kind != 0 && fe_restrict_nodes_ok(xfer(c, l))) {   // small transfer: one node pass
+    CK(launch_fe_restrict_nodes<T>(xfer(c, l), (const T *)F.P1[pi], r, rc, c->stream));
+    return;
+  }
   FEArgs<T> a = fe_args<T>(c, c->lv[l - 1]);
   a.mode = 3;
   a.out = rc;
   if (F.t_kind == 0) {
     a.ebuf = const_cast<T *>(r);   // the DG vector is the element buffer of the FE level
   } else {
-    CK(launch_fe_restrict_cells<T>(xfer(c, l), (const T *)F.P1[pi], r, (T *)c->ebuf[pi], c->stream));
+    CK(launch_fe_restrict_cells<T>(xfer(c, l), (const T *)F.P1[pi], r,
+                                   (T *)(c->nv > 1 ? c->mv.ebuf[pi] : c->ebuf[pi]), c->stream));
   }
   CK(launch_fe_gather<T>(a, c->stream));
 }
@@ -253,7 +286,7 @@ void prolongate_level(sipg_ctx *c, int l, const T *xc, T *x) {
     CK(launch_dg_transfer<T>(xfer(c, l), (const T *)F.P1[pi], xc, x, true, c->stream));
   } else if (F.t_kind == 0) {
     FEArgs<T> a = fe_args<T>(c, c->lv[l - 1]);
-    CK(launch_c_prolongate_add<T>(a, xc, x, c->stream));
+    CK(launch_c_prolongate_add<T>(a, xc, x, c->stream, F.ndofs));
   } else {
     CK(launch_fe_prolongate_add<T>(xfer(c, l), (const T *)F.P1[pi], xc, x, c->stream));
   }
@@ -271,7 +304,7 @@ void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_
   const double theta = 0.5 * (lhi + llo), delta = 0.5 * (lhi - llo);
   bool have_prev;
   if (zero_start) {
-    CK(launch_xdb<T>(x, (T)(1.0 / theta), dinv, b, L.ndofs, c->stream));
+    CK(launch_xdb<T>(x, (T)(1.0 / theta), dinv, b, L.ndofs, c->stream, c->nv));
     have_prev = false;   // x_0 = 0
   } else {
     apply_level<T>(c, l, x, xt, 1, x, nullptr, b, dinv, T(1), T(0), (T)(1.0 / theta));
@@ -295,22 +328,29 @@ void learned_smooth(sipg_ctx *c, const T *b, T *x, int steps, bool zero_start);
 // Algorithm 2 with x^(l) = 0 on entry: rhs in lv[l].vb; returns the buffer
 // (vx or vt of that level) that holds x^(l).  No state changes between calls,
 // so the whole cycle can be captured once and replayed.
+// V-cycle vector k (0 vb, 1 vx, 2 vr, 3 vt) of level l in the current work set
+template <typename T>
+T *lvec(sipg_ctx *c, int l, int k) {
+  if (c->nv > 1) return (T *)c->mv.v[4 * l + k];
+  const Level &L = c->lv[l];
+  void *const *v[4] = {L.vb, L.vx, L.vr, L.vt};
+  return (T *)v[k][pidx<T>()];
+}
+
 template <typename T>
 T *vcycle_rec(sipg_ctx *c, int l) {
-  constexpr int pi = pidx<T>();
-  Level &L = c->lv[l];
-  T *b = (T *)L.vb[pi];
+  T *b = lvec<T>(c, l, 0);
   if (l == 0) {
-    CK((launch_dense_gemv<T, T>(c->Ainv, b, (T *)L.vx[pi], c->n0, c->stream)));
-    return (T *)L.vx[pi];
+    CK((launch_dense_gemv<T, T>(c->Ainv, b, lvec<T>(c, l, 1), c->n0, c->stream, c->nv)));
+    return lvec<T>(c, l, 1);
   }
-  T *x = (T *)L.vx[pi], *xt = (T *)L.vt[pi];
+  T *x = lvec<T>(c, l, 1), *xt = lvec<T>(c, l, 3);
   const int ns = c->prm.cheb_degree;
   const bool learned = (l == c->L) && c->use_learned;
   if (learned) learned_smooth<T>(c, b, x, c->net.steps_pre, true);
   else chebyshev<T>(c, l, b, x, xt, ns, true);
-  apply_level<T>(c, l, x, (T *)L.vr[pi], 2, nullptr, nullptr, b);
-  restrict_level<T>(c, l, (const T *)L.vr[pi], (T *)c->lv[l - 1].vb[pi]);
+  apply_level<T>(c, l, x, lvec<T>(c, l, 2), 2, nullptr, nullptr, b);
+  restrict_level<T>(c, l, lvec<T>(c, l, 2), lvec<T>(c, l - 1, 0));
   const T *xc = vcycle_rec<T>(c, l - 1);
   prolongate_level<T>(c, l, xc, x);
   if (learned) learned_smooth<T>(c, b, x, c->net.steps_post, false);
@@ -320,15 +360,15 @@ T *vcycle_rec(sipg_ctx *c, int l) {
 
 // z = M^-1 r with FP64 vectors in and out
 void vcycle_body(sipg_ctx *c, const double *r, double *z) {
-  Level &F = c->lv[c->L];
+  const int64_t n = c->lv[c->L].ndofs * c->nv;
   if (c->prm.precision == 0) {
-    CK(cudaMemcpyAsync(F.vb[0], r, F.ndofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(lvec<double>(c, c->L, 0), r, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     const double *x = vcycle_rec<double>(c, c->L);
-    CK(cudaMemcpyAsync(z, x, F.ndofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(z, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   } else {
-    CK((launch_cast<float, double>((float *)F.vb[1], r, F.ndofs, c->stream)));
+    CK((launch_cast<float, double>(lvec<float>(c, c->L, 0), r, n, c->stream)));
     const float *x = vcycle_rec<float>(c, c->L);
-    CK((launch_cast<double, float>(z, x, F.ndofs, c->stream)));
+    CK((launch_cast<double, float>(z, x, n, c->stream)));
   }
 }
 
@@ -341,19 +381,33 @@ void precondition(sipg_ctx *c) {
   const int pi = c->prm.precision;
   cudaGraphExec_t *gslot = c->use_learned ? &c->vgraph_l[pi] : &c->vgraph[pi];
   int *calls = c->use_learned ? &c->vcalls_l[pi] : &c->vcalls[pi];
+  const double *r = c->fr;
+  double *z = c->fz;
+  if (c->nv > 1) {   // the multi-vector cycle on the multi-vector flexible-CG vectors
+    if (c->mv.graph && c->mv.graph_nv != c->nv) {
+      cudaGraphExecDestroy(c->mv.graph);
+      c->mv.graph = nullptr;
+      c->mv.calls = 0;
+    }
+    c->mv.graph_nv = c->nv;
+    gslot = &c->mv.graph;
+    calls = &c->mv.calls;
+    r = c->mv.r;
+    z = c->mv.z;
+  }
   if (*gslot) {
     CK(cudaGraphLaunch(*gslot, c->stream));
     note_launch();
     return;
   }
   if (c->stream == nullptr || (*calls)++ < 1) {
-    vcycle_body(c, c->fr, c->fz);
+    vcycle_body(c, r, z);
     return;
   }
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   try {
-    vcycle_body(c, c->fr, c->fz);
+    vcycle_body(c, r, z);
   } catch (...) {
     cudaStreamEndCapture(c->stream, &g);
     if (g) cudaGraphDestroy(g);
@@ -470,47 +524,84 @@ void alloc_work(sipg_ctx *c, Level &L) {
   }
 }
 
-// Tile-shape autotuner: for each precision and each DG pass of the finest
-// level, time the compiled cells-per-block variants on this operator and keep
-// the fastest.  Results are cached per (n, geometry, precision, pass) for the
-// process, so batches of equal degrees tune once.
+// Tile-shape autotuner.  A cell kernel's block width cb (cells per block)
+// fixes how many cells an SM holds at once (the occupancy calculator's
+// resident blocks times cb) and hence how full the last wave of blocks is.
+// The candidates are the widths whose waves leave the fewest cell slots
+// idle (weighted by the share of live lanes in the block's last warp), plus
+// the compiled default; each is timed on the level and the fastest kept.
+// Results are cached per (n, geometry, precision, pass, cells) for the
+// process, so contexts and batch members of equal shape tune once.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tune;
+std::map<std::tuple<int, int, int, int, int64_t>, int> g_tune;
 
 template <typename T>
-void autotune_pass(sipg_ctx *c, int pass) {
+std::vector<int> tile_candidates(const Level &L, int pass, int keep) {
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int maxcb = pass < 2 ? dg_max_cells_per_block<T>(L.n) : fe_max_cells_per_block<T>(L.n);
+  std::vector<std::pair<double, int>> score;
+  for (int cb = 1; cb <= maxcb; ++cb) {
+    int occ = 0;
+    CK(pass < 2 ? dg_blocks_per_sm<T>(L.n, L.curved, pass, cb, &occ) : fe_blocks_per_sm<T>(L.n, L.curved, cb, &occ));
+    if (occ <= 0) continue;
+    const int threads = cb * L.n * L.n;
+    const double lanes = threads / (32.0 * ((threads + 31) / 32));
+    const int64_t slots = (int64_t)occ * nsm, groups = (L.ncells + cb - 1) / cb;
+    const int64_t waves = (groups + slots - 1) / slots;
+    score.push_back({(double)L.ncells / ((double)waves * slots * cb) * lanes, cb});
+  }
+  std::stable_sort(score.begin(), score.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+  std::vector<int> out{dg_cells_per_block<T>(L.n)};
+  for (const auto &sc : score) {
+    if ((int)out.size() > keep) break;
+    if (std::find(out.begin(), out.end(), sc.second) == out.end()) out.push_back(sc.second);
+  }
+  return out;
+}
+
+template <typename T>
+void autotune_level(sipg_ctx *c, int l, int pass) {
   constexpr int pi = pidx<T>();
-  const Level &L = c->lv[c->L];
-  const auto key = std::make_tuple(L.n, (int)L.curved, pi, pass);
+  Level &L = c->lv[l];
+  const auto key = std::make_tuple(L.n, (int)L.curved, pi, pass, L.ncells);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      c->cb[pi][pass] = it->second;
+      L.cb[pi][pass] = it->second;
       return;
     }
   }
-  const int D = dg_cells_per_block<T>(L.n);
-  std::vector<int> cands{D, (D + 1) / 2, 2 * D, 1};
-  std::sort(cands.begin(), cands.end());
-  cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
-  T *u = dalloc<T>(c, L.ndofs), *v = dalloc<T>(c, L.ndofs);
-  CK(cudaMemsetAsync(u, 0, L.ndofs * sizeof(T), c->stream));
-  DGArgs<T> a = dg_args<T>(c, L);
-  a.u = u;
-  a.out = v;
-  a.mode = 0;
+  const std::vector<int> cands = tile_candidates<T>(L, pass, 4);
+  const int64_t len = pass < 2 ? L.ndofs : (int64_t)L.grid[0] * L.grid[1] * L.grid[2];
+  T *u = dalloc<T>(c, len), *v = dalloc<T>(c, L.ncells * (int64_t)L.n * L.n * L.n);
+  CK(cudaMemsetAsync(u, 0, len * sizeof(T), c->stream));
+  DGArgs<T> a{};
+  FEArgs<T> f{};
+  if (pass < 2) {
+    a = dg_args<T>(c, L);
+    a.u = u;
+    a.out = v;
+    a.mode = 0;
+  } else {
+    f = fe_args<T>(c, L);
+    f.u = u;
+    f.ebuf = v;   // the cell pass writes ncells n^3 values: the DG length of this mesh
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_cb = D;
+  int best_cb = cands[0];
   for (int cb : cands) {
     auto run = [&]() {
       if (pass == 0) CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, cb));
-      else CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream, cb));
+      else if (pass == 1) CK(launch_dg_integrate<T>(L.n, L.curved, a, c->stream, cb));
+      else CK(launch_fe_cells<T>(L.n, L.curved, f, false, c->stream, cb));
     };
-    CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, 0));   // valid scratch for the integration pass
+    if (pass == 1) CK(launch_dg_eval<T>(L.n, L.curved, a, c->stream, 0));   // valid scratch for the integration
     run();
     CK(cudaEventRecord(e0, c->stream));
     const int reps = 5;
@@ -526,7 +617,7 @@ void autotune_pass(sipg_ctx *c, int pass) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->cb[pi][pass] = best_cb;
+  L.cb[pi][pass] = best_cb;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best_cb;
 }
@@ -662,9 +753,14 @@ void setup(sipg_ctx *c) {
   c->dg_trace[1] = dalloc<float>(c, dg_trace_len);
   CK(cudaDeviceSynchronize());   // geometry uploads (legacy stream) complete before stream work
   if (P.autotune) {
-    for (int pass = 0; pass < 2; ++pass) {
-      autotune_pass<double>(c, pass);
-      autotune_pass<float>(c, pass);
+    // the finest DG level always; the other cell-kernel levels of the solver
+    for (int l = c->solver ? 1 : c->L; l <= c->L; ++l) {
+      const int k = c->lv[l].kind;
+      if (k == 1 && c->lv[l].deg <= P.fe_assemble) continue;   // assembled stencil: no cell pass to tune
+      for (int pass = k == 0 ? 0 : 2; pass <= (k == 0 ? 1 : 2); ++pass) {
+        autotune_level<double>(c, l, pass);
+        autotune_level<float>(c, l, pass);
+      }
     }
   }
   c->scal = dalloc<double>(c, 64);
@@ -677,6 +773,20 @@ void setup(sipg_ctx *c) {
   }
   c->ebuf[0] = dalloc<double>(c, ebuf_len);
   c->ebuf[1] = dalloc<float>(c, ebuf_len);
+  // assembled stencils of the low-degree FE levels that get smoothed
+  if (P.fe_assemble < 0 || P.fe_assemble > 2) throw_inval("fe_assemble must be 0, 1 or 2");
+  for (int l = 1; l < nl; ++l) {
+    Level &L = c->lv[l];
+    if (L.kind != 1 || L.deg > P.fe_assemble) continue;
+    const int w = 2 * L.deg + 1;
+    const int64_t len = (int64_t)w * w * w * L.ndofs;
+    double *cd = dalloc<double>(c, len);
+    float *cf = dalloc<float>(c, len);
+    CK(launch_fe_stencil_setup(L.curved, fe_args<double>(c, L), cd, c->stream));
+    CK((launch_cast<float, double>(cf, cd, len, c->stream)));
+    L.stencil[0] = cd;
+    L.stencil[1] = cf;
+  }
   // inverse diagonals
   for (int l = 1; l < nl; ++l) {
     Level &L = c->lv[l];
@@ -731,9 +841,17 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
-  // r = b - A x
-  apply_level<double>(c, c->L, x, c->fr, 2, nullptr, nullptr, b);
-  const double bn = std::sqrt(dot(c, b, b, N, 4));
+  // ||b||^2 and ||x||^2 in one pass; r = b - A x, or r = b for a zero start
+  // vector (no operator application)
+  CK(launch_dot2(b, b, x, x, N, c->partials, c->counter, c->scal + 4, s));
+  double bx[2];
+  CK(cudaMemcpyAsync(bx, c->scal + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bx[1] == 0.0)
+    CK(cudaMemcpyAsync(c->fr, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else
+    apply_level<double>(c, c->L, x, c->fr, 2, nullptr, nullptr, b);
+  const double bn = std::sqrt(bx[0]);
   if (!std::isfinite(bn)) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1105,6 +1223,7 @@ void sipg_default_params(sipg_params *p) {
   p->smoother = 0;
   p->operator_only = 0;
   std::strcpy(p->coarsening, "cph");
+  p->fe_assemble = 1;
   p->stream = nullptr;
 }
 
@@ -1153,6 +1272,7 @@ sipg_status sipg_destroy(sipg_ctx *c) {
     if (g) cudaGraphExecDestroy(g);
   for (auto &g : c->vgraph_l)
     if (g) cudaGraphExecDestroy(g);
+  if (c->mv.graph) cudaGraphExecDestroy(c->mv.graph);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
   return SIPG_OK;
@@ -1336,16 +1456,16 @@ sipg_status sipg_time_apply(sipg_ctx *c, int precision, const void *u, void *v, 
         DGArgs<double> a = dg_args<double>(c, L);
         a.u = (const double *)u;
         a.out = (double *)v;
-        CK(launch_dg_eval<double>(L.n, L.curved, a, c->stream, c->cb[0][0]));
+        CK(launch_dg_eval<double>(L.n, L.curved, a, c->stream, L.cb[0][0]));
         CK(cudaEventRecord(ev[1], c->stream));
-        CK(launch_dg_integrate<double>(L.n, L.curved, a, c->stream, c->cb[0][1]));
+        CK(launch_dg_integrate<double>(L.n, L.curved, a, c->stream, L.cb[0][1]));
       } else {
         DGArgs<float> a = dg_args<float>(c, L);
         a.u = (const float *)u;
         a.out = (float *)v;
-        CK(launch_dg_eval<float>(L.n, L.curved, a, c->stream, c->cb[1][0]));
+        CK(launch_dg_eval<float>(L.n, L.curved, a, c->stream, L.cb[1][0]));
         CK(cudaEventRecord(ev[1], c->stream));
-        CK(launch_dg_integrate<float>(L.n, L.curved, a, c->stream, c->cb[1][1]));
+        CK(launch_dg_integrate<float>(L.n, L.curved, a, c->stream, L.cb[1][1]));
       }
       CK(cudaEventRecord(ev[2], c->stream));
       CK(cudaEventSynchronize(ev[2]));
@@ -1362,11 +1482,35 @@ sipg_status sipg_time_apply(sipg_ctx *c, int precision, const void *u, void *v, 
   });
 }
 
-sipg_status sipg_tile_shape(const sipg_ctx *c, int precision, int pass, int *cells_per_block) {
-  if (!c || !cells_per_block || precision < 0 || precision > 1 || pass < 0 || pass > 1) return SIPG_EINVAL;
-  const int v = c->cb[precision][pass];
-  const int n = c->lv[c->L].n;
+sipg_status sipg_tile_shape(const sipg_ctx *c, int level, int precision, int pass, int *cells_per_block) {
+  if (!c || !cells_per_block || precision < 0 || precision > 1 || pass < 0 || pass > 2 || level < 0 ||
+      level > c->L || (c->lv[level].kind == 0) != (pass < 2))
+    return SIPG_EINVAL;
+  const int v = c->lv[level].cb[precision][pass];
+  const int n = c->lv[level].n;
   *cells_per_block = v ? v : (precision == 0 ? dg_cells_per_block<double>(n) : dg_cells_per_block<float>(n));
+  return SIPG_OK;
+}
+
+sipg_status sipg_set_tile_shape(sipg_ctx *c, int level, int precision, int pass, int cells_per_block) {
+  if (!c || precision < 0 || precision > 1 || pass < 0 || pass > 2 || level < 0 || level > c->L ||
+      (c->lv[level].kind == 0) != (pass < 2))
+    return SIPG_EINVAL;
+  const int n = c->lv[level].n;
+  const int mx = pass < 2 ? (precision == 0 ? dg_max_cells_per_block<double>(n) : dg_max_cells_per_block<float>(n))
+                          : (precision == 0 ? fe_max_cells_per_block<double>(n) : fe_max_cells_per_block<float>(n));
+  if (cells_per_block < 0 || cells_per_block > mx) return SIPG_EINVAL;
+  c->lv[level].cb[precision][pass] = cells_per_block;
+  // captured V-cycles hold the old launch shapes
+  for (int p = 0; p < 2; ++p) {
+    if (c->vgraph[p]) cudaGraphExecDestroy(c->vgraph[p]);
+    if (c->vgraph_l[p]) cudaGraphExecDestroy(c->vgraph_l[p]);
+    c->vgraph[p] = c->vgraph_l[p] = nullptr;
+    c->vcalls[p] = c->vcalls_l[p] = 0;
+  }
+  if (c->mv.graph) cudaGraphExecDestroy(c->mv.graph);
+  c->mv.graph = nullptr;
+  c->mv.calls = 0;
   return SIPG_OK;
 }
 
@@ -1542,27 +1686,33 @@ void batch_set_plan(sipg_batch *B, int mode, const double *const *u, double *con
   }
 }
 
-sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *const *x, double rtol, int maxit,
-                             sipg_solve_info *infos) {
-  const int np = (int)B->ctx.size();
-  cudaStream_t s = B->stream;
-  std::vector<const double *> xu(np), pu(np);
-  std::vector<double *> rout(np), vout(np);
-  for (int p = 0; p < np; ++p) {
-    sipg_ctx *c = B->ctx[p];
-    B->segs[p] = Seg{x[p], c->fr, c->fp, c->fv, c->fz, b[p], (long)c->lv[c->L].ndofs, 1};
-    xu[p] = x[p];
-    pu[p] = c->fp;
-    rout[p] = c->fr;
-    vout[p] = c->fv;
-  }
+// Flexible CG (Section 3, Algorithm 1 with Notay's beta) for np systems in
+// lockstep: every step runs on all active systems at once, the scalars of
+// system p sit at sc[p * kSegSlots + slot] (0 gamma, 1 z.Ap, 2 p.Ap, 3 r.r,
+// 4 b.b, 5 r0.r0); a system leaves the iteration when it converges, breaks
+// down or reaches maxit.  residual(): r = b - A x; apply(): v = A p;
+// precondition(): z = M^-1 r, each for all systems.
+struct Lockstep {
+  cudaStream_t s;
+  std::vector<Seg> &segs;
+  Seg *d_segs;
+  double *sc, *partials;
+  unsigned *counters;
+  std::string &err;
+};
+
+template <typename FR, typename FA, typename FP>
+sipg_status lockstep_fcg(Lockstep K, FR residual, FA apply, FP precondition_all, double rtol, int maxit,
+                         sipg_solve_info *infos) {
+  const int np = (int)K.segs.size();
+  cudaStream_t s = K.s;
   auto upload_segs = [&]() {
-    CK(cudaMemcpyAsync(B->d_segs, B->segs.data(), np * sizeof(Seg), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(K.d_segs, K.segs.data(), np * sizeof(Seg), cudaMemcpyHostToDevice, s));
   };
   const int st = kSegSlots;
   std::vector<double> hsc((size_t)np * st);
   auto read_sc = [&]() {
-    CK(cudaMemcpyAsync(hsc.data(), B->sc, hsc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hsc.data(), K.sc, hsc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   };
   cudaEvent_t e0, e1;
@@ -1570,12 +1720,11 @@ sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *cons
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
   upload_segs();
-  batch_set_plan(B, 2, xu.data(), rout.data());   // r = b - A x
-  CK(batch_apply(B->plan, s));
-  CK(seg_dot(B->d_segs, np, 0, B->partials, B->counters, B->sc, st, 4, s));
-  batch_precondition(B);
-  CK(seg_dot(B->d_segs, np, 1, B->partials, B->counters, B->sc, st, 0, s));
-  CK(seg_update_p(B->d_segs, np, B->sc, st, 1, s));
+  residual();
+  CK(seg_dot(K.d_segs, np, 0, K.partials, K.counters, K.sc, st, 4, s));
+  precondition_all();
+  CK(seg_dot(K.d_segs, np, 1, K.partials, K.counters, K.sc, st, 0, s));
+  CK(seg_update_p(K.d_segs, np, K.sc, st, 1, s));
   read_sc();
   std::vector<double> r0(np), rn(np);
   std::vector<int> it(np, 0);
@@ -1583,12 +1732,12 @@ sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *cons
   sipg_status status = SIPG_OK;
   for (int p = 0; p < np; ++p) {
     if (!std::isfinite(hsc[p * st + 4])) {
-      B->err = "a right-hand side is not finite";
+      K.err = "a right-hand side is not finite";
       status = SIPG_ENAN;
     }
     r0[p] = rn[p] = std::sqrt(hsc[p * st + 5]);
     hist[p].push_back(r0[p]);
-    if (r0[p] == 0.0) B->segs[p].active = 0;
+    if (r0[p] == 0.0) K.segs[p].active = 0;
   }
   if (status != SIPG_OK) {
     cudaEventDestroy(e0);
@@ -1599,40 +1748,39 @@ sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *cons
   while (true) {
     int nact = 0;
     for (int p = 0; p < np; ++p) {
-      if (B->segs[p].active && it[p] >= maxit) {
-        B->segs[p].active = 0;
+      if (K.segs[p].active && it[p] >= maxit) {
+        K.segs[p].active = 0;
         status = SIPG_ENOTCONV;
       }
-      nact += B->segs[p].active;
+      nact += K.segs[p].active;
     }
     if (nact == 0) break;
     upload_segs();
-    batch_set_plan(B, 0, pu.data(), vout.data());   // v = A p
-    CK(batch_apply(B->plan, s));
-    CK(seg_dot(B->d_segs, np, 2, B->partials, B->counters, B->sc, st, 2, s));
-    CK(seg_update_xr(B->d_segs, np, B->partials, B->counters, B->sc, st, s));
+    apply();
+    CK(seg_dot(K.d_segs, np, 2, K.partials, K.counters, K.sc, st, 2, s));
+    CK(seg_update_xr(K.d_segs, np, K.partials, K.counters, K.sc, st, s));
     read_sc();
     for (int p = 0; p < np; ++p) {
-      if (!B->segs[p].active) continue;
+      if (!K.segs[p].active) continue;
       const double *q = &hsc[p * st];
       ++it[p];
       if (!(q[2] > 0) || !std::isfinite(q[3])) {
-        B->segs[p].active = 0;
+        K.segs[p].active = 0;
         status = SIPG_EBREAKDOWN;
-        B->err = "flexible CG breakdown in a batched problem";
+        K.err = "flexible CG breakdown in one of the systems solved together";
         continue;
       }
       rn[p] = std::sqrt(q[3]);
       hist[p].push_back(rn[p]);
-      if (rn[p] <= rtol * r0[p]) B->segs[p].active = 0;
+      if (rn[p] <= rtol * r0[p]) K.segs[p].active = 0;
     }
     upload_segs();
     int still = 0;
-    for (int p = 0; p < np; ++p) still += B->segs[p].active;
+    for (int p = 0; p < np; ++p) still += K.segs[p].active;
     if (still == 0) break;
-    batch_precondition(B);
-    CK(seg_dot(B->d_segs, np, 3, B->partials, B->counters, B->sc, st, 0, s));
-    CK(seg_update_p(B->d_segs, np, B->sc, st, 0, s));
+    precondition_all();
+    CK(seg_dot(K.d_segs, np, 3, K.partials, K.counters, K.sc, st, 0, s));
+    CK(seg_update_p(K.d_segs, np, K.sc, st, 0, s));
   }
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
@@ -1653,8 +1801,120 @@ sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *cons
       I.seconds = ms * 1e-3;
       for (int j = 0; j < (int)hist[p].size() && j < 256; ++j) I.res_history[j] = hist[p][j];
     }
-  if (status == SIPG_ENOTCONV) B->err = "a batched problem reached maxit before the tolerance";
+  if (status == SIPG_ENOTCONV) K.err = "a system reached maxit before the tolerance";
   return status;
+}
+
+sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *const *x, double rtol, int maxit,
+                             sipg_solve_info *infos) {
+  const int np = (int)B->ctx.size();
+  std::vector<const double *> xu(np), pu(np);
+  std::vector<double *> rout(np), vout(np);
+  for (int p = 0; p < np; ++p) {
+    sipg_ctx *c = B->ctx[p];
+    B->segs[p] = Seg{x[p], c->fr, c->fp, c->fv, c->fz, b[p], (long)c->lv[c->L].ndofs, 1};
+    xu[p] = x[p];
+    pu[p] = c->fp;
+    rout[p] = c->fr;
+    vout[p] = c->fv;
+  }
+  Lockstep K{B->stream, B->segs, B->d_segs, B->sc, B->partials, B->counters, B->err};
+  return lockstep_fcg(
+      K,
+      [&]() {   // r = b - A x
+        batch_set_plan(B, 2, xu.data(), rout.data());
+        CK(batch_apply(B->plan, B->stream));
+      },
+      [&]() {   // v = A p
+        batch_set_plan(B, 0, pu.data(), vout.data());
+        CK(batch_apply(B->plan, B->stream));
+      },
+      [&]() { batch_precondition(B); }, rtol, maxit, infos);
+}
+
+// ------------------------------------------------ many right-hand sides
+// Work set for nv vectors of the context's problem: every level's V-cycle
+// vectors (V-cycle precision), the cell-kernel scratch (both precisions),
+// the flexible-CG vectors and the per-system scalars.  Grown on demand;
+// growing drops the captured multi-vector cycle.
+void ensure_multi(sipg_ctx *c, int nv) {
+  auto &M = c->mv;
+  if (M.cap >= nv) return;
+  CK(cudaStreamSynchronize(c->stream));
+  if (M.graph) cudaGraphExecDestroy(M.graph);
+  M.graph = nullptr;
+  M.calls = 0;
+  M.graph_nv = 0;
+  std::vector<void *> old;
+  for (void *q : M.v) old.push_back(q);
+  for (void *q : {M.grad[0], M.grad[1], M.trace[0], M.trace[1], M.ebuf[0], M.ebuf[1], (void *)M.r, (void *)M.z,
+                  (void *)M.p, (void *)M.v_, (void *)M.d_segs, (void *)M.sc, (void *)M.partials,
+                  (void *)M.counters})
+    old.push_back(q);
+  for (void *q : old) {
+    if (!q) continue;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), q);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(q);
+  }
+  M = sipg_ctx::Multi{};   // no pointer survives a regrowth
+  const int pi = c->prm.precision;
+  const size_t es = pi == 0 ? sizeof(double) : sizeof(float);
+  const int nl = (int)c->lv.size();
+  M.v.assign(4 * nl, nullptr);
+  int64_t grad = 0, trace = 0, ebuf = 0;
+  for (int l = 0; l < nl; ++l) {
+    const Level &L = c->lv[l];
+    for (int k = 0; k < 4; ++k) M.v[4 * l + k] = dalloc<char>(c, (int64_t)(L.ndofs * nv * es));
+    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    if (L.kind == 0) {
+      grad = std::max(grad, L.ncells * 3 * n3);
+      trace = std::max(trace, L.ncells * 12 * (int64_t)L.n * L.n);
+    }
+    ebuf = std::max(ebuf, L.ncells * n3);
+  }
+  M.grad[0] = dalloc<double>(c, grad * nv);
+  M.trace[0] = dalloc<double>(c, trace * nv);
+  M.ebuf[0] = dalloc<double>(c, ebuf * nv);
+  if (pi == 1) {
+    M.grad[1] = dalloc<float>(c, grad * nv);
+    M.trace[1] = dalloc<float>(c, trace * nv);
+    M.ebuf[1] = dalloc<float>(c, ebuf * nv);
+  }
+  const int64_t N = c->lv[c->L].ndofs * nv;
+  M.r = dalloc<double>(c, N);
+  M.z = dalloc<double>(c, N);
+  M.p = dalloc<double>(c, N);
+  M.v_ = dalloc<double>(c, N);
+  M.d_segs = (Seg *)dalloc<char>(c, (int64_t)(nv * sizeof(Seg)));
+  M.sc = dalloc<double>(c, (int64_t)nv * kSegSlots);
+  M.partials = dalloc<double>(c, (int64_t)nv * kSegBlocksHost * 2);
+  M.counters = dalloc<unsigned>(c, nv);
+  CK(cudaMemset(M.counters, 0, nv * sizeof(unsigned)));
+  M.cap = nv;
+}
+
+// restores the single-vector work set on every exit
+struct MultiScope {
+  sipg_ctx *c;
+  MultiScope(sipg_ctx *c_, int nv) : c(c_) { c->nv = nv; }
+  ~MultiScope() { c->nv = 1; }
+};
+
+sipg_status solve_multi_impl(sipg_ctx *c, int nrhs, const double *B, double *X, double rtol, int maxit,
+                             sipg_solve_info *infos) {
+  ensure_multi(c, nrhs);
+  MultiScope scope(c, nrhs);
+  auto &M = c->mv;
+  const int64_t N = c->lv[c->L].ndofs;
+  M.segs.resize(nrhs);
+  for (int r = 0; r < nrhs; ++r)
+    M.segs[r] = Seg{X + r * N, M.r + r * N, M.p + r * N, M.v_ + r * N, M.z + r * N, B + r * N, (long)N, 1};
+  c->use_learned = 0;   // the multi-vector cycle smooths with Chebyshev
+  Lockstep K{c->stream, M.segs, M.d_segs, M.sc, M.partials, M.counters, c->err};
+  return lockstep_fcg(
+      K, [&]() { apply_level<double>(c, c->L, X, M.r, 2, nullptr, nullptr, B); },
+      [&]() { apply_level<double>(c, c->L, M.p, M.v_, 0); }, [&]() { precondition(c); }, rtol, maxit, infos);
 }
 
 template <typename F>
@@ -1675,6 +1935,38 @@ sipg_status bguarded(sipg_batch *B, F &&f) {
 }
 
 }  // namespace
+
+sipg_status sipg_solve_multi(sipg_ctx *c, int nrhs, const double *B, double *X, double rtol, int maxit,
+                             sipg_solve_info *infos) {
+  if (!c || !B || !X || !c->solver || nrhs < 1 || nrhs > 4096 || maxit < 0 || !(rtol >= 0)) return SIPG_EINVAL;
+  if (nrhs == 1) return sipg_solve(c, B, X, rtol, maxit, 0, infos);
+  return guarded(c, [&]() -> sipg_status { return solve_multi_impl(c, nrhs, B, X, rtol, maxit, infos); });
+}
+
+sipg_status sipg_operator_apply_multi(sipg_ctx *c, int precision, int nv, const void *U, void *V) {
+  if (!c || !U || !V || U == V || nv < 1 || nv > 4096 || (precision != 0 && precision != 1)) return SIPG_EINVAL;
+  if (nv == 1) return sipg_operator_apply(c, precision, U, V);
+  if (!c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    ensure_multi(c, nv);
+    if (precision == 1 && !c->mv.grad[1]) {   // FP32 scratch of a context whose cycle runs in FP64
+      int64_t grad = 0, trace = 0;
+      for (const Level &L : c->lv)
+        if (L.kind == 0) {
+          grad = std::max(grad, L.ncells * 3 * (int64_t)L.n * L.n * L.n);
+          trace = std::max(trace, L.ncells * 12 * (int64_t)L.n * L.n);
+        }
+      c->mv.grad[1] = dalloc<float>(c, grad * c->mv.cap);
+      c->mv.trace[1] = dalloc<float>(c, trace * c->mv.cap);
+    }
+    MultiScope scope(c, nv);
+    if (precision == 0)
+      apply_level<double>(c, c->L, (const double *)U, (double *)V, 0);
+    else
+      apply_level<float>(c, c->L, (const float *)U, (float *)V, 0);
+    return SIPG_OK;
+  });
+}
 
 extern "C" {
 
@@ -1728,7 +2020,7 @@ sipg_status sipg_batch_create(int nprob, const sipg_mesh *meshes, const sipg_par
       B->segs.assign(nprob, Seg{});
       CK(cudaMalloc(&B->d_segs, nprob * sizeof(Seg)));
       CK(cudaMalloc(&B->sc, (size_t)nprob * kSegSlots * sizeof(double)));
-      CK(cudaMalloc(&B->partials, (size_t)nprob * 32 * 2 * sizeof(double)));
+      CK(cudaMalloc(&B->partials, (size_t)nprob * kSegBlocksHost * 2 * sizeof(double)));
       CK(cudaMalloc(&B->counters, (size_t)nprob * sizeof(unsigned)));
       CK(cudaMemset(B->counters, 0, (size_t)nprob * sizeof(unsigned)));
       CK(cudaEventCreateWithFlags(&B->ev_start, cudaEventDisableTiming));

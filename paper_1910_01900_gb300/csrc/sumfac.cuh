@@ -152,6 +152,18 @@ __device__ __forceinline__ void sweep_inplace(T *s, int d, int l) {
 // Values of one padded tile array for n points per direction (host and device).
 __host__ __device__ constexpr int tile_values(int n) { return ((n % 2 == 0) ? n + 1 : n) * n * n; }
 
+// Most threads per block of the cell kernels (their __launch_bounds__: at
+// most 85 registers a thread, which the sweeps need without spilling).
+constexpr int kCellThreads = 768;
+
+// Largest cells per thread block of the cell kernels (four tile arrays of
+// shared memory per cell): kCellThreads threads and 227 KB of shared memory.
+__host__ __device__ constexpr int max_cb(int n, int elem_bytes) {
+  return (kCellThreads / (n * n)) < (232448 / (4 * tile_values(n) * elem_bytes))
+             ? (kCellThreads / (n * n))
+             : (232448 / (4 * tile_values(n) * elem_bytes));
+}
+
 // Cells per thread block for a tile size n (about 256 threads, n^2 threads per cell).
 __host__ __device__ constexpr int default_cb(int n) {
   return n == 2 ? 64 : n == 3 ? 28 : n == 4 ? 16 : n == 5 ? 10 : n == 6 ? 7 : n == 7 ? 5 : n == 8 ? 4 : 3;

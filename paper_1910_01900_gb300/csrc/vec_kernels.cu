@@ -178,6 +178,8 @@ __global__ void dense_gemv_kernel(const double *__restrict__ Ainv, const Tb *__r
                                   int n) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
+  b += (size_t)blockIdx.y * n;   // vector blockIdx.y
+  x += (size_t)blockIdx.y * n;
   const double *row = Ainv + (size_t)warp * n;
   double s = 0;
   for (int j = lane; j < n; j += 32) s = fma(row[j], (double)b[j], s);
@@ -185,14 +187,16 @@ __global__ void dense_gemv_kernel(const double *__restrict__ Ainv, const Tb *__r
   if (lane == 0) x[warp] = (Tx)s;
 }
 template <typename Tb, typename Tx>
-cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cudaStream_t s) {
+cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cudaStream_t s, int nv) {
   const int bs = 256, wpb = bs / 32;
-  dense_gemv_kernel<Tb, Tx><<<(n + wpb - 1) / wpb, bs, 0, s>>>(Ainv, b, x, n);
+  if (n <= 0) return cudaSuccess;
+  dense_gemv_kernel<Tb, Tx><<<dim3((n + wpb - 1) / wpb, nv), bs, 0, s>>>(Ainv, b, x, n);
   note_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_dense_gemv<double, double>(const double *, const double *, double *, int, cudaStream_t);
-template cudaError_t launch_dense_gemv<float, float>(const double *, const float *, float *, int, cudaStream_t);
+template cudaError_t launch_dense_gemv<double, double>(const double *, const double *, double *, int, cudaStream_t,
+                                                       int);
+template cudaError_t launch_dense_gemv<float, float>(const double *, const float *, float *, int, cudaStream_t, int);
 
 // ------------------------------------------------------------ peak probe
 // Eight independent FMA chains per thread, all SMs busy; the result is kept
@@ -251,13 +255,15 @@ namespace sipg {
 // x = c * dinv * b (first Chebyshev step from a zero start)
 template <typename T>
 __global__ void xdb_kernel(T *x, T c, const T *dinv, const T *b, long n) {
+  x += blockIdx.y * n;   // vector blockIdx.y; dinv is shared
+  b += blockIdx.y * n;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     x[i] = c * dinv[i] * b[i];
 }
 template <typename T>
-cudaError_t launch_xdb(T *x, T c, const T *dinv, const T *b, int64_t n, cudaStream_t s) {
+cudaError_t launch_xdb(T *x, T c, const T *dinv, const T *b, int64_t n, cudaStream_t s, int nv) {
   if (n <= 0) return cudaSuccess;
-  xdb_kernel<T><<<grid_for(n), 256, 0, s>>>(x, c, dinv, b, n);
+  xdb_kernel<T><<<dim3(grid_for(n), nv), 256, 0, s>>>(x, c, dinv, b, n);
   note_launch();
   return cudaGetLastError();
 }
@@ -274,8 +280,8 @@ cudaError_t launch_xpby(T *p, const T *z, T beta, int64_t n, cudaStream_t s) {
   note_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_xdb<double>(double *, double, const double *, const double *, int64_t, cudaStream_t);
-template cudaError_t launch_xdb<float>(float *, float, const float *, const float *, int64_t, cudaStream_t);
+template cudaError_t launch_xdb<double>(double *, double, const double *, const double *, int64_t, cudaStream_t, int);
+template cudaError_t launch_xdb<float>(float *, float, const float *, const float *, int64_t, cudaStream_t, int);
 template cudaError_t launch_xpby<double>(double *, const double *, double, int64_t, cudaStream_t);
 template cudaError_t launch_xpby<float>(float *, const float *, float, int64_t, cudaStream_t);
 }  // namespace sipg

@@ -21,7 +21,8 @@ EXPORTS = [
     "sipg_level_apply", "sipg_inverse_diagonal", "sipg_smooth", "sipg_restrict", "sipg_prolongate_add",
     "sipg_coarse_solve", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
     "sipg_operator_apply_noalloc", "sipg_launch_count", "sipg_batch_create", "sipg_batch_destroy",
-    "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_solve", "sipg_tile_shape",
+    "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_solve", "sipg_tile_shape", "sipg_set_tile_shape", "sipg_solve_multi",
+    "sipg_operator_apply_multi",
     "sipg_smoother_train", "sipg_set_smoother", "sipg_mlp_shape", "sipg_mlp_params", "sipg_mlp_forward",
     "sipg_mlp_gradients", "sipg_mlp_features", "sipg_l2_error",
 ]
@@ -45,7 +46,7 @@ class Params(ctypes.Structure):
                 ("p_coarsen", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("lambda_override", ctypes.c_double),
                 ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("coarsening", ctypes.c_char * 8),
-                ("autotune", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("fe_assemble", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -89,11 +90,14 @@ def lib():
         L.sipg_vcycle.argtypes = [vp, vp, vp]
         L.sipg_solve.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveInfo)]
         L.sipg_solve_host.argtypes = [vp, vp, vp, dbl, i32, ctypes.POINTER(SolveInfo)]
+        L.sipg_solve_multi.argtypes = [vp, i32, vp, vp, dbl, i32, ctypes.POINTER(SolveInfo)]
+        L.sipg_operator_apply_multi.argtypes = [vp, i32, i32, vp, vp]
         L.sipg_time_apply.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_float)]
         L.sipg_fma_peak.argtypes = [i32, vp, ctypes.POINTER(dbl)]
         L.sipg_launch_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
-        L.sipg_tile_shape.argtypes = [vp, i32, i32, ctypes.POINTER(i32)]
+        L.sipg_tile_shape.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32)]
+        L.sipg_set_tile_shape.argtypes = [vp, i32, i32, i32, i32]
         L.sipg_smoother_train.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(TrainInfo)]
         L.sipg_set_smoother.argtypes = [vp, i32, i32, i32]
         ip = ctypes.POINTER(i32)
@@ -149,7 +153,7 @@ def make_mesh(m, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(
 
 
 def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph"):
+                operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None):
     prm = Params()
     lib().sipg_default_params(ctypes.byref(prm))
     prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
@@ -158,6 +162,8 @@ def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iter
     prm.autotune = int(bool(autotune))
     prm.p_coarsen = int(p_coarsen)
     prm.coarsening = coarsening.encode()
+    if fe_assemble is not None:
+        prm.fe_assemble = int(fe_assemble)
     prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return prm
 
@@ -167,7 +173,8 @@ class Context:
 
     def __init__(self, m, degree, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
                  precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                 operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", _handle=None):
+                 operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None,
+                 _handle=None):
         L = lib()
         mesh, mm = make_mesh(m, deform, amp, lo, hi, bc)
         self.degree, self.precision = int(degree), int(precision)
@@ -178,7 +185,7 @@ class Context:
             self.h = _handle
             return
         prm = make_params(degree, precision, penalty_factor, cheb_degree, eig_iters, lambda_override,
-                          operator_only, stream, autotune, p_coarsen, coarsening)
+                          operator_only, stream, autotune, p_coarsen, coarsening, fe_assemble)
         h = ctypes.c_void_p()
         st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
         if st != OK:
@@ -285,6 +292,28 @@ class Context:
             self._check(st)
         return info
 
+    def solve_multi(self, B, X, rtol=1e-10, maxit=200, allow_notconv=False):
+        """Solve for every row of B (shape (nrhs, num_dofs), FP64, device) at once; X holds the
+        start vectors and receives the solutions.  Returns one SolveInfo per right-hand side."""
+        import torch
+        nrhs, n = B.shape
+        assert n == self.num_dofs() and tuple(X.shape) == (nrhs, n)
+        infos = (SolveInfo * nrhs)()
+        st = lib().sipg_solve_multi(self.h, nrhs, _ptr(B, torch.float64, nrhs * n), _ptr(X, torch.float64, nrhs * n),
+                                    float(rtol), int(maxit), infos)
+        if not (allow_notconv and st == ENOTCONV):
+            self._check(st)
+        return list(infos)
+
+    def apply_multi(self, U, V):
+        """V = A U for every row of U (shape (nv, num_dofs), FP64 or FP32, device)."""
+        import torch
+        precision = 0 if U.dtype == torch.float64 else 1
+        nv, n = U.shape
+        assert n == self.num_dofs() and tuple(V.shape) == (nv, n)
+        self._check(lib().sipg_operator_apply_multi(self.h, precision, nv, _ptr(U, U.dtype, nv * n),
+                                                    _ptr(V, U.dtype, nv * n)))
+
     def solve_host(self, b_host, x_host, rtol=1e-10, maxit=200):
         import numpy as np
         n = self.num_dofs()
@@ -350,10 +379,16 @@ class Context:
         self._check(lib().sipg_mlp_features(self.h, _ptr(r, torch.float64, self.num_dofs()),
                                             _ptr(feat, torch.float32), _ptr(scale, torch.float32)))
 
-    def tile_shape(self, precision, pass_):
+    def tile_shape(self, precision, pass_, level=None):
+        """Cells per block of a cell kernel (pass 0/1 DG evaluation/integration, 2 FE cells)."""
         v = ctypes.c_int()
-        self._check(lib().sipg_tile_shape(self.h, int(precision), int(pass_), ctypes.byref(v)))
+        lvl = self.num_levels - 1 if level is None else int(level)
+        self._check(lib().sipg_tile_shape(self.h, lvl, int(precision), int(pass_), ctypes.byref(v)))
         return v.value
+
+    def set_tile_shape(self, precision, pass_, cells_per_block, level=None):
+        lvl = self.num_levels - 1 if level is None else int(level)
+        self._check(lib().sipg_set_tile_shape(self.h, lvl, int(precision), int(pass_), int(cells_per_block)))
 
     def time_apply(self, u, v, repeats=20):
         import torch

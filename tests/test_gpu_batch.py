@@ -109,3 +109,74 @@ def test_32_right_hand_sides():
         info = c.solve(bs[r], x, rtol=1e-10)
         assert info.iterations == infos[r].iterations
         assert rel(xs[r].cpu().numpy(), x.cpu().numpy()) <= 1e-9
+
+
+@pytest.mark.parametrize("precision,deform", [(0, 0), (1, 1)])
+def test_apply_multi_equals_single_applies(precision, deform):
+    """One launch per pass for nv vectors of one operator: each row equals the single apply."""
+    from paper_1910_01900_gb300 import Context
+    m, k, nv = (6, 4, 5), 3, 7
+    ctx = Context(m, k, deform=deform, precision=precision)
+    n = ctx.num_dofs()
+    dt = torch.float64 if precision == 0 else torch.float32
+    U = torch.stack([torch.as_tensor(sipg_inputs.uniform(n, 70 + r)) for r in range(nv)]).to(DEV, dt)
+    V = torch.full_like(U, float("nan"))
+    ctx.apply_multi(U, V)
+    torch.cuda.synchronize()
+    o = SIPG(Mesh(m, deform=deform), k)
+    for r in range(nv):
+        ref = torch.empty_like(U[r])
+        ctx.apply(U[r].contiguous(), ref)
+        torch.cuda.synchronize()
+        assert torch.equal(V[r], ref), r
+        if precision == 0:
+            assert rel(V[r].cpu().numpy(), o.apply(U[r].cpu().numpy())) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_multi_equals_single_solves(precision):
+    """nrhs right-hand sides in lockstep through multi-vector V-cycles: the same iteration
+    counts and solutions as one solve per right-hand side, and the oracle's solve."""
+    from paper_1910_01900_gb300 import Context
+    m, k, nrhs = 4, 3, 6
+    ctx = Context(m, k, precision=precision)
+    n = ctx.num_dofs()
+    B = torch.stack([torch.as_tensor(sipg_inputs.uniform(n, sipg_inputs.SEED_RHS + r)) for r in range(nrhs)]).to(DEV)
+    B[3] *= 1e3                 # scaled right-hand side: same iterates up to the scale
+    X = torch.zeros_like(B)
+    infos = ctx.solve_multi(B, X, rtol=1e-10)
+    torch.cuda.synchronize()
+    single = Context(m, k, precision=precision)
+    for r in range(nrhs):
+        x = torch.zeros(n, dtype=torch.float64, device=DEV)
+        info = single.solve(B[r].contiguous(), x, rtol=1e-10)
+        assert infos[r].converged and infos[r].iterations == info.iterations, r
+        assert rel(X[r].cpu().numpy(), x.cpu().numpy()) <= (1e-12 if precision == 0 else 1e-9), r
+    mg = CPHMultigrid(Mesh(m), k)
+    bo = B[0].cpu().numpy()
+    xo, it, _ = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
+    assert rel(X[0].cpu().numpy(), xo) <= (1e-10 if precision == 0 else 1e-8)
+    if precision == 0:
+        assert infos[0].iterations == it
+    # a second call with fewer right-hand sides reuses the work set
+    X2 = torch.zeros_like(B[:2])
+    infos2 = ctx.solve_multi(B[:2].contiguous(), X2, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert torch.equal(X2, X[:2]) and [i.iterations for i in infos2] == [i.iterations for i in infos[:2]]
+
+
+def test_solve_multi_zero_and_nan_rows():
+    """A zero right-hand side stops at once with x = 0; a non-finite one is refused."""
+    from paper_1910_01900_gb300 import Context
+    from paper_1910_01900_gb300.native import SipgError
+    ctx = Context(4, 2)
+    n = ctx.num_dofs()
+    B = torch.stack([torch.as_tensor(sipg_inputs.uniform(n, 5)), torch.zeros(n, dtype=torch.float64)]).to(DEV)
+    X = torch.zeros_like(B)
+    infos = ctx.solve_multi(B, X, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert infos[0].converged and infos[1].converged and infos[1].iterations == 0
+    assert float(X[1].abs().max()) == 0.0
+    B[1, 17] = float("nan")
+    with pytest.raises(SipgError):
+        ctx.solve_multi(B, torch.zeros_like(B), rtol=1e-10)

@@ -113,6 +113,42 @@ def test_levels_diagonals_and_fe_apply(m, k, deform):
             assert rel(d.cpu().numpy(), lev.dinv) <= 1e-12
 
 
+@pytest.mark.parametrize("deform,bc", [(1, (0, 1, 0, 0, 1, 0)), (0, (1, 1, 0, 1, 1, 1))])
+def test_assembled_low_degree_levels_match_matrix_free(deform, bc):
+    """FE levels of degree 1 (by default) and 2 (fe_assemble=2) apply an assembled stencil:
+    the same operator as the matrix-free cell and node passes and as the oracle's FE matrix,
+    with Dirichlet and Neumann sides mixed (identity rows and zero columns only on Dirichlet
+    nodes)."""
+    m, k = 6, 4   # DG4, FE4, FE2 (assembled), FE1 6^3 (assembled), FE1 3^3 (coarse)
+    ctx_a = _ctx(m, k, deform=deform, bc=bc, lambda_override=2.0, fe_assemble=2)
+    ctx_f = _ctx(m, k, deform=deform, bc=bc, lambda_override=2.0, fe_assemble=0)
+    mg = CPHMultigrid(Mesh(m, deform=deform, bc=bc), k, lambdas=[2.0] * 16)
+    checked = 0
+    for l in range(1, len(mg.levels)):
+        lev = mg.levels[l]
+        if lev.kind != "fe" or lev.space.p > 2:
+            continue
+        u = sipg_inputs.uniform(lev.n, 500 + l)
+        u[lev.space.constrained] *= -3.0
+        ref = lev.apply(u)
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            va, vf = (torch.empty(lev.n, dtype=dt, device=DEV) for _ in range(2))
+            ctx_a.level_apply(l, gpu(u, dt), va)
+            ctx_f.level_apply(l, gpu(u, dt), vf)
+            torch.cuda.synchronize()
+            assert rel(va.cpu().numpy(), ref) <= tol, (l, dt)
+            assert rel(vf.cpu().numpy(), ref) <= tol, (l, dt)
+        checked += 1
+    assert checked == 2
+    r = gpu(sipg_inputs.uniform(ctx_a.num_dofs(), 77))
+    za, zf = torch.empty_like(r), torch.empty_like(r)
+    ctx_a.vcycle(r, za)
+    ctx_f.vcycle(r, zf)
+    torch.cuda.synchronize()
+    zo = mg.vcycle(r.cpu().numpy())
+    assert rel(za.cpu().numpy(), zo) <= 1e-12 and rel(zf.cpu().numpy(), zo) <= 1e-12
+
+
 @pytest.mark.parametrize("m,k,deform", [(6, 4, 0), (6, 5, 1), (8, 2, 0)])
 def test_transfers_match_sparse_matrices(m, k, deform):
     ctx, mg = _hierarchy(m, k, deform, lambda_override=2.0)
@@ -207,6 +243,24 @@ def test_solve_to_1e10_same_iterations_as_oracle(m, k, deform):
     assert rel(x32.cpu().numpy(), ref) <= 1e-8
 
 
+def test_solve_from_a_nonzero_start_vector():
+    """x0 != 0 takes the r0 = b - A x0 branch (x0 = 0 skips that apply): same iterates as the
+    oracle's flexible CG started from the same x0, and the same solution as from zero."""
+    m, k = 4, 3
+    ctx, mg = _hierarchy(m, k, 1)
+    bo = sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_RHS)
+    x0 = 0.3 * sipg_inputs.uniform(ctx.num_dofs(), 9)
+    ref, it, hist = fcg(mg.levels[-1].apply, bo, x0.copy(), mg.vcycle, rtol=1e-10)
+    x = gpu(x0)
+    info = ctx.solve(gpu(bo), x, rtol=1e-10)
+    assert info.converged and info.iterations == it
+    assert abs(info.r0_norm - hist[0]) <= 1e-12 * hist[0]
+    assert rel(x.cpu().numpy(), ref) <= 1e-10
+    xz = torch.zeros_like(x)
+    ctx.solve(gpu(bo), xz, rtol=1e-12)
+    assert rel(x.cpu().numpy(), xz.cpu().numpy()) <= 1e-6
+
+
 def test_solve_host_round_trip_and_nan_rejected():
     ctx = _ctx(4, 2)
     b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
@@ -265,10 +319,48 @@ def test_autotuned_tile_shapes_keep_parity(k, deform):
         v = torch.empty(len(u), dtype=dt, device=DEV)
         ctx.apply(gpu(u, dt), v)
         assert rel(v.cpu().numpy(), ref) <= tol
-    from paper_1910_01900_gb300.csrc_info import tile_candidates
+    from paper_1910_01900_gb300.csrc_info import max_cells_per_block
     for prec in (0, 1):
         for p in (0, 1):
-            assert ctx.tile_shape(prec, p) in tile_candidates(k + 1)
+            assert 1 <= ctx.tile_shape(prec, p) <= max_cells_per_block(k + 1, 8 >> prec)
+
+
+@pytest.mark.parametrize("k,deform", [(3, 1), (6, 0)])
+def test_every_tile_width_gives_identical_results(k, deform):
+    """A cell kernel's block width changes the launch, not the arithmetic: bitwise equal
+    results on the DG level (both passes) and on every FE level (cell pass)."""
+    from paper_1910_01900_gb300.csrc_info import max_cells_per_block
+    m = (5, 4, 6)
+    ctx = _ctx(m, k, deform=deform)
+    u64 = gpu(sipg_inputs.uniform(ctx.num_dofs(), 21))
+    ref64 = torch.empty_like(u64)
+    ctx.apply(u64, ref64)
+    torch.cuda.synchronize()
+    assert rel(ref64.cpu().numpy(), SIPG(Mesh(m, deform=deform), k).apply(u64.cpu().numpy())) <= 1e-12
+    for level in range(1, ctx.num_levels):
+        kind, deg, _ = ctx.level_info(level)
+        passes = (0, 1) if kind == 0 else (2,)
+        for dt, prec in ((torch.float64, 0), (torch.float32, 1)):
+            u = gpu(sipg_inputs.uniform(ctx.num_dofs(level), 30 + level), dt)
+            ref = torch.empty_like(u)
+            ctx.level_apply(level, u, ref)
+            mx = max_cells_per_block(deg + 1, 8 >> prec)
+            for cb in sorted({1, 2, 3, mx // 2, mx - 1, mx}):
+                for p in passes:
+                    ctx.set_tile_shape(prec, p, cb, level=level)
+                    assert ctx.tile_shape(prec, p, level=level) == cb
+                v = torch.full_like(u, float("nan"))
+                ctx.level_apply(level, u, v)
+                torch.cuda.synchronize()
+                assert torch.equal(v, ref), (level, prec, cb)
+            for p in passes:
+                ctx.set_tile_shape(prec, p, 0, level=level)
+    # widths beyond the limits and passes a level does not have are refused
+    from paper_1910_01900_gb300.native import SipgError
+    with pytest.raises(SipgError):
+        ctx.set_tile_shape(0, 0, max_cells_per_block(k + 1, 8) + 1)
+    with pytest.raises(SipgError):
+        ctx.set_tile_shape(0, 2, 1)
 
 
 def test_apply_is_deterministic_bitwise():
