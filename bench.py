@@ -52,7 +52,7 @@ NS = 5
 # DRAM bytes per DoF of the FP64 curved k=5 integration pass, from the ncu
 # capture summarised in profiles/dg_kernels_curved32_k5_fp64.md (32^3 cells,
 # scaled to this workload by the number of cells it processes).
-INTEGRATE_DRAM_BYTES_PER_DOF = 126.2
+INTEGRATE_DRAM_BYTES_PER_DOF = 126.1
 DG_APPLIES_PER_SOLVE = ITERATIONS * 2 * NS + ITERATIONS + 1
 
 

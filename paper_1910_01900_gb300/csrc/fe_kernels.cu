@@ -401,16 +401,21 @@ __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__
     row[d] = P1 + ((size_t)child * nf + r) * nc;
     base[d] = cc * G.pc;
   }
+  // factored tensor contraction: x, then y, then z (nc^3 + nc^2 + nc FMAs)
   T sum = T(0);
 #pragma unroll
-  for (int jz = 0; jz < (NC > 0 ? NC : nc); ++jz)
+  for (int jz = 0; jz < (NC > 0 ? NC : nc); ++jz) {
+    T sy = T(0);
 #pragma unroll
     for (int jy = 0; jy < (NC > 0 ? NC : nc); ++jy) {
-      const T wyz = row[1][jy] * row[2][jz];
-      const size_t off = (size_t)G.gc[0] * ((base[1] + jy) + (size_t)G.gc[1] * (base[2] + jz));
+      const size_t off = (size_t)G.gc[0] * ((base[1] + jy) + (size_t)G.gc[1] * (base[2] + jz)) + base[0];
+      T sx = T(0);
 #pragma unroll
-      for (int jx = 0; jx < (NC > 0 ? NC : nc); ++jx) sum += row[0][jx] * wyz * xc[off + base[0] + jx];
+      for (int jx = 0; jx < (NC > 0 ? NC : nc); ++jx) sx = fma(row[0][jx], xc[off + jx], sx);
+      sy = fma(row[1][jy], sx, sy);
     }
+    sum = fma(row[2][jz], sy, sum);
+  }
   xf[gid] += sum;
 }
 
