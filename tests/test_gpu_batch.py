@@ -111,14 +111,16 @@ def test_32_right_hand_sides():
         assert rel(xs[r].cpu().numpy(), x.cpu().numpy()) <= 1e-9
 
 
-@pytest.mark.parametrize("precision,deform", [(0, 0), (1, 1)])
-def test_apply_multi_equals_single_applies(precision, deform):
-    """One launch per pass for nv vectors of one operator: each row equals the single apply."""
+@pytest.mark.parametrize("precision,deform,vec_dtype", [(0, 0, torch.float64), (1, 1, torch.float32),
+                                                      (0, 1, torch.float32)])
+def test_apply_multi_equals_single_applies(precision, deform, vec_dtype):
+    """One launch per pass for nv vectors of one operator: each row equals the single apply
+    (also FP32 vectors on a context whose cycle runs in FP64: scratch made on first use)."""
     from paper_1910_01900_gb300 import Context
     m, k, nv = (6, 4, 5), 3, 7
     ctx = Context(m, k, deform=deform, precision=precision)
     n = ctx.num_dofs()
-    dt = torch.float64 if precision == 0 else torch.float32
+    dt = vec_dtype
     U = torch.stack([torch.as_tensor(sipg_inputs.uniform(n, 70 + r)) for r in range(nv)]).to(DEV, dt)
     V = torch.full_like(U, float("nan"))
     ctx.apply_multi(U, V)
@@ -129,8 +131,8 @@ def test_apply_multi_equals_single_applies(precision, deform):
         ctx.apply(U[r].contiguous(), ref)
         torch.cuda.synchronize()
         assert torch.equal(V[r], ref), r
-        if precision == 0:
-            assert rel(V[r].cpu().numpy(), o.apply(U[r].cpu().numpy())) <= 1e-12
+        assert rel(V[r].cpu().numpy(), o.apply(U[r].cpu().numpy().astype(np.float64))) <= \
+            (1e-12 if dt == torch.float64 else 1e-5)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -163,6 +165,13 @@ def test_solve_multi_equals_single_solves(precision):
     infos2 = ctx.solve_multi(B[:2].contiguous(), X2, rtol=1e-10)
     torch.cuda.synchronize()
     assert torch.equal(X2, X[:2]) and [i.iterations for i in infos2] == [i.iterations for i in infos[:2]]
+    # more right-hand sides than before: the work set grows, the cycle graph is captured anew
+    B3 = torch.cat([B, B[:3] * -2.0])
+    X3 = torch.zeros_like(B3)
+    infos3 = ctx.solve_multi(B3, X3, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert torch.equal(X3[:nrhs], X) and all(i.converged for i in infos3)
+    assert rel(X3[nrhs:].cpu().numpy(), -2.0 * X[:3].cpu().numpy()) <= 1e-9
 
 
 def test_solve_multi_zero_and_nan_rows():
