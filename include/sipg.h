@@ -265,9 +265,11 @@ sipg_status sipg_batch_solve(sipg_batch *batch, const double *const *b_dev, doub
  * (k+1)^3 values; smoothing step x <- x + c s y per cell.  BF16 weights and
  * activations, FP32 accumulation (tensor cores), FP32 master weights.  The
  * solve stays a flexible CG, so its result does not depend on the network;
- * the Chebyshev cycle's average rate (measured while generating the data)
- * judges each learned step and a worse step switches the solve back to
- * Chebyshev (sipg_solve_info.fell_back). */
+ * the Chebyshev cycle's average rate rho (measured while generating the data)
+ * judges each learned step by residual reduction per unit time: a step that
+ * reduces the residual by less than rho^(t_learned / t_chebyshev), with t the
+ * time of one iteration with each cycle (measured after training), switches
+ * the solve back to Chebyshev (sipg_solve_info.fell_back). */
 typedef struct {
   int npairs, epochs, steps;      /* training pairs, epochs, Adam steps          */
   double loss_first, loss_last;   /* mean squared error, first and last epoch    */
@@ -276,6 +278,8 @@ typedef struct {
   double seconds;                 /* wall time of data generation and training  */
   double target_max;              /* largest |e|/s of the data (before scaling)  */
   double nonfinite;               /* number of non-finite targets (0 expected)   */
+  double iter_ms_chebyshev;       /* one flexible-CG iteration's V-cycle plus    */
+  double iter_ms_learned;         /* outer apply, with each smoother (ms)        */
 } sipg_train_info;
 /* Generates npairs (cell residual -> cell error) pairs from the plain cycle
  * and trains the network with Adam (batches of 256).  For the first 4

@@ -154,7 +154,9 @@ def run_learned(steps, stream, npairs=100000, epochs=20):
                                                            "loss_first": info.loss_first,
                                                            "loss_last": info.loss_last,
                                                            "seconds": info.seconds,
-                                                           "chebyshev_rate": info.cheb_rate}}
+                                                           "chebyshev_rate": info.cheb_rate,
+                                                           "iter_ms_chebyshev": info.iter_ms_chebyshev,
+                                                           "iter_ms_learned": info.iter_ms_learned}}
     print(json.dumps({"workload": "curved32_k4", "train": out["train"]}), flush=True)
     for which, label in ((0, "chebyshev"), (1, "learned")):
         ctx.set_smoother(which, 2, 2) if which else ctx.set_smoother(0)

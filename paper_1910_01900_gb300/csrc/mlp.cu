@@ -5,10 +5,14 @@
 // plain multigrid produces, used in place of the Chebyshev smoother on the
 // finest level inside flexible CG.
 //
-// GEMM: C[M x N] = sum_k A(m, k) B(k, n) with A, B in BF16 addressed through
-// row and column strides (so transposed operands need no copy), FP32
-// accumulation on mma.sync m16n8k16 tensor-core instructions, 64 x 64 block
-// tiles (4 warps of 32 x 32), optional bias, ReLU and BF16 or FP32 output.
+// GEMMs: the forward pass (the smoother's inference inside the V-cycle and
+// training's forward) runs on the tcgen05 tensor cores with the accumulator in
+// tensor memory (gemm_tc_kernel below; activations and transposed weights both
+// K-contiguous).  The backward pass's GEMMs, whose operands are transposed
+// through strides, use C[M x N] = sum_k A(m, k) B(k, n) with A, B in BF16
+// addressed through row and column strides, FP32 accumulation on mma.sync
+// m16n8k16 instructions, 64 x 64 block tiles (4 warps of 32 x 32), optional
+// bias, ReLU and BF16 or FP32 output.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -106,6 +110,241 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
       }
 }
 
+// ---------------------------------------------------- tcgen05 GEMM
+// C[M x N] = A[M x K] Bt[N x K]^T on the 5th-generation tensor cores, for the
+// network's forward pass (activations times weights, both K-contiguous; the
+// weights are kept transposed for it).  One CTA computes a 128 x N tile (N =
+// the whole output width, a multiple of 16 up to 256) with tcgen05.mma
+// (kind::f16, BF16 operands, FP32 accumulator in tensor memory).  Both
+// operands are staged through shared memory in the K-major canonical layout
+// without swizzle: 8-row x 16-byte core matrices, adjacent along K at 128
+// bytes (leading byte offset), adjacent along M/N at (KC/8) x 128 bytes
+// (stride byte offset).  K runs in chunks of KC = 64 through two shared-memory
+// stages: the 128 threads copy the 16-byte pieces of chunk i + 1 with cp.async
+// (zero-filled outside the matrices) while the tensor core works on chunk i;
+// once a chunk has landed it is made visible to the tensor core
+// (fence.proxy.async) and one thread issues four K = 16 MMAs and commits them
+// to the stage's mbarrier, which every thread waits on (bounded) before the
+// stage is refilled.  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 = tile rows),
+// adds the bias, applies ReLU and stores FP32 or BF16.
+constexpr int TC_M = 128, TC_KC = 64;
+// one stage: A (128 x 64 bf16 = 16 KB) then B (up to 256 x 64 bf16 = 32 KB);
+// the two stages interleave: stage b of A at b x TC_STAGE, of B at 16 KB + b x TC_STAGE
+constexpr int TC_STAGE = 48 * 1024;
+// dynamic shared memory per CTA: two stages, 96 KB, which also keeps at most
+// two CTAs on an SM, so their tensor-memory columns (<= 256 each) always fit
+// in the SM's 512 and tcgen05.alloc never waits
+constexpr int TC_SMEM = 2 * TC_STAGE;
+constexpr int TC_WAIT_LIMIT = 1 << 22;   // mbarrier polls before a CTA gives up
+__device__ int g_tc_timeout;             // set by a CTA whose MMA wait ran out
+
+struct TcArgs {
+  const __nv_bfloat16 *A;    // [M][lda], K contiguous
+  const __nv_bfloat16 *Bt;   // [N][ldb], K contiguous
+  long lda, ldb;
+  int M, N, K;
+  const float *bias;   // [N] or null
+  int relu;
+  float *Cf;           // fp32 output (or null)
+  __nv_bfloat16 *Cb;   // bf16 output (or null)
+  long ldc;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (all >> 4), fixed version bits 46-48 = 0b001, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+// byte offset of the 16-byte piece (row r, K group g of 8) in a core-matrix tile
+__device__ __forceinline__ uint32_t tc_core_off(int r, int g) {
+  return (uint32_t)(((r >> 3) * (TC_KC >> 3) + g) * 128 + (r & 7) * 16);
+}
+
+__device__ __forceinline__ void tc_copy16(uint32_t dst, const void *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(128) gemm_tc_kernel(const TcArgs g, const uint32_t ncols) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ uint32_t tmem_slot;
+  // stage b: A tile (TC_M x TC_KC bf16) at sA + b TC_STAGE, B tile (N x TC_KC) at sB + b TC_STAGE
+  const uint32_t sA = smem_u32(tc_smem);
+  const uint32_t sB = smem_u32(tc_smem + TC_M * TC_KC * 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_M;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  // instruction descriptor: D FP32 (bit 4), A and B BF16 (bits 7, 10), both
+  // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(g.N >> 3) << 17) |
+                         ((uint32_t)(TC_M >> 4) << 24);
+  constexpr int G = TC_KC / 8;   // 16-byte groups per row and chunk
+  // two stages: the copies of chunk i + 1 are in flight while the tensor core
+  // works on chunk i.  Stage b holds chunks b, b + 2, ...; barrier b completes
+  // once per MMA batch issued on stage b (parity = use count & 1).
+  const int nch = (g.K + TC_KC - 1) / TC_KC;
+  auto stage = [&](int chunk) {
+    const int k0 = chunk * TC_KC;
+    const uint32_t a0 = sA + (uint32_t)(chunk & 1) * TC_STAGE, b0 = sB + (uint32_t)(chunk & 1) * TC_STAGE;
+    for (int i = tid; i < TC_M * G; i += 128) {   // K group fastest: each row read in 128-byte runs
+      const int r = i / G, q = i - r * G;
+      const bool valid = m0 + r < g.M && k0 + 8 * q < g.K;
+      tc_copy16(a0 + tc_core_off(r, q), valid ? g.A + (long)(m0 + r) * g.lda + k0 + 8 * q : g.A, valid);
+    }
+    for (int i = tid; i < g.N * G; i += 128) {
+      const int r = i / G, q = i - r * G;
+      const bool valid = k0 + 8 * q < g.K;
+      tc_copy16(b0 + tc_core_off(r, q), valid ? g.Bt + (long)r * g.ldb + k0 + 8 * q : g.Bt, valid);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  auto mma_wait = [&](int chunk) {   // every thread: the MMAs of `chunk` are done
+    return tc_wait(smem_u32(&mbar[chunk & 1]), (uint32_t)((chunk >> 1) & 1)) ? 1 : 0;
+  };
+  int ok = 1, issued = -1;   // last chunk whose MMAs were issued
+  stage(0);
+  for (int i = 0; i < nch && ok; ++i) {
+    if (i + 1 < nch) {
+      // stage (i + 1) & 1 was last read by the MMAs of chunk i - 1
+      if (i >= 1) ok = __syncthreads_and(mma_wait(i - 1));
+      if (!ok) break;
+      stage(i + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // chunk i has landed
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = sA + (uint32_t)(i & 1) * TC_STAGE, b0 = sB + (uint32_t)(i & 1) * TC_STAGE;
+#pragma unroll
+      for (int kk = 0; kk < TC_KC; kk += 16) {
+        const uint64_t ad = tc_desc(a0 + (kk >> 3) * 128, 128, G * 128);
+        const uint64_t bd = tc_desc(b0 + (kk >> 3) * 128, 128, G * 128);
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[i & 1]))
+                   : "memory");
+    }
+    issued = i;
+  }
+  // MMAs complete in issue order: the last chunk's barrier covers them all
+  if (ok) {
+    ok = __syncthreads_and(mma_wait(nch - 1));
+  } else {
+    // a wait ran out: drain the copies, give the MMAs in flight one more
+    // bounded wait, then write nothing and free the tensor memory below
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (issued >= 0) (void)mma_wait(issued);
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int gm = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < g.N; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+          "[%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (gm < g.M) {
+        // the thread's 16 consecutive outputs of its row go out as whole
+        // 16-byte vectors (full 32-byte sectors), not as scattered scalars
+        float x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          x[j] = __uint_as_float(v[j]);
+          if (g.bias) x[j] += g.bias[c0 + j];
+          if (g.relu) x[j] = fmaxf(x[j], 0.f);
+        }
+        if (g.Cf) {
+          float4 *dst = reinterpret_cast<float4 *>(g.Cf + (long)gm * g.ldc + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        }
+        if (g.Cb) {
+          uint32_t w[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            w[q] = pack2(__float2bfloat16(x[2 * q]), __float2bfloat16(x[2 * q + 1]));
+          uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + (long)gm * g.ldc + c0);
+          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_tc_timeout, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// Weights transposed for the forward GEMM: Wt[n][k] = W[k][n] for the three
+// layers (W1 [Fp][H], W2 [H][H], W3 [H][No] in the parameter vector).
+__global__ void transpose_weights_kernel(const __nv_bfloat16 *Pb, long oW1, long oW2, long oW3, int Fp, int H,
+                                         int No, __nv_bfloat16 *Pt) {
+  const long n1 = (long)H * Fp, n2 = (long)H * H, n3 = (long)No * H;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3; i += (long)gridDim.x * blockDim.x) {
+    if (i < n1) {
+      const long n = i / Fp, k = i - n * Fp;
+      Pt[i] = Pb[oW1 + k * H + n];
+    } else if (i < n1 + n2) {
+      const long j = i - n1, n = j / H, k = j - n * H;
+      Pt[i] = Pb[oW2 + k * H + n];
+    } else {
+      const long j = i - n1 - n2, n = j / H, k = j - n * H;
+      Pt[i] = Pb[oW3 + k * No + n];
+    }
+  }
+}
+
 // Features of cells (first cell c0, count nc) from a DG residual: the cell's
 // n^3 values, then per face (-x,+x,-y,+y,-z,+z) the neighbour's n^2 values on
 // the shared face (zeros on the boundary); scaled by their RMS.  One warp per cell.
@@ -143,8 +382,11 @@ __global__ void gather_features_kernel(const T *r, int n, int m0, int m1, int m2
   // a cell whose local residual is (numerically) zero gets zero inputs and scale 0
   const double s = sqrt(ss / nf);
   const bool ok = s > 1e-30 && s < 1e30;
+  // one reciprocal per cell, then FP32 products (the inputs are BF16 anyway;
+  // an FP64 division per value would cost more than the whole network here)
+  const float inv = ok ? (float)(1.0 / s) : 0.f;
   for (int j = lane; j < ldx; j += 32)
-    X[(size_t)w * ldx + j] = __float2bfloat16(ok && j < nf ? (float)(value(j) / s) : 0.f);
+    X[(size_t)w * ldx + j] = __float2bfloat16(j < nf ? (float)value(j) * inv : 0.f);
   if (lane == 0) scale[w] = ok ? (float)s : 0.f;
 }
 
@@ -268,10 +510,56 @@ cudaError_t mlp_gemm(const void *A, long sam, long sak, const void *B, long sbk,
                      const float *bias, int relu, float *Cf, void *Cb, long ldc, int accumulate, cudaStream_t s) {
   GemmArgs g{(const __nv_bfloat16 *)A, sam, sak, (const __nv_bfloat16 *)B, sbk, sbn, M, N, K, bias, relu, Cf,
              (__nv_bfloat16 *)Cb, ldc, accumulate};
+  if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
   gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t mlp_gemm_tc(const void *A, long lda, const void *Bt, long ldb, int M, int N, int K, const float *bias,
+                        int relu, float *Cf, void *Cb, long ldc, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  // 16-byte pieces in and out: K-contiguous rows and output rows start on 16 bytes
+  if (N < 16 || N > 256 || N % 16 || K < 16 || K % 16 || lda % 8 || ldb % 8 || ldc % 8 || ((uintptr_t)A & 15) ||
+      ((uintptr_t)Bt & 15) || ((uintptr_t)Cf & 15) || ((uintptr_t)Cb & 15))
+    return cudaErrorInvalidValue;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)N) ncols <<= 1;
+  TcArgs g{(const __nv_bfloat16 *)A, (const __nv_bfloat16 *)Bt, lda, ldb, M, N, K, bias, relu, Cf,
+           (__nv_bfloat16 *)Cb, ldc};
+  gemm_tc_kernel<<<(M + TC_M - 1) / TC_M, 128, TC_SMEM, s>>>(g, ncols);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_transpose_weights(const void *Pb, long oW1, long oW2, long oW3, int Fp, int H, int No, void *Pt,
+                                  cudaStream_t s) {
+  const long n = (long)H * Fp + (long)H * H + (long)No * H;
+  transpose_weights_kernel<<<(int)std::min<long>(blocks(n), 152L * 8), 256, 0, s>>>(
+      (const __nv_bfloat16 *)Pb, oW1, oW2, oW3, Fp, H, No, (__nv_bfloat16 *)Pt);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_tc_status(int *timed_out) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_timeout, sizeof(int));
+  if (e == cudaSuccess && v) {
+    const int z = 0;
+    e = cudaMemcpyToSymbol(g_tc_timeout, &z, sizeof(int));
+  }
+  *timed_out = v;
+  return e;
 }
 
 template <typename T>

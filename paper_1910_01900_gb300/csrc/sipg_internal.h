@@ -273,6 +273,16 @@ cudaError_t seg_update_p(const Seg *segs, int np, const double *sc, int sc_strid
 // ---- learned smoother network (mlp.cu); bf16 buffers passed as void*
 cudaError_t mlp_gemm(const void *A, long sam, long sak, const void *B, long sbk, long sbn, int M, int N, int K,
                      const float *bias, int relu, float *Cf, void *Cb, long ldc, int accumulate, cudaStream_t s);
+// C = A Bt^T on tcgen05 tensor cores (A [M][lda], Bt [N][ldb], both K
+// contiguous, BF16; N a multiple of 16 up to 256, K a multiple of 16)
+cudaError_t mlp_gemm_tc(const void *A, long lda, const void *Bt, long ldb, int M, int N, int K, const float *bias,
+                        int relu, float *Cf, void *Cb, long ldc, cudaStream_t s);
+// Pt = the three weight matrices transposed (K contiguous) for mlp_gemm_tc
+cudaError_t mlp_transpose_weights(const void *Pb, long oW1, long oW2, long oW3, int Fp, int H, int No, void *Pt,
+                                  cudaStream_t s);
+// reads and clears the flag a tensor-core GEMM sets when its MMA completion
+// wait ran out (the CTA then wrote no output)
+cudaError_t mlp_tc_status(int *timed_out);
 template <typename T>
 cudaError_t mlp_gather(const T *r, int n, const int m[3], const int *cells, int c0, int nc, void *X, int ldx,
                        float *scale, cudaStream_t s);

@@ -48,12 +48,18 @@ struct sipg_ctx {
     float cscale = 1.f;    // output scale c: correction = c * s * y
     float *P = nullptr, *M = nullptr, *V = nullptr, *G = nullptr;   // fp32 params, Adam moments, grads
     void *Pb = nullptr;    // bf16 copy of P
+    void *Pt = nullptr;    // bf16 weights transposed (K contiguous) for the tensor-core forward pass
+    long oT1 = 0, oT2 = 0, oT3 = 0;
     // inference / training buffers for up to `rows` rows
     long rows = 0;
     void *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dH = nullptr;
     float *Y = nullptr, *dYf = nullptr, *scale = nullptr;
     double *loss = nullptr;
     double rho_cheb = 1.0;  // average rate of the Chebyshev cycle (judge of the learned one)
+    // time of one flexible-CG iteration with each cycle (V-cycle + outer
+    // operator), measured after training; the learned cycle must reduce the
+    // residual at least as fast per unit time as the Chebyshev cycle
+    double t_iter_cheb = 0, t_iter_learned = 0;
     int steps_pre = 2, steps_post = 2;
   } net;
   // Several right-hand sides at once (sipg_solve_multi, sipg_operator_apply_multi):
@@ -899,7 +905,11 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
     // the Chebyshev cycle judges the learned one: a step that reduces the
     // residual less than the Chebyshev cycle's average rate switches the rest
     // of the solve back to Chebyshev (flexible CG keeps the iteration valid)
-    if (c->use_learned && rn > c->net.rho_cheb * rprev) {
+    // (rate per unit time: a cheaper learned iteration may reduce less per step)
+    const double tr = (c->net.t_iter_cheb > 0 && c->net.t_iter_learned > 0)
+                          ? c->net.t_iter_learned / c->net.t_iter_cheb
+                          : 1.0;
+    if (c->use_learned && rn > std::pow(c->net.rho_cheb, tr) * rprev) {
       c->use_learned = 0;
       fell_back = 1;
     }
@@ -909,6 +919,14 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
   }
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
+  if (learned_at_start) {   // a tensor-core GEMM of the learned cycle that timed out wrote nothing
+    int timed_out = 0;
+    CK(mlp_tc_status(&timed_out));
+    if (timed_out) {
+      c->err = "a tensor-core GEMM of the learned smoother timed out waiting for its MMAs";
+      st = SIPG_ETIMEOUT;
+    }
+  }
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
@@ -937,6 +955,12 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
 // residuals, scaled by their RMS; output: the cell's correction) that stands in
 // for the Chebyshev smoother on the finest level.  Not in the paper.
 
+// the transposed BF16 weights follow every change of the BF16 weights
+void net_weights_updated(sipg_ctx *c) {
+  auto &N = c->net;
+  CK(mlp_transpose_weights(N.Pb, N.oW1, N.oW2, N.oW3, N.Fp, N.H, N.No, N.Pt, c->stream));
+}
+
 void net_setup(sipg_ctx *c, long rows) {
   auto &N = c->net;
   const Level &F = c->lv[c->L];
@@ -957,6 +981,10 @@ void net_setup(sipg_ctx *c, long rows) {
     N.V = dalloc<float>(c, N.np);
     N.G = dalloc<float>(c, N.np);
     N.Pb = dalloc<uint16_t>(c, N.np);
+    N.oT1 = 0;
+    N.oT2 = (long)N.H * N.Fp;
+    N.oT3 = N.oT2 + (long)N.H * N.H;
+    N.Pt = dalloc<uint16_t>(c, N.oT3 + (long)N.No * N.H);
     N.loss = dalloc<double>(c, 2);
     // He-uniform initial weights from the counter-based generator, zero biases
     std::vector<float> h(N.np, 0.f);
@@ -971,6 +999,7 @@ void net_setup(sipg_ctx *c, long rows) {
     fill(N.oW3, N.H, N.H, N.No, 4003);
     CK(cudaMemcpyAsync(N.P, h.data(), N.np * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CK(mlp_f2bf(N.P, N.Pb, N.np, c->stream));
+    net_weights_updated(c);
     CK(cudaStreamSynchronize(c->stream));
     N.ready = true;
   }
@@ -994,9 +1023,18 @@ inline void *bfm(void *base, long off) { return (uint16_t *)base + off; }
 void net_forward(sipg_ctx *c, const void *X, long ldx, int B) {
   auto &N = c->net;
   cudaStream_t s = c->stream;
-  CK(mlp_gemm(X, ldx, 1, bf(N.Pb, N.oW1), N.H, 1, B, N.H, N.Fp, N.P + N.ob1, 1, nullptr, N.H1, N.H, 0, s));
-  CK(mlp_gemm(N.H1, N.H, 1, bf(N.Pb, N.oW2), N.H, 1, B, N.H, N.H, N.P + N.ob2, 1, nullptr, N.H2, N.H, 0, s));
-  CK(mlp_gemm(N.H2, N.H, 1, bf(N.Pb, N.oW3), N.No, 1, B, N.No, N.H, N.P + N.ob3, 0, N.Y, nullptr, N.No, 0, s));
+  // one layer: out = act(in W + b) with W [K][Nout]; on the tcgen05 tensor
+  // cores (transposed weights) when the output width fits one MMA tile
+  auto layer = [&](const void *in, long ld, long oW, long oT, int K, int Nout, const float *bias, int relu,
+                   float *Cf, void *Cb) {
+    if (Nout % 16 == 0 && Nout <= 256)
+      CK(mlp_gemm_tc(in, ld, bf(N.Pt, oT), K, B, Nout, K, bias, relu, Cf, Cb, Nout, s));
+    else
+      CK(mlp_gemm(in, ld, 1, bf(N.Pb, oW), Nout, 1, B, Nout, K, bias, relu, Cf, Cb, Nout, 0, s));
+  };
+  layer(X, ldx, N.oW1, N.oT1, N.Fp, N.H, N.P + N.ob1, 1, nullptr, N.H1);
+  layer(N.H1, N.H, N.oW2, N.oT2, N.H, N.H, N.P + N.ob2, 1, nullptr, N.H2);
+  layer(N.H2, N.H, N.oW3, N.oT3, N.H, N.No, N.P + N.ob3, 0, N.Y, nullptr);
 }
 
 // gradients of the mean squared error over B rows (X row stride ldx, T row stride ldt) into N.G
@@ -1152,6 +1190,7 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
       ++step;
       const float lr = 1e-3f * (ep >= epochs * 2 / 3 ? 0.3f : 1.0f);
       CK(mlp_adam(N.P, N.M, N.V, N.G, N.np, lr, step, N.Pb, c->stream));
+      net_weights_updated(c);
     }
     double l;
     CK(cudaMemcpyAsync(&l, N.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1169,6 +1208,32 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   CK(cudaStreamSynchronize(c->stream));
   N.trained = true;
   // graphs of a learned cycle captured earlier hold old weights only by pointer: nothing to redo
+  {
+    // time one iteration's work with each cycle: V-cycle on fr plus one outer operator application
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto iter_ms = [&](int learned) {
+      c->use_learned = learned;
+      vcycle_body(c, c->fr, c->fz);
+      apply_level<double>(c, c->L, c->fz, c->fv, 0);
+      CK(cudaEventRecord(e0, c->stream));
+      for (int r = 0; r < 3; ++r) {
+        vcycle_body(c, c->fr, c->fz);
+        apply_level<double>(c, c->L, c->fz, c->fv, 0);
+      }
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      return ms / 3.0;
+    };
+    N.t_iter_cheb = iter_ms(0);
+    N.t_iter_learned = iter_ms(1);
+    c->use_learned = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->npairs = (int)R;
@@ -1181,6 +1246,8 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
     info->target_max = tmax;
     info->nonfinite = (double)hbad;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->iter_ms_chebyshev = N.t_iter_cheb;
+    info->iter_ms_learned = N.t_iter_learned;
   }
   return SIPG_OK;
 }
@@ -1514,9 +1581,25 @@ sipg_status sipg_set_tile_shape(sipg_ctx *c, int level, int precision, int pass,
   return SIPG_OK;
 }
 
+// A tensor-core GEMM whose MMA wait ran out wrote no output: report it.
+static sipg_status tc_check(sipg_ctx *c) {
+  CK(cudaStreamSynchronize(c->stream));
+  int timed_out = 0;
+  CK(mlp_tc_status(&timed_out));
+  if (timed_out) {
+    c->err = "a tensor-core GEMM of the learned smoother timed out waiting for its MMAs";
+    return SIPG_ETIMEOUT;
+  }
+  return SIPG_OK;
+}
+
 sipg_status sipg_smoother_train(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_train_info *info) {
   if (!c || !c->solver || npairs < 256 || npairs > 10000000 || epochs < 1) return SIPG_EINVAL;
-  return guarded(c, [&]() -> sipg_status { return train_impl(c, npairs, epochs, seed, info); });
+  return guarded(c, [&]() -> sipg_status {
+    const sipg_status st = train_impl(c, npairs, epochs, seed, info);
+    const sipg_status tc = tc_check(c);
+    return st != SIPG_OK ? st : tc;
+  });
 }
 
 sipg_status sipg_set_smoother(sipg_ctx *c, int which, int steps_pre, int steps_post) {
@@ -1564,6 +1647,7 @@ sipg_status sipg_mlp_params(sipg_ctx *c, int set, float *host) {
     if (set) {
       CK(cudaMemcpyAsync(N.P, host, N.np * sizeof(float), cudaMemcpyHostToDevice, c->stream));
       CK(mlp_f2bf(N.P, N.Pb, N.np, c->stream));
+      net_weights_updated(c);
     } else {
       CK(cudaMemcpyAsync(host, N.P, N.np * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     }
@@ -1580,7 +1664,7 @@ sipg_status sipg_mlp_forward(sipg_ctx *c, const float *X, int B, float *Y) {
     CK(mlp_pad_f2bf(X, B, N.F, N.Fp, N.X, c->stream));
     net_forward(c, N.X, N.Fp, B);
     CK(cudaMemcpyAsync(Y, N.Y, (size_t)B * N.No * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-    return SIPG_OK;
+    return tc_check(c);
   });
 }
 
@@ -1598,7 +1682,7 @@ sipg_status sipg_mlp_gradients(sipg_ctx *c, const float *X, const float *T, int 
     CK(cudaMemcpyAsync(&l, N.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (loss) *loss = l;
-    return SIPG_OK;
+    return tc_check(c);
   });
 }
 

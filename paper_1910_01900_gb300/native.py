@@ -32,7 +32,8 @@ class TrainInfo(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int), ("epochs", ctypes.c_int), ("steps", ctypes.c_int),
                 ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("out_scale", ctypes.c_double),
                 ("cheb_rate", ctypes.c_double), ("seconds", ctypes.c_double), ("target_max", ctypes.c_double),
-                ("nonfinite", ctypes.c_double)]
+                ("nonfinite", ctypes.c_double), ("iter_ms_chebyshev", ctypes.c_double),
+                ("iter_ms_learned", ctypes.c_double)]
 
 
 class Mesh(ctypes.Structure):

@@ -69,6 +69,27 @@ def test_forward_and_gradients_match_cpu_network():
         assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 3e-2
 
 
+@pytest.mark.parametrize("k,B", [(4, 1), (4, 129), (5, 300), (6, 77)])
+def test_forward_row_tails_and_widths(k, B):
+    """The forward pass runs on tcgen05 tensor cores in 128-row tiles: partial last tiles,
+    a single row, and an output width above one MMA tile (k = 6: 343 -> 352 columns, the
+    mma.sync fallback) all match the CPU network."""
+    ctx = _ctx(3, k)
+    sh = ctx.mlp_shape()
+    rng = np.random.default_rng(11 + B)
+    flat = ctx.mlp_params()
+    flat[:] = rng.standard_normal(flat.size).astype(np.float32) * 0.05
+    ctx.mlp_params(flat)
+    Ws, bs = _split(flat, sh)
+    X = rng.standard_normal((B, sh["in_dim"])).astype(np.float32)
+    Y = torch.full((B * sh["out_pad"],), float("nan"), dtype=torch.float32, device=DEV)
+    ctx.mlp_forward(torch.as_tensor(X).to(DEV), Y)
+    yref, _ = mlp.forward(X.astype(np.float64), Ws, bs, bf16=True)
+    y = Y.cpu().numpy().reshape(B, sh["out_pad"])[:, :sh["out_dim"]]
+    assert np.all(np.isfinite(y))
+    assert np.linalg.norm(y - yref) / np.linalg.norm(yref) <= 1e-2
+
+
 def test_training_and_learned_solve():
     """Train on pairs from the plain cycle; the FCG solve still reaches 1e-10."""
     m, k = 8, 3
