@@ -280,17 +280,23 @@ typedef struct {
   double nonfinite;               /* number of non-finite targets (0 expected)   */
   double iter_ms_chebyshev;       /* one flexible-CG iteration's V-cycle plus    */
   double iter_ms_learned;         /* outer apply, with each smoother (ms)        */
+  double damping;                 /* omega applied to c after training           */
+  double step_reduction;          /* ||r - omega A d|| / ||r|| of that step      */
 } sipg_train_info;
 /* Generates npairs (cell residual -> cell error) pairs from the plain cycle
  * and trains the network with Adam (batches of 256).  For the first 4
  * flexible-CG iterates of 4 seeded uniform right-hand sides, the cycle's input
  * b_v = r_j and its exact correction x* = A^-1 b_v (solved to 1e-12) give
- * pairs at seeded random cells of two kinds: before smoothing (b_v, x*) and
- * after pre-smoothing and the coarse-grid correction (b_v - A x, x* - x),
- * the state a post-smoother works on. */
+ * pairs at seeded random cells after pre-smoothing and the coarse-grid
+ * correction (b_v - A x, x* - x): the high-frequency error a smoother works
+ * on.  Then the step is damped: on the last such residual r the output scale
+ * c is multiplied by the omega minimising ||r - omega A d|| for the step d
+ * taken from x = 0. */
 sipg_status sipg_smoother_train(sipg_ctx *ctx, int npairs, int epochs, uint64_t seed, sipg_train_info *info);
 /* which = 0: Chebyshev (default); 1: learned (trained network required), with
- * steps_pre and steps_post network steps around the coarse correction. */
+ * steps_pre and steps_post network steps around the coarse correction;
+ * steps_pre = 0 keeps Chebyshev pre-smoothing (the network is trained on the
+ * post-smoothing state), 1..16 network steps; steps_post 1..16. */
 sipg_status sipg_set_smoother(sipg_ctx *ctx, int which, int steps_pre, int steps_post);
 /* Network shape: in_dim (and padded width), hidden width, out_dim (and
  * padded width), number of parameters.  Flat parameter layout (FP32):

@@ -156,10 +156,12 @@ def run_learned(steps, stream, npairs=100000, epochs=20):
                                                            "seconds": info.seconds,
                                                            "chebyshev_rate": info.cheb_rate,
                                                            "iter_ms_chebyshev": info.iter_ms_chebyshev,
-                                                           "iter_ms_learned": info.iter_ms_learned}}
+                                                           "iter_ms_learned": info.iter_ms_learned,
+                                                           "damping": info.damping,
+                                                           "step_reduction": info.step_reduction}}
     print(json.dumps({"workload": "curved32_k4", "train": out["train"]}), flush=True)
-    for which, label in ((0, "chebyshev"), (1, "learned")):
-        ctx.set_smoother(which, 2, 2) if which else ctx.set_smoother(0)
+    for which, pre, post, label in ((0, 0, 1, "chebyshev"), (1, 0, 1, "learned"), (1, 2, 2, "learned_2_2")):
+        ctx.set_smoother(which, pre, post)
 
         def solve():
             x.zero_()
@@ -169,6 +171,16 @@ def run_learned(steps, stream, npairs=100000, epochs=20):
         out[label] = {"ms": ms, "iterations": r.iterations, "converged": bool(r.converged), "n10": r.n10,
                       "fell_back": int(r.fell_back)}
     out["learned_speedup"] = out["chebyshev"]["ms"] / out["learned"]["ms"]
+    # the plain FP64 multigrid on the same problem and right-hand side
+    ctx64 = Context(m, k, deform=1, precision=0, stream=stream)
+
+    def solve64():
+        x.zero_()
+        return ctx64.solve(b, x, rtol=1e-10, maxit=300)
+    with torch.cuda.stream(stream):
+        ms, r = _timed(solve64, steps, stream)
+    out["plain_fp64_mg"] = {"ms": ms, "iterations": r.iterations, "converged": bool(r.converged), "n10": r.n10}
+    out["learned_speedup_vs_plain_fp64_mg"] = ms / out["learned"]["ms"]
     return out
 
 

@@ -60,7 +60,9 @@ struct sipg_ctx {
     // operator), measured after training; the learned cycle must reduce the
     // residual at least as fast per unit time as the Chebyshev cycle
     double t_iter_cheb = 0, t_iter_learned = 0;
-    int steps_pre = 2, steps_post = 2;
+    double omega = 1;       // damping applied to the trained output scale
+    double step_reduction = 1;   // residual reduction of one damped step on that data
+    int steps_pre = 0, steps_post = 1;   // Chebyshev pre-smoothing, one network post-step
   } net;
   // Several right-hand sides at once (sipg_solve_multi, sipg_operator_apply_multi):
   // nv vectors of every level's V-cycle data and of the cell-kernel scratch,
@@ -353,8 +355,8 @@ T *vcycle_rec(sipg_ctx *c, int l) {
   T *x = lvec<T>(c, l, 1), *xt = lvec<T>(c, l, 3);
   const int ns = c->prm.cheb_degree;
   const bool learned = (l == c->L) && c->use_learned;
-  if (learned) learned_smooth<T>(c, b, x, c->net.steps_pre, true);
-  else chebyshev<T>(c, l, b, x, xt, ns, true);
+  if (learned && c->net.steps_pre > 0) learned_smooth<T>(c, b, x, c->net.steps_pre, true);
+  else chebyshev<T>(c, l, b, x, xt, ns, true);   // steps_pre = 0: Chebyshev pre-smoothing
   apply_level<T>(c, l, x, lvec<T>(c, l, 2), 2, nullptr, nullptr, b);
   restrict_level<T>(c, l, lvec<T>(c, l, 2), lvec<T>(c, l - 1, 0));
   const T *xc = vcycle_rec<T>(c, l - 1);
@@ -1079,6 +1081,32 @@ void learned_smooth(sipg_ctx *c, const T *b, T *x, int steps, bool zero_start) {
 template void learned_smooth<double>(sipg_ctx *, const double *, double *, int, bool);
 template void learned_smooth<float>(sipg_ctx *, const float *, float *, int, bool);
 
+// Time of one flexible-CG iteration's work with the Chebyshev (learned = 0)
+// or the learned cycle: a V-cycle on fr plus one outer operator application
+// (mean of 3 after one warm-up, CUDA events on the context stream).
+double iteration_ms(sipg_ctx *c, int learned) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int save = c->use_learned;
+  c->use_learned = learned;
+  vcycle_body(c, c->fr, c->fz);
+  apply_level<double>(c, c->L, c->fz, c->fv, 0);
+  CK(cudaEventRecord(e0, c->stream));
+  for (int r = 0; r < 3; ++r) {
+    vcycle_body(c, c->fr, c->fz);
+    apply_level<double>(c, c->L, c->fz, c->fv, 0);
+  }
+  CK(cudaEventRecord(e1, c->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  c->use_learned = save;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / 3.0;
+}
+
 sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_train_info *info) {
   auto t0 = std::chrono::steady_clock::now();
   const Level &F = c->lv[c->L];
@@ -1118,10 +1146,12 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   };
   // Snapshots of the plain cycle at work: for FCG iterate j of a seeded random
   // right-hand side, the cycle's input b_v = r_j; its exact correction
-  // x*_v = A^-1 b_v (solved to 1e-12); pairs of two kinds at random cells:
-  //  - before smoothing (x = 0): residual b_v, error x*_v;
-  //  - after pre-smoothing and the coarse-grid correction (the state the
-  //    post-smoother starts from): residual b_v - A x, error x*_v - x.
+  // x*_v = A^-1 b_v (solved to 1e-12); pairs at random cells taken after
+  // pre-smoothing and the coarse-grid correction (the state the post-smoother
+  // starts from): residual b_v - A x, error x*_v - x -- the high-frequency
+  // error a smoother has to remove.  (The full error x*_v of the cycle's input
+  // is dominated by smooth components no cell-local map can predict; pairs of
+  // that kind taught the network corrections far too large.)
   for (int sidx = 0; sidx < S; ++sidx) {
     for (int64_t i = 0; i < Nd; ++i) hb[i] = uniform_pm1(seed + 1 + sidx, (uint64_t)i);
     CK(cudaStreamSynchronize(c->stream));   // the previous right-hand side is no longer read
@@ -1140,8 +1170,6 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
       rho_sum += inf.rho;
       ++rho_cnt;
       const long snaps = (long)S * J, cnt = (sidx * J + j == snaps - 1) ? R - row : R / snaps;
-      const long c1 = cnt / 2;
-      add_pairs(bv, xv, c1);
       // the cycle up to the post-smoother, in FP64
       double *x = xx, *xt = xt2;
       chebyshev<double>(c, c->L, bv, x, xt, c->prm.cheb_degree, true);
@@ -1152,7 +1180,9 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
       apply_level<double>(c, c->L, x, r, 2, nullptr, nullptr, bv);
       CK(cudaMemcpyAsync(e, xv, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       CK(launch_axpy<double>(e, -1.0, x, Nd, c->stream));
-      add_pairs(r, e, cnt - c1);
+      add_pairs(r, e, cnt);
+      if (sidx == S - 1 && j == J - 1)   // kept for the damping below
+        CK(cudaMemcpyAsync(bv, r, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
   }
   c->smoother = save_smoother;
@@ -1209,31 +1239,22 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   N.trained = true;
   // graphs of a learned cycle captured earlier hold old weights only by pointer: nothing to redo
   {
-    // time one iteration's work with each cycle: V-cycle on fr plus one outer operator application
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    auto iter_ms = [&](int learned) {
-      c->use_learned = learned;
-      vcycle_body(c, c->fr, c->fz);
-      apply_level<double>(c, c->L, c->fz, c->fv, 0);
-      CK(cudaEventRecord(e0, c->stream));
-      for (int r = 0; r < 3; ++r) {
-        vcycle_body(c, c->fr, c->fz);
-        apply_level<double>(c, c->L, c->fz, c->fv, 0);
-      }
-      CK(cudaEventRecord(e1, c->stream));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      return ms / 3.0;
-    };
-    N.t_iter_cheb = iter_ms(0);
-    N.t_iter_learned = iter_ms(1);
-    c->use_learned = 0;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    // Damping of the learned step on the data it was trained for: on the last
+    // snapshot's residual after pre-smoothing and coarse-grid correction, r,
+    // take the step d = corr(r) from x = 0 and scale the output by the omega
+    // minimising ||r - omega A d||, so that the step does not increase such
+    // residuals.
+    learned_smooth<double>(c, bv, xx, 1, true);
+    apply_level<double>(c, c->L, xx, e, 0);
+    const double rad = dot(c, bv, e, Nd, 11), add = dot(c, e, e, Nd, 12), rr = dot(c, bv, bv, Nd, 13);
+    const double omega = (add > 0 && std::isfinite(rad / add)) ? rad / add : 0.0;
+    // ||r - omega A d|| / ||r|| with the optimal omega
+    N.step_reduction = rr > 0 ? std::sqrt(std::max(0.0, rr - omega * rad) / rr) : 1.0;
+    N.cscale = (float)(N.cscale * std::max(0.0, omega));
+    N.omega = omega;
   }
+  N.t_iter_cheb = iteration_ms(c, 0);
+  N.t_iter_learned = iteration_ms(c, 1);
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->npairs = (int)R;
@@ -1248,6 +1269,8 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     info->iter_ms_chebyshev = N.t_iter_cheb;
     info->iter_ms_learned = N.t_iter_learned;
+    info->damping = N.omega;
+    info->step_reduction = N.step_reduction;
   }
   return SIPG_OK;
 }
@@ -1603,7 +1626,7 @@ sipg_status sipg_smoother_train(sipg_ctx *c, int npairs, int epochs, uint64_t se
 }
 
 sipg_status sipg_set_smoother(sipg_ctx *c, int which, int steps_pre, int steps_post) {
-  if (!c || which < 0 || which > 1 || steps_pre < 1 || steps_post < 1 || steps_pre > 16 || steps_post > 16)
+  if (!c || which < 0 || which > 1 || steps_pre < 0 || steps_post < 1 || steps_pre > 16 || steps_post > 16)
     return SIPG_EINVAL;
   if (which == 1 && !c->net.trained) {
     c->err = "the learned smoother has not been trained (sipg_smoother_train)";
@@ -1618,8 +1641,14 @@ sipg_status sipg_set_smoother(sipg_ctx *c, int which, int steps_pre, int steps_p
       }
     c->vcalls_l[0] = c->vcalls_l[1] = 0;
   }
+  const bool changed = c->net.steps_pre != steps_pre || c->net.steps_post != steps_post;
   c->net.steps_pre = steps_pre;
   c->net.steps_post = steps_post;
+  if (which == 1 && changed)   // the fallback test compares time per iteration
+    return guarded(c, [&]() -> sipg_status {
+      c->net.t_iter_learned = iteration_ms(c, 1);
+      return SIPG_OK;
+    });
   return SIPG_OK;
 }
 

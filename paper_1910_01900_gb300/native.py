@@ -33,7 +33,8 @@ class TrainInfo(ctypes.Structure):
                 ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("out_scale", ctypes.c_double),
                 ("cheb_rate", ctypes.c_double), ("seconds", ctypes.c_double), ("target_max", ctypes.c_double),
                 ("nonfinite", ctypes.c_double), ("iter_ms_chebyshev", ctypes.c_double),
-                ("iter_ms_learned", ctypes.c_double)]
+                ("iter_ms_learned", ctypes.c_double), ("damping", ctypes.c_double),
+                ("step_reduction", ctypes.c_double)]
 
 
 class Mesh(ctypes.Structure):
@@ -333,7 +334,9 @@ class Context:
         self._check(lib().sipg_smoother_train(self.h, int(npairs), int(epochs), int(seed), ctypes.byref(info)))
         return info
 
-    def set_smoother(self, which, steps_pre=2, steps_post=2):
+    def set_smoother(self, which, steps_pre=0, steps_post=1):
+        """0 Chebyshev; 1 learned: steps_pre network pre-steps (0 = Chebyshev pre-smoothing) and
+        steps_post network post-steps."""
         self._check(lib().sipg_set_smoother(self.h, int(which), int(steps_pre), int(steps_post)))
 
     def mlp_shape(self):

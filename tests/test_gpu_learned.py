@@ -96,6 +96,9 @@ def test_training_and_learned_solve():
     ctx = _ctx(m, k)
     info = ctx.train_smoother(npairs=20000, epochs=8, seed=7)
     assert info.loss_last < info.loss_first
+    # what the network gains: one damped network step removes part of the residual the
+    # post-smoother faces (after pre-smoothing and coarse-grid correction)
+    assert 0 < info.damping and info.step_reduction < 0.95, (info.damping, info.step_reduction)
     b = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_RHS)).to(DEV)
     x0 = torch.zeros_like(b)
     ref = ctx.solve(b, x0, rtol=1e-10)
