@@ -107,6 +107,15 @@ typedef struct {
                               levels matrix-free.  Degree 2 (125 points) is
                               slower than matrix-free on GB300 and is kept
                               for comparison only                          */
+  int coarse_dense_max;    /* coarsest level solved by a dense inverse up to
+                              this many unknowns (default 2197 = 13^3 nodes:
+                              every mesh whose sizes halve down to <= 12
+                              cells); larger coarse levels (odd or prime
+                              mesh sizes) get coarse_iters Jacobi-PCG
+                              iterations instead, an inexact coarse solve
+                              like the paper's AMG-CG (Section 3.2), which
+                              the flexible CG absorbs                        */
+  int coarse_iters;        /* default 50                                       */
   void *stream;            /* cudaStream_t or NULL                             */
 } sipg_params;
 

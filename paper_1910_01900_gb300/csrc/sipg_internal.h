@@ -220,6 +220,15 @@ cudaError_t launch_fcg_update_xr(double *x, double *r, const double *p, const do
                                  const double *sc, double *partials, unsigned *counter, double *out,
                                  cudaStream_t s);
 cudaError_t launch_fcg_update_p(double *p, const double *z, const double *sc, int64_t n, cudaStream_t s);
+// coarse-level Jacobi-PCG with device-resident FP64 scalars (cycle precision T)
+template <typename T>
+cudaError_t launch_cg_dot(const T *x, const T *y, int64_t n, double *partials, unsigned *counter, double *out,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_update_xr(T *x, T *r, const T *p, const T *q, int64_t n, const double *gamma, const double *pq,
+                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_update_p(T *p, const T *z, int64_t n, const double *gnew, const double *gold, cudaStream_t s);
 template <typename Tb, typename Tx>
 cudaError_t launch_dense_gemv(const double *Ainv, const Tb *b, Tx *x, int n, cudaStream_t s, int nv = 1);
 

@@ -30,6 +30,10 @@ struct sipg_ctx {
   void *ebuf[2] = {nullptr, nullptr};
   double *Ainv = nullptr;
   int n0 = 0;
+  // coarsest level too large for the dense inverse: fixed Jacobi-PCG
+  // iterations on it (p, q work vectors in both precisions)
+  bool coarse_cg = false;
+  void *cg_p[2] = {nullptr, nullptr}, *cg_q[2] = {nullptr, nullptr};
   double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fv = nullptr, *fx = nullptr, *fb = nullptr;
   double *scal = nullptr, *partials = nullptr;
   unsigned *counter = nullptr;
@@ -333,9 +337,6 @@ void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_
 template <typename T>
 void learned_smooth(sipg_ctx *c, const T *b, T *x, int steps, bool zero_start);
 
-// Algorithm 2 with x^(l) = 0 on entry: rhs in lv[l].vb; returns the buffer
-// (vx or vt of that level) that holds x^(l).  No state changes between calls,
-// so the whole cycle can be captured once and replayed.
 // V-cycle vector k (0 vb, 1 vx, 2 vr, 3 vt) of level l in the current work set
 template <typename T>
 T *lvec(sipg_ctx *c, int l, int k) {
@@ -345,11 +346,59 @@ T *lvec(sipg_ctx *c, int l, int k) {
   return (T *)v[k][pidx<T>()];
 }
 
+// Inexact coarse solve on level 0 (FE_1 on the coarsest mesh) when it is too
+// large for the dense inverse: coarse_iters Jacobi-preconditioned CG
+// iterations from x = 0 (Algorithm 1 with D^-1 as the preconditioner; the
+// paper solves its coarse level inexactly with AMG-CG, Section 3.2).  Every
+// scalar stays in device memory (slots 16-18 of the context's scalar array)
+// and the iteration count is fixed, so the V-cycle stays capturable.  With
+// several vectors (multi-vector cycles) each is solved in turn.
+template <typename T>
+void coarse_cg_solve(sipg_ctx *c, const T *b_all, T *x_all) {
+  constexpr int pi = pidx<T>();
+  const Level &L0 = c->lv[0];
+  const int64_t n = L0.ndofs;
+  const int nv = c->nv;
+  const T *dinv = (const T *)L0.dinv[pi];
+  T *p = (T *)c->cg_p[pi], *q = (T *)c->cg_q[pi];
+  double *g[2] = {c->scal + 16, c->scal + 17}, *pq = c->scal + 18;
+  c->nv = 1;   // one vector at a time (level-0 operator on single vectors)
+  try {
+    for (int v = 0; v < nv; ++v) {
+      const T *b = b_all + v * n;
+      T *x = x_all + v * n;
+      T *r = lvec<T>(c, 0, 2);
+      T *z = lvec<T>(c, 0, 3);
+      CK(cudaMemsetAsync(x, 0, n * sizeof(T), c->stream));
+      CK(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+      CK(launch_xdb<T>(z, T(1), dinv, r, n, c->stream));
+      CK(launch_cg_dot<T>(r, z, n, c->partials, c->counter, g[0], c->stream));
+      CK(cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+      for (int k = 0; k < c->prm.coarse_iters; ++k) {
+        apply_level<T>(c, 0, p, q, 0);
+        CK(launch_cg_dot<T>(p, q, n, c->partials, c->counter, pq, c->stream));
+        CK(launch_cg_update_xr<T>(x, r, p, q, n, g[k & 1], pq, c->stream));
+        CK(launch_xdb<T>(z, T(1), dinv, r, n, c->stream));
+        CK(launch_cg_dot<T>(r, z, n, c->partials, c->counter, g[(k + 1) & 1], c->stream));
+        CK(launch_cg_update_p<T>(p, z, n, g[(k + 1) & 1], g[k & 1], c->stream));
+      }
+    }
+  } catch (...) {
+    c->nv = nv;
+    throw;
+  }
+  c->nv = nv;
+}
+
+// Algorithm 2 with x^(l) = 0 on entry: rhs in lv[l].vb; returns the buffer
+// (vx or vt of that level) that holds x^(l).  No state changes between calls,
+// so the whole cycle can be captured once and replayed.
 template <typename T>
 T *vcycle_rec(sipg_ctx *c, int l) {
   T *b = lvec<T>(c, l, 0);
   if (l == 0) {
-    CK((launch_dense_gemv<T, T>(c->Ainv, b, lvec<T>(c, l, 1), c->n0, c->stream, c->nv)));
+    if (c->coarse_cg) coarse_cg_solve<T>(c, b, lvec<T>(c, l, 1));
+    else CK((launch_dense_gemv<T, T>(c->Ainv, b, lvec<T>(c, l, 1), c->n0, c->stream, c->nv)));
     return lvec<T>(c, l, 1);
   }
   T *x = lvec<T>(c, l, 1), *xt = lvec<T>(c, l, 3);
@@ -781,9 +830,14 @@ void setup(sipg_ctx *c) {
   }
   c->ebuf[0] = dalloc<double>(c, ebuf_len);
   c->ebuf[1] = dalloc<float>(c, ebuf_len);
-  // assembled stencils of the low-degree FE levels that get smoothed
+  // a coarsest level above coarse_dense_max unknowns is solved by Jacobi-PCG
+  if (P.coarse_dense_max < 0 || P.coarse_iters < 1 || P.coarse_iters > 10000)
+    throw_inval("coarse_dense_max must be >= 0 and coarse_iters in 1..10000");
+  c->coarse_cg = c->lv[0].ndofs > P.coarse_dense_max;
+  const int lfirst = c->coarse_cg ? 0 : 1;   // levels that need an operator beyond the V-cycle's smoothing
+  // assembled stencils of the low-degree FE levels that get applied
   if (P.fe_assemble < 0 || P.fe_assemble > 2) throw_inval("fe_assemble must be 0, 1 or 2");
-  for (int l = 1; l < nl; ++l) {
+  for (int l = lfirst; l < nl; ++l) {
     Level &L = c->lv[l];
     if (L.kind != 1 || L.deg > P.fe_assemble) continue;
     const int w = 2 * L.deg + 1;
@@ -795,8 +849,8 @@ void setup(sipg_ctx *c) {
     L.stencil[0] = cd;
     L.stencil[1] = cf;
   }
-  // inverse diagonals
-  for (int l = 1; l < nl; ++l) {
+  // inverse diagonals (smoothed levels; the coarse level too for its Jacobi-PCG)
+  for (int l = lfirst; l < nl; ++l) {
     Level &L = c->lv[l];
     double *d = dalloc<double>(c, L.ndofs);
     if (L.kind == 0) {
@@ -819,8 +873,15 @@ void setup(sipg_ctx *c) {
   // smoothing range
   for (int l = 1; l < nl; ++l)
     c->lv[l].lambda = P.lambda_override > 0 ? P.lambda_override : estimate_lambda(c, l);
-  // coarse matrix and its inverse
-  {
+  // coarse matrix and its inverse, or the work vectors of the coarse Jacobi-PCG
+  if (c->coarse_cg) {
+    const int64_t n0 = c->lv[0].ndofs;
+    c->n0 = (int)n0;
+    c->cg_p[0] = dalloc<double>(c, n0);
+    c->cg_q[0] = dalloc<double>(c, n0);
+    c->cg_p[1] = dalloc<float>(c, n0);
+    c->cg_q[1] = dalloc<float>(c, n0);
+  } else {
     std::vector<double> A;
     int N;
     Mapping cmap(specs.back().md);
@@ -1314,6 +1375,8 @@ void sipg_default_params(sipg_params *p) {
   p->operator_only = 0;
   std::strcpy(p->coarsening, "cph");
   p->fe_assemble = 1;
+  p->coarse_dense_max = 2197;
+  p->coarse_iters = 50;
   p->stream = nullptr;
 }
 
@@ -1497,7 +1560,8 @@ sipg_status sipg_prolongate_add(sipg_ctx *c, int level, const void *xc, void *x)
 sipg_status sipg_coarse_solve(sipg_ctx *c, const double *b, double *x) {
   if (!c || !b || !x || !c->solver) return SIPG_EINVAL;
   return guarded(c, [&]() -> sipg_status {
-    CK((launch_dense_gemv<double, double>(c->Ainv, b, x, c->n0, c->stream)));
+    if (c->coarse_cg) coarse_cg_solve<double>(c, b, x);
+    else CK((launch_dense_gemv<double, double>(c->Ainv, b, x, c->n0, c->stream)));
     return SIPG_OK;
   });
 }

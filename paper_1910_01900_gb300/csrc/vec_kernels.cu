@@ -172,6 +172,70 @@ cudaError_t launch_fcg_update_p(double *p, const double *z, const double *sc, in
   return cudaGetLastError();
 }
 
+// ------------------------------------------ coarse-level Jacobi-PCG
+// Kernels of a fixed number of preconditioned CG iterations on vectors of the
+// cycle's precision with FP64 scalars that stay in device memory (so the
+// iteration can be captured in the V-cycle's graph): deterministic dot
+// products, and updates that read their step lengths from the scalar slots.
+template <typename T>
+__global__ void cg_dot_kernel(const T *x, const T *y, long n, double *partials, unsigned *counter, double *out) {
+  double a = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    a = fma((double)x[i], (double)y[i], a);
+  reduce2_finish(a, 0.0, partials, counter, out);
+}
+template <typename T>
+cudaError_t launch_cg_dot(const T *x, const T *y, int64_t n, double *partials, unsigned *counter, double *out,
+                          cudaStream_t s) {
+  cg_dot_kernel<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partials, counter, out);
+  note_launch();
+  return cudaGetLastError();
+}
+// x += alpha p, r -= alpha q with alpha = gamma / pq (0 when pq is not positive)
+template <typename T>
+__global__ void cg_update_xr_kernel(T *x, T *r, const T *p, const T *q, long n, const double *gamma,
+                                    const double *pq) {
+  const double alpha = pq[0] > 0 ? gamma[0] / pq[0] : 0.0;
+  const T a = (T)alpha;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    x[i] = fma(a, p[i], x[i]);
+    r[i] = fma(-a, q[i], r[i]);
+  }
+}
+template <typename T>
+cudaError_t launch_cg_update_xr(T *x, T *r, const T *p, const T *q, int64_t n, const double *gamma, const double *pq,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cg_update_xr_kernel<T><<<grid_for(n), 256, 0, s>>>(x, r, p, q, n, gamma, pq);
+  note_launch();
+  return cudaGetLastError();
+}
+// p = z + beta p with beta = gamma_new / gamma_old (0 when gamma_old is not positive)
+template <typename T>
+__global__ void cg_update_p_kernel(T *p, const T *z, long n, const double *gnew, const double *gold) {
+  const double beta = gold[0] > 0 ? gnew[0] / gold[0] : 0.0;
+  const T b = (T)beta;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    p[i] = fma(b, p[i], z[i]);
+}
+template <typename T>
+cudaError_t launch_cg_update_p(T *p, const T *z, int64_t n, const double *gnew, const double *gold, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cg_update_p_kernel<T><<<grid_for(n), 256, 0, s>>>(p, z, n, gnew, gold);
+  note_launch();
+  return cudaGetLastError();
+}
+#define SIPG_CG_INST(T)                                                                                      \
+  template cudaError_t launch_cg_dot<T>(const T *, const T *, int64_t, double *, unsigned *, double *,       \
+                                        cudaStream_t);                                                       \
+  template cudaError_t launch_cg_update_xr<T>(T *, T *, const T *, const T *, int64_t, const double *,       \
+                                              const double *, cudaStream_t);                                 \
+  template cudaError_t launch_cg_update_p<T>(T *, const T *, int64_t, const double *, const double *,        \
+                                             cudaStream_t);
+SIPG_CG_INST(double)
+SIPG_CG_INST(float)
+#undef SIPG_CG_INST
+
 // Coarse solve x = A0^-1 b with the explicit inverse (one warp per row, FP64).
 template <typename Tb, typename Tx>
 __global__ void dense_gemv_kernel(const double *__restrict__ Ainv, const Tb *__restrict__ b, Tx *__restrict__ x,

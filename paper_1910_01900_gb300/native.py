@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
                 ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int), ("lambda_override", ctypes.c_double),
                 ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("coarsening", ctypes.c_char * 8),
                 ("autotune", ctypes.c_int), ("fe_assemble", ctypes.c_int),
+                ("coarse_dense_max", ctypes.c_int), ("coarse_iters", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -155,7 +156,8 @@ def make_mesh(m, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(
 
 
 def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
-                operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None):
+                operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None,
+                coarse_dense_max=None, coarse_iters=None):
     prm = Params()
     lib().sipg_default_params(ctypes.byref(prm))
     prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
@@ -166,6 +168,10 @@ def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iter
     prm.coarsening = coarsening.encode()
     if fe_assemble is not None:
         prm.fe_assemble = int(fe_assemble)
+    if coarse_dense_max is not None:
+        prm.coarse_dense_max = int(coarse_dense_max)
+    if coarse_iters is not None:
+        prm.coarse_iters = int(coarse_iters)
     prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return prm
 
@@ -176,7 +182,7 @@ class Context:
     def __init__(self, m, degree, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
                  precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
                  operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None,
-                 _handle=None):
+                 coarse_dense_max=None, coarse_iters=None, _handle=None):
         L = lib()
         mesh, mm = make_mesh(m, deform, amp, lo, hi, bc)
         self.degree, self.precision = int(degree), int(precision)
@@ -187,7 +193,8 @@ class Context:
             self.h = _handle
             return
         prm = make_params(degree, precision, penalty_factor, cheb_degree, eig_iters, lambda_override,
-                          operator_only, stream, autotune, p_coarsen, coarsening, fe_assemble)
+                          operator_only, stream, autotune, p_coarsen, coarsening, fe_assemble,
+                          coarse_dense_max, coarse_iters)
         h = ctypes.c_void_p()
         st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
         if st != OK:

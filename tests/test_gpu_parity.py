@@ -450,3 +450,57 @@ def test_coarsening_without_c_is_rejected():
     from paper_1910_01900_gb300 import SipgError
     with pytest.raises(SipgError):
         _ctx(4, 2, coarsening="ph")
+
+
+def test_iterative_coarse_solve_small_mesh():
+    """A coarsest level above coarse_dense_max gets fixed Jacobi-PCG iterations instead of the
+    dense inverse: forced here on a small mesh, where 50 iterations nearly solve it exactly."""
+    m, k = 4, 3
+    ctx = _ctx(m, k, coarse_dense_max=0, coarse_iters=50)
+    mg = CPHMultigrid(Mesh(m), k)
+    n0 = ctx.num_dofs(0)
+    b0 = sipg_inputs.uniform(n0, 61)
+    b0[mg.levels[0].space.constrained] = 0.0
+    x = torch.empty(n0, dtype=torch.float64, device=DEV)
+    ctx.coarse_solve(gpu(b0), x)
+    torch.cuda.synchronize()
+    assert rel(x.cpu().numpy(), mg.coarse.solve(b0)) <= 1e-4
+    b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
+    ctx.rhs(b)
+    xd = torch.zeros_like(b)
+    dense = _ctx(m, k).solve(b, xd, rtol=1e-10)
+    for prec in (0, 1):
+        c = _ctx(m, k, precision=prec, coarse_dense_max=0, coarse_iters=50)
+        xc = torch.zeros_like(b)
+        info = c.solve(b, xc, rtol=1e-10)
+        assert info.converged and info.iterations <= dense.iterations + 2, (prec, info.iterations)
+        assert rel(xc.cpu().numpy(), xd.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_odd_mesh_with_large_coarse_level(precision):
+    """m = 17 cannot be halved: the coarsest FE_1 level has 18^3 = 5832 unknowns, above the
+    dense limit, and is solved by Jacobi-PCG; the solve (on a stream, so the V-cycle with the
+    coarse iteration is captured as a CUDA graph) still reaches 1e-10 and so does a block of
+    right-hand sides."""
+    s = torch.cuda.Stream()
+    m, k = 17, 2
+    with torch.cuda.stream(s):
+        ctx = _ctx(m, k, deform=1, precision=precision, stream=s)
+        assert ctx.num_dofs(0) == 18 ** 3
+        b = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_RHS)).to(DEV)
+        x = torch.zeros_like(b)
+        for _ in range(2):   # the second solve replays the captured cycle
+            x.zero_()
+            info = ctx.solve(b, x, rtol=1e-10, maxit=40)
+            assert info.converged and info.iterations <= 20, info.iterations
+        r = torch.empty_like(b)
+        ctx.apply(x, r)
+        s.synchronize()
+        assert (torch.linalg.norm(b - r) / torch.linalg.norm(b)).item() <= 2e-10
+        B = torch.stack([b, -0.5 * b, torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), 3)).to(DEV)])
+        X = torch.zeros_like(B)
+        infos = ctx.solve_multi(B, X, rtol=1e-10, maxit=40)
+        s.synchronize()
+        assert all(i.converged for i in infos)
+        assert rel(X[1].cpu().numpy(), -0.5 * x.cpu().numpy()) <= 1e-6
