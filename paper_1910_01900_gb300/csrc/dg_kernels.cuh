@@ -353,22 +353,25 @@ __device__ __forceinline__ VecPtrs<T> vec_ptrs(const DGArgs<T> &a, const int r) 
 }
 
 // One thread block handles cb consecutive cells of one vector with cb N^2
-// threads; block b is cell group b / nv of vector b % nv, so the vectors of
-// one group run side by side and share its geometry in L2.  cb is a launch
+// threads.  MULTI (several vectors of one operator): block b is cell group
+// b / nv of vector b % nv, so the vectors of one group run side by side and
+// share its geometry in L2.  The single-vector kernels are compiled apart:
+// the per-vector offsets cost registers, which cost resident blocks (the FP32
+// integration pass at 16 MDoF ran 14% slower with them).  cb is a launch
 // parameter (picked per level and size by the tile-shape autotuner): one
 // compiled kernel serves every block width up to kCellThreads threads.
-template <typename T, int N, bool CURVED>
+template <typename T, int N, bool CURVED, bool MULTI>
 __global__ void __launch_bounds__(kCellThreads) dg_eval_kernel(const DGArgs<T> a, const int cb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int grp = blockIdx.x / a.nv, vec = blockIdx.x - grp * a.nv;
+  const int grp = MULTI ? blockIdx.x / a.nv : blockIdx.x, vec = MULTI ? blockIdx.x - grp * a.nv : 0;
   const int cell0 = grp * cb;
   dg_eval_body<T, N, CURVED>(a, vec_ptrs(a, vec), cell0, min(cb, a.ncells - cell0), reinterpret_cast<T *>(smem_raw));
 }
 
-template <typename T, int N, bool CURVED>
+template <typename T, int N, bool CURVED, bool MULTI>
 __global__ void __launch_bounds__(kCellThreads) dg_integrate_kernel(const DGArgs<T> a, const int cb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int grp = blockIdx.x / a.nv, vec = blockIdx.x - grp * a.nv;
+  const int grp = MULTI ? blockIdx.x / a.nv : blockIdx.x, vec = MULTI ? blockIdx.x - grp * a.nv : 0;
   const int cell0 = grp * cb;
   dg_integrate_body<T, N, CURVED>(a, vec_ptrs(a, vec), cell0, min(cb, a.ncells - cell0),
                                   reinterpret_cast<T *>(smem_raw));

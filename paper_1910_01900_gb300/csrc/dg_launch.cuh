@@ -13,10 +13,17 @@ static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s, in
   const int64_t grid = (int64_t)((a.ncells + cb - 1) / cb) * a.nv;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  if (integrate)
-    dg_integrate_kernel<T, N, CURVED><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
-  else
-    dg_eval_kernel<T, N, CURVED><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+  if (a.nv > 1) {
+    if (integrate)
+      dg_integrate_kernel<T, N, CURVED, true><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+    else
+      dg_eval_kernel<T, N, CURVED, true><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+  } else {
+    if (integrate)
+      dg_integrate_kernel<T, N, CURVED, false><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+    else
+      dg_eval_kernel<T, N, CURVED, false><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -25,9 +32,9 @@ static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s, in
 template <typename T, int N, bool CURVED>
 static cudaError_t occ_dg(bool integrate, int cb, int *blocks) {
   const size_t smem = (size_t)cb * 4 * Tile<N>::T3 * sizeof(T);
-  return integrate ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_integrate_kernel<T, N, CURVED>,
+  return integrate ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_integrate_kernel<T, N, CURVED, false>,
                                                                    cb * N * N, smem)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_eval_kernel<T, N, CURVED>,
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_eval_kernel<T, N, CURVED, false>,
                                                                    cb * N * N, smem);
 }
 
@@ -38,10 +45,14 @@ static cudaError_t prep_dg_n() {
   const int smem = max_cb(N, sizeof(T)) * 4 * Tile<N>::T3 * (int)sizeof(T);
   cudaError_t e = cudaSuccess;
   for (cudaError_t r :
-       {cudaFuncSetAttribute(dg_integrate_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-        cudaFuncSetAttribute(dg_integrate_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-        cudaFuncSetAttribute(dg_eval_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-        cudaFuncSetAttribute(dg_eval_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)})
+       {cudaFuncSetAttribute(dg_integrate_kernel<T, N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_integrate_kernel<T, N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_eval_kernel<T, N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_eval_kernel<T, N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_integrate_kernel<T, N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_integrate_kernel<T, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_eval_kernel<T, N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_eval_kernel<T, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)})
     if (r != cudaSuccess) e = r;
   return e;
 }

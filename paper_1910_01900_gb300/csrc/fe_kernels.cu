@@ -29,8 +29,10 @@ __device__ __forceinline__ bool node_constrained(const int g[3], const int grid[
          (g[2] == 0 && bc[4] == 0) || (g[2] == grid[2] - 1 && bc[5] == 0);
 }
 
-// cb cells per thread block (a launch parameter, cb N^2 threads)
-template <typename T, int N, bool CURVED>
+// cb cells per thread block (a launch parameter, cb N^2 threads); MULTI:
+// several vectors, block b = cell group b / nv of vector b % nv (compiled
+// apart from the single-vector kernel, whose offsets would cost registers)
+template <typename T, int N, bool CURVED, bool MULTI>
 __global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a, const int cb) {
   constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -38,10 +40,10 @@ __global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   // block -> (cell group, vector); the vectors of one group are neighbours
-  const int grp = blockIdx.x / a.nv, vec = blockIdx.x - grp * a.nv;
+  const int grp = MULTI ? blockIdx.x / a.nv : blockIdx.x, vec = MULTI ? blockIdx.x - grp * a.nv : 0;
   const int cell0 = grp * cb;
   const int ncta = min(cb, a.ncells - cell0);
-  const T *__restrict__ ug = a.u + vec * a.vs;
+  const T *__restrict__ ug = MULTI ? a.u + vec * a.vs : a.u;
   const bool act = cl < ncta;
   T *su = sm + cl * 4 * TT;
   for (int i = tid; i < ncta * N3; i += NT) {
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a
     load_line<T, N>(su, base, stride, x);
   }
   apply_mat<T, N, MSt>(x, y);
-  T *eb = a.ebuf + vec * a.es + (size_t)(cell0 + cl) * N3 + l;
+  T *eb = (MULTI ? a.ebuf + vec * a.es : a.ebuf) + (size_t)(cell0 + cl) * N3 + l;
 #pragma unroll
   for (int q = 0; q < N; ++q) eb[q * N2] = y[q];
 }
@@ -643,23 +645,31 @@ static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s, int cb) {
   const int64_t grid = (int64_t)((a.ncells + cb - 1) / cb) * a.nv;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  fe_cell_kernel<T, N, CURVED><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+  if (a.nv > 1)
+    fe_cell_kernel<T, N, CURVED, true><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+  else
+    fe_cell_kernel<T, N, CURVED, false><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T, int N, bool CURVED>
 static cudaError_t occ_fe_cells(int cb, int *blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fe_cell_kernel<T, N, CURVED>, cb * N * N,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fe_cell_kernel<T, N, CURVED, false>, cb * N * N,
                                                        (size_t)cb * 4 * Tile<N>::T3 * sizeof(T));
 }
 
 template <typename T, int N>
 static cudaError_t prep_fe_n() {
   const int smem = max_cb(N, sizeof(T)) * 4 * Tile<N>::T3 * (int)sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(fe_cell_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fe_cell_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t r :
+       {cudaFuncSetAttribute(fe_cell_kernel<T, N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(fe_cell_kernel<T, N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(fe_cell_kernel<T, N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(fe_cell_kernel<T, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)})
+    if (r != cudaSuccess) e = r;
+  return e;
 }
 
 cudaError_t prepare_fe_kernels() {
