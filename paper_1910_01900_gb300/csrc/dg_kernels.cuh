@@ -360,8 +360,15 @@ __device__ __forceinline__ VecPtrs<T> vec_ptrs(const DGArgs<T> &a, const int r) 
 // integration pass at 16 MDoF ran 14% slower with them).  cb is a launch
 // parameter (picked per level and size by the tile-shape autotuner): one
 // compiled kernel serves every block width up to kCellThreads threads.
+// kMinCellBlocks caps FP32 variants at 40 registers (two blocks of
+// kCellThreads per SM): left free, the compiler gave some of them 48-60
+// (FP32 curved integration at k = 2: 50 registers, 16% slower at 16 MDoF).
+// FP64 variants (56-64 registers, bound by the FP64 pipe) are left free.
+template <typename T>
+constexpr int kMinCellBlocks = sizeof(T) == 4 ? 2 : 1;
+
 template <typename T, int N, bool CURVED, bool MULTI>
-__global__ void __launch_bounds__(kCellThreads) dg_eval_kernel(const DGArgs<T> a, const int cb) {
+__global__ void __launch_bounds__(kCellThreads, kMinCellBlocks<T>) dg_eval_kernel(const DGArgs<T> a, const int cb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int grp = MULTI ? blockIdx.x / a.nv : blockIdx.x, vec = MULTI ? blockIdx.x - grp * a.nv : 0;
   const int cell0 = grp * cb;
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(kCellThreads) dg_eval_kernel(const DGArgs<T> a
 }
 
 template <typename T, int N, bool CURVED, bool MULTI>
-__global__ void __launch_bounds__(kCellThreads) dg_integrate_kernel(const DGArgs<T> a, const int cb) {
+__global__ void __launch_bounds__(kCellThreads, kMinCellBlocks<T>) dg_integrate_kernel(const DGArgs<T> a, const int cb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int grp = MULTI ? blockIdx.x / a.nv : blockIdx.x, vec = MULTI ? blockIdx.x - grp * a.nv : 0;
   const int cell0 = grp * cb;
