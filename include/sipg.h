@@ -111,7 +111,7 @@ typedef struct {
                               this many unknowns (default 2197 = 13^3 nodes:
                               every mesh whose sizes halve down to <= 12
                               cells); larger coarse levels (odd or prime
-                              mesh sizes) get coarse_iters Jacobi-PCG
+                              mesh sizes) get coarse_iters FP64 Jacobi-PCG
                               iterations instead, an inexact coarse solve
                               like the paper's AMG-CG (Section 3.2), which
                               the flexible CG absorbs                        */

@@ -33,7 +33,7 @@ struct sipg_ctx {
   // coarsest level too large for the dense inverse: fixed Jacobi-PCG
   // iterations on it (p, q work vectors in both precisions)
   bool coarse_cg = false;
-  void *cg_p[2] = {nullptr, nullptr}, *cg_q[2] = {nullptr, nullptr};
+  double *cg_p = nullptr, *cg_q = nullptr;   // FP64 search and product vectors of the coarse CG
   double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fv = nullptr, *fx = nullptr, *fb = nullptr;
   double *scal = nullptr, *partials = nullptr;
   unsigned *counter = nullptr;
@@ -351,36 +351,47 @@ T *lvec(sipg_ctx *c, int l, int k) {
 // iterations from x = 0 (Algorithm 1 with D^-1 as the preconditioner; the
 // paper solves its coarse level inexactly with AMG-CG, Section 3.2).  Every
 // scalar stays in device memory (slots 16-18 of the context's scalar array)
-// and the iteration count is fixed, so the V-cycle stays capturable.  With
-// several vectors (multi-vector cycles) each is solved in turn.
-template <typename T>
-void coarse_cg_solve(sipg_ctx *c, const T *b_all, T *x_all) {
-  constexpr int pi = pidx<T>();
+// and the iteration count is fixed, so the V-cycle stays capturable.  The
+// iteration runs in FP64 whatever the cycle's precision (like the dense
+// inverse): an FP32 cycle casts its right-hand side into level 0's FP64
+// vectors, which only the FP64 cycle uses otherwise, and casts the result
+// back.  With several vectors (multi-vector cycles) each is solved in turn.
+void coarse_cg_fp64(sipg_ctx *c, const double *b, double *x) {
   const Level &L0 = c->lv[0];
   const int64_t n = L0.ndofs;
-  const int nv = c->nv;
-  const T *dinv = (const T *)L0.dinv[pi];
-  T *p = (T *)c->cg_p[pi], *q = (T *)c->cg_q[pi];
+  const double *dinv = (const double *)L0.dinv[0];
+  double *p = c->cg_p, *q = c->cg_q;
   double *g[2] = {c->scal + 16, c->scal + 17}, *pq = c->scal + 18;
+  double *r = lvec<double>(c, 0, 2), *z = lvec<double>(c, 0, 3);
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), c->stream));
+  CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CK(launch_xdb<double>(z, 1.0, dinv, r, n, c->stream));
+  CK(launch_cg_dot<double>(r, z, n, c->partials, c->counter, g[0], c->stream));
+  CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  for (int k = 0; k < c->prm.coarse_iters; ++k) {
+    apply_level<double>(c, 0, p, q, 0);
+    CK(launch_cg_dot<double>(p, q, n, c->partials, c->counter, pq, c->stream));
+    CK(launch_cg_update_xr<double>(x, r, p, q, n, g[k & 1], pq, c->stream));
+    CK(launch_xdb<double>(z, 1.0, dinv, r, n, c->stream));
+    CK(launch_cg_dot<double>(r, z, n, c->partials, c->counter, g[(k + 1) & 1], c->stream));
+    CK(launch_cg_update_p<double>(p, z, n, g[(k + 1) & 1], g[k & 1], c->stream));
+  }
+}
+
+template <typename T>
+void coarse_cg_solve(sipg_ctx *c, const T *b_all, T *x_all) {
+  const int64_t n = c->lv[0].ndofs;
+  const int nv = c->nv;
   c->nv = 1;   // one vector at a time (level-0 operator on single vectors)
   try {
     for (int v = 0; v < nv; ++v) {
-      const T *b = b_all + v * n;
-      T *x = x_all + v * n;
-      T *r = lvec<T>(c, 0, 2);
-      T *z = lvec<T>(c, 0, 3);
-      CK(cudaMemsetAsync(x, 0, n * sizeof(T), c->stream));
-      CK(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-      CK(launch_xdb<T>(z, T(1), dinv, r, n, c->stream));
-      CK(launch_cg_dot<T>(r, z, n, c->partials, c->counter, g[0], c->stream));
-      CK(cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-      for (int k = 0; k < c->prm.coarse_iters; ++k) {
-        apply_level<T>(c, 0, p, q, 0);
-        CK(launch_cg_dot<T>(p, q, n, c->partials, c->counter, pq, c->stream));
-        CK(launch_cg_update_xr<T>(x, r, p, q, n, g[k & 1], pq, c->stream));
-        CK(launch_xdb<T>(z, T(1), dinv, r, n, c->stream));
-        CK(launch_cg_dot<T>(r, z, n, c->partials, c->counter, g[(k + 1) & 1], c->stream));
-        CK(launch_cg_update_p<T>(p, z, n, g[(k + 1) & 1], g[k & 1], c->stream));
+      if constexpr (std::is_same<T, double>::value) {
+        coarse_cg_fp64(c, b_all + v * n, x_all + v * n);
+      } else {
+        double *bd = lvec<double>(c, 0, 0), *xd = lvec<double>(c, 0, 1);
+        CK((launch_cast<double, T>(bd, b_all + v * n, n, c->stream)));
+        coarse_cg_fp64(c, bd, xd);
+        CK((launch_cast<T, double>(x_all + v * n, xd, n, c->stream)));
       }
     }
   } catch (...) {
@@ -877,10 +888,8 @@ void setup(sipg_ctx *c) {
   if (c->coarse_cg) {
     const int64_t n0 = c->lv[0].ndofs;
     c->n0 = (int)n0;
-    c->cg_p[0] = dalloc<double>(c, n0);
-    c->cg_q[0] = dalloc<double>(c, n0);
-    c->cg_p[1] = dalloc<float>(c, n0);
-    c->cg_q[1] = dalloc<float>(c, n0);
+    c->cg_p = dalloc<double>(c, n0);
+    c->cg_q = dalloc<double>(c, n0);
   } else {
     std::vector<double> A;
     int N;

@@ -233,7 +233,6 @@ cudaError_t launch_cg_update_p(T *p, const T *z, int64_t n, const double *gnew, 
   template cudaError_t launch_cg_update_p<T>(T *, const T *, int64_t, const double *, const double *,        \
                                              cudaStream_t);
 SIPG_CG_INST(double)
-SIPG_CG_INST(float)
 #undef SIPG_CG_INST
 
 // Coarse solve x = A0^-1 b with the explicit inverse (one warp per row, FP64).
