@@ -305,10 +305,11 @@ sipg_status sipg_smoother_train(sipg_ctx *ctx, int npairs, int epochs, uint64_t 
 /* which = 0: Chebyshev (default); 1: learned (trained network required), with
  * steps_pre and steps_post network steps around the coarse correction;
  * steps_pre = 0 keeps Chebyshev pre-smoothing (the network is trained on the
- * post-smoothing state), 1..16 network steps; steps_post 1..16.  Selecting the
- * learned smoother with new step counts times one solver iteration of that
- * cycle (a few V-cycles on the context's stream, synchronised) for the
- * fallback test. */
+ * post-smoothing state), 1..16 network steps; steps_post 0..16, where 0
+ * leaves the finest level without post-smoothing (the cycle without the
+ * network, to measure what its steps add).  Selecting the learned smoother
+ * with new step counts times one solver iteration of that cycle (a few
+ * V-cycles on the context's stream, synchronised) for the fallback test. */
 sipg_status sipg_set_smoother(sipg_ctx *ctx, int which, int steps_pre, int steps_post);
 /* Network shape: in_dim (and padded width), hidden width, out_dim (and
  * padded width), number of parameters.  Flat parameter layout (FP32):

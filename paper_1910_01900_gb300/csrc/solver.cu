@@ -1699,7 +1699,7 @@ sipg_status sipg_smoother_train(sipg_ctx *c, int npairs, int epochs, uint64_t se
 }
 
 sipg_status sipg_set_smoother(sipg_ctx *c, int which, int steps_pre, int steps_post) {
-  if (!c || which < 0 || which > 1 || steps_pre < 0 || steps_post < 1 || steps_pre > 16 || steps_post > 16)
+  if (!c || which < 0 || which > 1 || steps_pre < 0 || steps_post < 0 || steps_pre > 16 || steps_post > 16)
     return SIPG_EINVAL;
   if (which == 1 && !c->net.trained) {
     c->err = "the learned smoother has not been trained (sipg_smoother_train)";

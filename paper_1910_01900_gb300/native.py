@@ -343,7 +343,7 @@ class Context:
 
     def set_smoother(self, which, steps_pre=0, steps_post=1):
         """0 Chebyshev; 1 learned: steps_pre network pre-steps (0 = Chebyshev pre-smoothing) and
-        steps_post network post-steps."""
+        steps_post network post-steps (0 = no post-smoothing: the cycle without the network)."""
         self._check(lib().sipg_set_smoother(self.h, int(which), int(steps_pre), int(steps_post)))
 
     def mlp_shape(self):

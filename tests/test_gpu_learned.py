@@ -114,5 +114,27 @@ def test_training_and_learned_solve():
     got2 = ctx.solve(b, x2, rtol=1e-10, maxit=200)
     assert got2.converged and got2.learned == 1
     assert (torch.linalg.norm(x2 - x0) / torch.linalg.norm(x0)).item() <= 1e-8
+    # what the network adds to the V-cycle: the energy norm of the error left by one cycle with
+    # Chebyshev pre-smoothing and no post-smoothing (the cycle without the network), and by the
+    # same cycle with one network post-step
+    r = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), 71)).to(DEV)
+    xs = torch.zeros_like(r)
+    ctx.set_smoother(0)
+    assert ctx.solve(r, xs, rtol=1e-12).converged
+
+    def energy(e):
+        ae = torch.empty_like(e)
+        ctx.apply(e, ae)
+        return torch.dot(e, ae).item() ** 0.5
+
+    def left_by_cycle():
+        z = torch.empty_like(r)
+        ctx.vcycle(r, z)
+        return energy(xs - z) / energy(xs)
+    ctx.set_smoother(1, 0, 0)
+    without = left_by_cycle()
+    ctx.set_smoother(1, 0, 1)
+    with_net = left_by_cycle()
+    assert with_net < without, (with_net, without)
     ctx.set_smoother(0)
     assert ref.converged
