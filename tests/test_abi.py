@@ -59,3 +59,54 @@ def test_product_package_has_no_cpu_fallback():
             if f.endswith(".py"):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.replace("no CPU", ""), f
+
+
+def test_null_handles_and_bad_arguments_are_rejected_before_device_work(lib):
+    """Every entry point answers SIPG_EINVAL to a null context, batch, mesh or output pointer
+    (the error behaviour include/sipg.h states), without touching the device."""
+    from paper_1910_01900_gb300 import native
+    N = None
+    calls = {
+        "sipg_create": (N, N, N),
+        "sipg_destroy": (N,),
+        "sipg_num_levels": (N, N),
+        "sipg_num_dofs": (N, 0, N),
+        "sipg_level_info": (N, 0, N, N, N),
+        "sipg_lambda": (N, 1, N),
+        "sipg_rhs": (N, 0, N),
+        "sipg_l2_error": (N, 0, N, N),
+        "sipg_operator_apply": (N, 0, N, N),
+        "sipg_operator_apply_multi": (N, 0, 2, N, N),
+        "sipg_level_apply": (N, 0, 0, N, N),
+        "sipg_inverse_diagonal": (N, 1, 0, N),
+        "sipg_smooth": (N, 1, N, N, 1),
+        "sipg_restrict": (N, 1, N, N),
+        "sipg_prolongate_add": (N, 1, N, N),
+        "sipg_coarse_solve": (N, N, N),
+        "sipg_vcycle": (N, N, N),
+        "sipg_solve": (N, N, N, 1e-10, 10, 0, N),
+        "sipg_solve_host": (N, N, N, 1e-10, 10, N),
+        "sipg_solve_multi": (N, 2, N, N, 1e-10, 10, N),
+        "sipg_time_apply": (N, 0, N, N, 1, N, N),
+        "sipg_tile_shape": (N, 0, 0, 0, N),
+        "sipg_set_tile_shape": (N, 0, 0, 0, 1),
+        "sipg_smoother_train": (N, 100, 1, 0, N),
+        "sipg_set_smoother": (N, 0, 0, 1),
+        "sipg_mlp_shape": (N, N, N, N, N, N, N),
+        "sipg_mlp_params": (N, 0, N),
+        "sipg_mlp_forward": (N, N, 1, N),
+        "sipg_mlp_gradients": (N, N, N, 1, N, N),
+        "sipg_mlp_features": (N, N, N, N),
+        "sipg_launch_count": (N,),
+        "sipg_fma_peak": (2, N, N),
+        "sipg_batch_create": (0, N, N, N),
+        "sipg_batch_destroy": (N,),
+        "sipg_batch_context": (N, 0, N),
+        "sipg_batch_apply": (N, N, N),
+        "sipg_batch_solve": (N, N, N, 1e-10, 10, N),
+        "sipg_operator_apply_noalloc": (N, 3, 1.0, N, N, N),
+    }
+    skip = {"sipg_default_params", "sipg_last_error", "sipg_batch_last_error"}
+    assert sorted(calls) == sorted(set(_declared()) - skip)
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == native.EINVAL, name
