@@ -331,11 +331,13 @@ sipg_status sipg_mlp_features(sipg_ctx *ctx, const double *r_dev, float *feat_de
 
 /* Cells per thread block a cell kernel of a level uses in the given
  * precision (pass 0 DG evaluation, 1 DG integration on a DG level; 2 the FE
- * cell pass on an FE level): the autotuned or set value, else the default.
- * EINVAL for a pass that does not exist on the level. */
+ * cell pass on an FE level): the autotuned or set value, else the default
+ * (about 256 threads per block, fewer cells per block on meshes that would
+ * otherwise give fewer blocks than the GPU has SMs).  EINVAL for a pass that
+ * does not exist on the level. */
 sipg_status sipg_tile_shape(const sipg_ctx *ctx, int level, int precision, int pass, int *cells_per_block);
 
-/* Sets that width (0 = the compiled default; at most 768 threads and 227 KB
+/* Sets that width (0 = the default above; at most 768 threads and 227 KB
  * of shared memory per block, else EINVAL).  The results do not depend on
  * it: every cell is computed by the same threads in the same order.  Drops
  * the context's captured V-cycle graphs (they hold the old launch shapes). */

@@ -116,8 +116,11 @@ struct Level {
   void *dinv[2] = {nullptr, nullptr};
   double lambda = 0;
   // cells per thread block of the cell kernels, [precision][DG evaluation,
-  // DG integration, FE cells]; 0 = compiled default (set by the autotuner)
+  // DG integration, FE cells]: cb0 is the setup default (the compiled
+  // default, lowered on meshes with fewer blocks than SMs), cb the width in
+  // use (cb0, the autotuner's choice or a set value; 0 = compiled default)
   int cb[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int cb0[2][3] = {{0, 0, 0}, {0, 0, 0}};
   // FE levels of low degree: assembled stencil [(2p+1)^3][nodes] in both
   // precisions (nullptr: matrix-free)
   void *stencil[2] = {nullptr, nullptr};

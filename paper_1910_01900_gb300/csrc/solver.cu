@@ -820,6 +820,23 @@ void setup(sipg_ctx *c) {
   c->dg_grad[1] = dalloc<float>(c, dg_grad_len);
   c->dg_trace[1] = dalloc<float>(c, dg_trace_len);
   CK(cudaDeviceSynchronize());   // geometry uploads (legacy stream) complete before stream work
+  {
+    // Default tile widths: the compiled default, lowered on meshes that would
+    // give fewer blocks than SMs, so that every SM gets cells (GB300 runs two
+    // FP64 FMAs per clock per SM: an FP64 pass over 64 cells in 4 blocks of
+    // 16 would use 4 of the 152 SMs).
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (Level &L : c->lv)
+      for (int pi = 0; pi < 2; ++pi)
+        for (int pass = 0; pass < 3; ++pass) {
+          int cb = dg_cells_per_block<double>(L.n);
+          if (nsm > 0 && (L.ncells + cb - 1) / cb < nsm)
+            cb = (int)std::max<int64_t>(1, (L.ncells + nsm - 1) / nsm);
+          L.cb[pi][pass] = L.cb0[pi][pass] = cb;
+        }
+  }
   if (P.autotune) {
     // the finest DG level always; the other cell-kernel levels of the solver
     for (int l = c->solver ? 1 : c->L; l <= c->L; ++l) {
@@ -1663,7 +1680,7 @@ sipg_status sipg_set_tile_shape(sipg_ctx *c, int level, int precision, int pass,
   const int mx = pass < 2 ? (precision == 0 ? dg_max_cells_per_block<double>(n) : dg_max_cells_per_block<float>(n))
                           : (precision == 0 ? fe_max_cells_per_block<double>(n) : fe_max_cells_per_block<float>(n));
   if (cells_per_block < 0 || cells_per_block > mx) return SIPG_EINVAL;
-  c->lv[level].cb[precision][pass] = cells_per_block;
+  c->lv[level].cb[precision][pass] = cells_per_block ? cells_per_block : c->lv[level].cb0[precision][pass];
   // captured V-cycles hold the old launch shapes
   for (int p = 0; p < 2; ++p) {
     if (c->vgraph[p]) cudaGraphExecDestroy(c->vgraph[p]);
