@@ -154,6 +154,41 @@ def test_cph_penalty_robustness(k):
     assert abs(n10[1] - n10[0]) < 1.0, n10
 
 
+def _golden_phc():
+    out = {}
+    with open(os.path.join(GOLDEN, "n10_cartesian_8cube_phc.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, pf, v = line.split()
+                out[(int(k), float(pf))] = float(v)
+    return out
+
+
+def _n10_of(order, k, pf=1.0):
+    mg = CPHMultigrid(Mesh(8), k, order=order, penalty_factor=pf)
+    fine = mg.levels[-1]
+    b = fine.space.rhs(lambda x: 3 * np.pi ** 2 * _exact(x))
+    _, it, hist = fcg(fine.apply, b, np.zeros_like(b), mg.vcycle)
+    return _n10(hist, it)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_c_transfer_last_near_paper_and_far_above_c_first(k):
+    """phc (p and h on the DG space, c last) near the paper's row, and more than twice the
+    iterations of cph: the paper's main finding on where the c-transfer goes."""
+    phc = _n10_of("phc", k)
+    assert abs(phc - _golden_phc()[(k, 1.0)]) < 1.5, phc
+    assert phc > 2.0 * _n10_of("cph", k)
+
+
+def test_c_transfer_last_is_not_penalty_robust():
+    """With c last the count grows about threefold when the penalty grows by 10^3 (paper: 14.8 ->
+    45.0 at p = 1), where cph stays put (test_cph_penalty_robustness)."""
+    phc1, phc1000 = _n10_of("phc", 1), _n10_of("phc", 1, 1000.0)
+    assert abs(phc1000 - _golden_phc()[(1, 1000.0)]) < 0.15 * _golden_phc()[(1, 1000.0)], phc1000
+    assert phc1000 > 2.5 * phc1
+
+
 def test_dg_transfers_reproduce_coarse_polynomials():
     from oracle.transfer import dg_transfer
     mesh = Mesh((2, 2, 4))
