@@ -348,8 +348,9 @@ sipg_status sipg_set_tile_shape(sipg_ctx *ctx, int level, int precision, int pas
 sipg_status sipg_launch_count(unsigned long long *n);
 
 /* Peak arithmetic probe: runs an independent-FMA loop on every SM for the
- * given precision (0 FP64 DFMA, 1 FP32 FFMA) and returns the measured rate in
- * FLOP/s (2 per FMA).  Not part of the method: used for the roofline. */
+ * given precision (0 FP64 DFMA, 1 FP32 FFMA, 2 FP64 tensor-core mma.sync
+ * m8n8k4) and returns the measured rate in FLOP/s (2 per multiply-add).  Not
+ * part of the method: used for the roofline.  EINVAL for another value. */
 sipg_status sipg_fma_peak(int precision, void *stream, double *flops_per_s);
 
 /* Operator apply that allocates no device memory.  The paper has no

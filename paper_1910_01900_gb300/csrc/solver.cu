@@ -1824,8 +1824,7 @@ sipg_status sipg_launch_count(unsigned long long *n) {
 }
 
 sipg_status sipg_fma_peak(int precision, void *stream, double *flops) {
-  if (!flops || (precision != 0 && precision != 1)) return SIPG_EINVAL;
-  std::string dummy;
+  if (!flops || precision < 0 || precision > 2) return SIPG_EINVAL;
   const cudaError_t e = fma_peak(precision, (cudaStream_t)stream, flops);
   return e == cudaSuccess ? SIPG_OK : SIPG_ECUDA;
 }

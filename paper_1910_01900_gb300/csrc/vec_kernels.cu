@@ -279,12 +279,32 @@ __global__ void fma_probe_kernel(T *sink, int iters, T a, T b) {
   if (s == (T)-12345.678) sink[0] = s;
 }
 
+// FP64 tensor-core probe: four independent m8n8k4 FP64 mma.sync chains per
+// warp (512 flops each per instruction), all SMs busy.
+__global__ void dmma_probe_kernel(double *sink, int iters) {
+  const double a = 1.0 + 1e-9 * threadIdx.x, b = 0.999999;
+  double c[4][2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[k][0] = c[k][1] = (double)k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                   : "+d"(c[k][0]), "+d"(c[k][1])
+                   : "d"(a), "d"(b));
+  }
+  double t = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t += c[k][0] + c[k][1];
+  if (t == -12345.678) sink[0] = t;
+}
+
 cudaError_t fma_peak(int precision, cudaStream_t s, double *flops) {
   int dev, nsm;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = nsm * 8, threads = 256;
-  const int iters = precision == 0 ? 2048 : 65536;
+  const int iters = precision == 1 ? 65536 : 2048;
   void *sink;
   cudaError_t e = cudaMalloc(&sink, 16);
   if (e != cudaSuccess) return e;
@@ -296,8 +316,10 @@ cudaError_t fma_peak(int precision, cudaStream_t s, double *flops) {
     cudaEventRecord(e0, s);
     if (precision == 0)
       fma_probe_kernel<double><<<blocks, threads, 0, s>>>((double *)sink, iters, 0.999999, 1e-7);
-    else
+    else if (precision == 1)
       fma_probe_kernel<float><<<blocks, threads, 0, s>>>((float *)sink, iters, 0.999999f, 1e-7f);
+    else
+      dmma_probe_kernel<<<blocks, threads, 0, s>>>((double *)sink, iters);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float ms;
@@ -308,7 +330,8 @@ cudaError_t fma_peak(int precision, cudaStream_t s, double *flops) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(sink);
-  *flops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3);
+  const double per_thread_iter = precision == 2 ? 4.0 * 512.0 / 32.0 : 2.0 * 8.0;   // flops
+  *flops = per_thread_iter * (double)iters * blocks * threads / (best * 1e-3);
   return e;
 }
 
