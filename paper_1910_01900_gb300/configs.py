@@ -13,7 +13,9 @@ curved32_k4     32^3 curved, k=4: learned smoother (trained on 10^5 pairs) vs Ch
 
 Times are CUDA-event times on the library stream (b and x on the device), the
 median of K repetitions after one warm-up; setup and training are reported
-separately.
+separately.  cube4_k3 and cube32_k4 also report the L2 error of each solution
+against the exact sine solution and the mixed-precision solution's relative
+difference from the FP64 one.
 """
 import argparse
 import json
@@ -71,6 +73,14 @@ def run_single(name, m, k, deform, steps, stream, rhs="manufactured"):
         key = "fp64_mg" if prec == 0 else "mixed"
         res[key] = {"ms": ms, "s_per_mdof": ms * 1e-3 * 1e6 / N, "iterations": info.iterations,
                     "n10": info.n10, "setup_s": setup, "dofs": N}
+        stream.synchronize()
+        if rhs == "manufactured":   # discretisation error against the exact sine solution
+            res[key]["l2_error_vs_exact"] = ctx.l2_error(x)
+        if prec == 0:
+            x_fp64 = x.clone()
+        else:                       # what the FP32 V-cycle changes in the converged solution
+            res[key]["rel_diff_vs_fp64_solution"] = (torch.linalg.norm(x - x_fp64) /
+                                                     torch.linalg.norm(x_fp64)).item()
         ctx.close()
     res["speedup_mixed_vs_fp64_mg"] = res["fp64_mg"]["ms"] / res["mixed"]["ms"]
     return res
