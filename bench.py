@@ -276,11 +276,30 @@ def oracle_apply_time(m, k, deform, N, reps):
     return (time.perf_counter() - t0) / reps
 
 
+def host_cpu():
+    """The host CPU as the OS names it: the model name (x86), else the Arm implementer and part
+    codes (Grace: 0x41 / 0xd4f), else the machine type."""
+    import platform
+    import re
+    try:
+        info = open("/proc/cpuinfo").read()
+        m = re.search(r"^model name\s*:\s*(.+)$", info, re.M)
+        if m:
+            return m.group(1).strip()
+        imp = re.search(r"^CPU implementer\s*:\s*(\S+)", info, re.M)
+        part = re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+        if imp and part:
+            return "%s, implementer %s, part %s" % (platform.machine(), imp.group(1), part.group(1))
+    except OSError:
+        pass
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(m, k, deform, N, reps=2):
     """The FP64 oracle on a bounded sample: full-mesh operator applies, scaled to one solve."""
     t = oracle_apply_time(m, k, deform, N, reps)
     return {"value": t * DG_APPLIES_PER_SOLVE * 1e6 / N, "unit": "s/MDoF", "cores": os.cpu_count(),
-            "kind": "oracle",
+            "cpu": host_cpu(), "kind": "oracle",
             "sample": "%d FP64 oracle applies of the full %d^3 curved k=%d operator (numpy), %.2f s each, "
                       "scaled by the %d fine-level applies of a %d-iteration solve (lower bound: FE levels, "
                       "transfers and vector updates not counted)" % (reps, m, k, t, DG_APPLIES_PER_SOLVE,
@@ -316,7 +335,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "curved16_k5: 16^3 curved cube, k=5, %d DoF, FP64" % N},
            "cpu_baseline": {"value": value, "unit": "s/MDoF", "kind": "oracle", "cores": os.cpu_count(),
-                            "sample": sample},
+                            "cpu": host_cpu(), "sample": sample},
            "e2e": {"value": value, "unit": "s/MDoF", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -63,3 +63,10 @@ def test_reference_arm_runs_on_rank_zero_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_host_cpu_is_named():
+    sys.path.insert(0, ROOT)
+    import bench
+    name = bench.host_cpu()
+    assert isinstance(name, str) and name and name != "unknown"
