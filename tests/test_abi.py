@@ -49,6 +49,29 @@ def test_default_params_and_create_rejects_bad_input(lib):
     p.degree = 0   # invalid: rejected before any device work
     assert lib.sipg_create(ctypes.byref(mesh), ctypes.byref(p), ctypes.byref(h)) == native.EINVAL
     assert b"degree" in lib.sipg_last_error(None)
+    # a non-positive penalty would make the operator indefinite: refused at setup, as are other
+    # out-of-range parameters and mesh descriptions
+    good, _ = native.make_mesh(4)
+    for field, value, word in (("penalty_factor", -1.0, b"penalty"), ("penalty_factor", 0.0, b"penalty"),
+                               ("precision", 2, b"precision"), ("cheb_degree", 0, b"smoother"),
+                               ("p_coarsen", 3, b"smoother")):
+        q = native.Params()
+        lib.sipg_default_params(ctypes.byref(q))
+        setattr(q, field, value)
+        assert lib.sipg_create(ctypes.byref(good), ctypes.byref(q), ctypes.byref(h)) == native.EINVAL, field
+        assert word in lib.sipg_last_error(None), (field, lib.sipg_last_error(None))
+    q = native.Params()
+    lib.sipg_default_params(ctypes.byref(q))
+    for field, value, word in (("bc", 2, b"bc"), ("m", 0, b"m must"), ("mapping_degree", 2, b"mapping")):
+        bad, _ = native.make_mesh(4, deform=1)
+        if field == "bc":
+            bad.bc[3] = value
+        elif field == "m":
+            bad.m[1] = value
+        else:
+            bad.mapping_degree = value
+        assert lib.sipg_create(ctypes.byref(bad), ctypes.byref(q), ctypes.byref(h)) == native.EINVAL, field
+        assert word in lib.sipg_last_error(None), (field, lib.sipg_last_error(None))
 
 
 def test_product_package_has_no_cpu_fallback():

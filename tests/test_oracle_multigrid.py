@@ -189,6 +189,27 @@ def test_c_transfer_last_is_not_penalty_robust():
     assert phc1000 > 2.5 * phc1
 
 
+def test_cph_iterations_are_mesh_independent():
+    """h-robustness: cph counts on 4^3 and 8^3 near the paper's rows and within one iteration of
+    each other (the paper's table varies by at most 1.8 from 4^3 to 16^3 at p = 1, 2)."""
+    ref = {}
+    with open(os.path.join(GOLDEN, "n10_cartesian_cph_h_robustness.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                m, k, v = line.split()
+                ref[(int(m), int(k))] = float(v)
+    for k in (1, 2):
+        n = {}
+        for m in (4, 8):
+            mg = CPHMultigrid(Mesh(m), k)
+            fine = mg.levels[-1]
+            b = fine.space.rhs(lambda x: 3 * np.pi ** 2 * _exact(x))
+            _, it, hist = fcg(fine.apply, b, np.zeros_like(b), mg.vcycle)
+            n[m] = _n10(hist, it)
+            assert abs(n[m] - ref[(m, k)]) < 1.5, (m, k, n[m])
+        assert abs(n[4] - n[8]) < 1.0, (k, n)
+
+
 def test_dg_transfers_reproduce_coarse_polynomials():
     from oracle.transfer import dg_transfer
     mesh = Mesh((2, 2, 4))
