@@ -133,3 +133,42 @@ def test_null_handles_and_bad_arguments_are_rejected_before_device_work(lib):
     assert sorted(calls) == sorted(set(_declared()) - skip)
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == native.EINVAL, name
+
+
+def test_header_is_plain_c_and_a_c_program_links_and_runs(lib, tmp_path):
+    """include/sipg.h compiles as strict C99 (no C++ or framework types), and a C program linked
+    against libsipg.so gets SIPG_EINVAL and the error text for a bad setup, with no GPU needed."""
+    import shutil
+    import subprocess
+    from paper_1910_01900_gb300 import native
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_sipg.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "sipg.h"
+int main(void) {
+  sipg_mesh mesh;
+  sipg_params prm;
+  sipg_ctx *ctx = NULL;
+  memset(&mesh, 0, sizeof mesh);
+  sipg_default_params(&prm);
+  for (int d = 0; d < 3; ++d) { mesh.m[d] = 4; mesh.lo[d] = 0.0; mesh.hi[d] = 1.0; }
+  mesh.mapping_degree = 3;
+  prm.degree = 9;                       /* out of range: refused before any device work */
+  sipg_status st = sipg_create(&mesh, &prm, &ctx);
+  printf("%d %s\n", (int)st, sipg_last_error(NULL));
+  return (st == SIPG_EINVAL && ctx == NULL) ? 0 : 1;
+}
+''')
+    exe = tmp_path / "use_sipg"
+    libdir = os.path.dirname(native.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lsipg",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.stdout, r.stderr)
+    assert r.stdout.startswith("%d " % native.EINVAL) and "degree" in r.stdout
