@@ -4,7 +4,7 @@ The iteration counts n10 of the paper's robustness tables (Cartesian 8^3,
 Chebyshev(5,5)) pin the multigrid loosely: the paper's coarse solve is AMG-CG
 to 1e-3 and its cube [-1, 1]^3, here the coarse solve is exact and the cube the
 unit cube.  What the tables fix firmly are the structural findings:
-  * cph iteration counts near the paper's row (golden file, +-1.5),
+  * cph iteration counts near the paper's rows, Cartesian and curved (golden files, +-1.5),
   * the c-transfer on the finest level cuts iterations by a large factor
     against the same steps with c last (phc),
   * with c first the count does not depend on the penalty factor, with c last
@@ -48,6 +48,12 @@ def _n10(k, order="cph", pseq=0, pf=1.0, curved=0, precision=1):
 def test_cph_iterations_near_paper_table(k):
     ref = _golden("n10_cartesian_8cube_cph.txt", 2)[(k,)]
     assert abs(_n10(k) - ref) < 1.5
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_cph_iterations_on_the_curved_mesh_near_paper_table(k):
+    ref = _golden("n10_curvilinear_8cube_cph.txt", 2)[(k,)]
+    assert abs(_n10(k, curved=1) - ref) < 1.5
 
 
 @pytest.mark.parametrize("k", [2, 3])
