@@ -140,11 +140,14 @@ class CPHMultigrid:
     Table SummaryCoarseningStrategies): 'c' DG -> FE at equal h and p, 'p'
     all polynomial levels down to degree 1, 'h' all geometric levels.  The
     default 'cph' is the paper's preferred strategy.  The coarsest level is
-    solved directly (its space is DG when the order has no 'c').
+    solved directly (its space is DG when the order has no 'c'), or with
+    ``coarse="amg"`` by CG preconditioned with smoothed-aggregation AMG to
+    ``amg_rtol`` (Section 3.3, ``oracle.amg``).
     """
 
     def __init__(self, mesh, k, penalty_factor=1.0, ns=5, cheb_lo=0.06, cheb_hi=1.2,
-                 eig_iters=20, lambdas=None, assemble_limit=6e7, p_rule="half", order="cph"):
+                 eig_iters=20, lambdas=None, assemble_limit=6e7, p_rule="half", order="cph", coarse="dense",
+                 amg_rtol=1e-3):
         self.ns, self.cheb_lo, self.cheb_hi = ns, cheb_lo, cheb_hi
 
         def make(kind, p, msh):
@@ -186,7 +189,11 @@ class CPHMultigrid:
         for l, lev in enumerate(self.levels):
             if l == 0:
                 A0 = lev.A if lev.A is not None else lev.space.assemble()
-                self.coarse = CoarseCholesky(A0)
+                if coarse == "amg":
+                    from .amg import AMGCoarseSolver
+                    self.coarse = AMGCoarseSolver(A0, rtol=amg_rtol)
+                else:
+                    self.coarse = CoarseCholesky(A0)
                 continue
             lev.diag = lev.space.diagonal()
             lev.dinv = 1.0 / lev.diag
