@@ -88,7 +88,14 @@ def forward(X, Ws, bs, bf16=False):
 
 
 def loss_and_grads(X, T, Ws, bs, bf16=False):
-    """Mean squared error L = sum ||y - t||^2 / (2 B) and its gradients."""
+    """Mean squared error L = sum ||y - t||^2 / (2 B) and its gradients.
+
+    With ``bf16=True`` the backward contractions take BF16 operands, as the
+    forward ones do: the output error D = (y - t) / B and every error passed
+    back through a layer are rounded to BF16 before they enter a product (the
+    last layer's bias gradient sums the unrounded D).  These are the rounding
+    points of a network whose matrix products all read BF16 values.
+    """
     q = bf16_round if bf16 else (lambda a: a)
     B = X.shape[0]
     Y, acts = forward(X, Ws, bs, bf16)
@@ -96,8 +103,9 @@ def loss_and_grads(X, T, Ws, bs, bf16=False):
     L = 0.5 * float(np.sum((Y - T) ** 2)) / B
     gW, gb = [None] * len(Ws), [None] * len(Ws)
     for i in range(len(Ws) - 1, -1, -1):
-        gW[i] = acts[i].T @ D
-        gb[i] = D.sum(axis=0)
+        Dq = q(D)
+        gW[i] = acts[i].T @ Dq
+        gb[i] = (D if i == len(Ws) - 1 else Dq).sum(axis=0)
         if i > 0:
-            D = (D @ q(Ws[i]).T) * (acts[i] > 0)
+            D = q(Dq @ q(Ws[i]).T) * (acts[i] > 0)
     return L, gW, gb

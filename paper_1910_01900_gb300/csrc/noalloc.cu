@@ -79,8 +79,11 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int degree, double penalty_factor,
                                                    const double *u_dev, double *v_dev, void *stream) {
   using namespace sipg;
-  if (!mesh || !u_dev || !v_dev || u_dev == v_dev) {
-    sipg::set_global_error("null or aliased argument");
+  // an error left pending by earlier, unrelated work of the caller would
+  // otherwise be reported as this call's failure
+  (void)cudaGetLastError();
+  if (!mesh || !u_dev || !v_dev) {
+    sipg::set_global_error("null argument");
     return SIPG_EINVAL;
   }
   if (degree < 1 || degree > 8 || !(penalty_factor > 0) || mesh->deform != 0) {
@@ -92,6 +95,13 @@ extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int de
       sipg::set_global_error("m must be >= 1 and extents positive");
       return SIPG_EINVAL;
     }
+  // the cell count in double first, so that none of the byte counts below is
+  // formed from a wrapped integer product (m = 2^21 per axis wraps 64 bits)
+  const double cells_d = (double)mesh->m[0] * mesh->m[1] * mesh->m[2];
+  if (cells_d > (double)(1 << 30)) {
+    sipg::set_global_error("problem needs more than the 64 MiB static scratch of sipg_operator_apply_noalloc");
+    return SIPG_EINVAL;
+  }
   for (int s = 0; s < 6; ++s)
     if (mesh->bc[s] != 0 && mesh->bc[s] != 1) {
       sipg::set_global_error("bc must be 0 or 1");
@@ -104,9 +114,17 @@ extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int de
   const size_t b_tau = align256((size_t)E * sizeof(double));
   const size_t b_w = align256((size_t)3 * n3 * sizeof(double));
   const size_t b_fw = align256((size_t)3 * n2 * sizeof(double));
-  if (E > (1LL << 30) || b_grad + b_trace + b_tau + b_w + b_fw > kScratchBytes) {
+  if (b_grad + b_trace + b_tau + b_w + b_fw > kScratchBytes) {
     sipg::set_global_error("problem needs more than the 64 MiB static scratch of sipg_operator_apply_noalloc");
     return SIPG_EINVAL;
+  }
+  {
+    // u and v must not overlap anywhere (v is written while u is still read)
+    const uintptr_t pu = (uintptr_t)u_dev, pv = (uintptr_t)v_dev, bytes = (uintptr_t)E * n3 * sizeof(double);
+    if (pu < pv + bytes && pv < pu + bytes) {
+      sipg::set_global_error("u and v overlap");
+      return SIPG_EINVAL;
+    }
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -128,8 +146,10 @@ extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int de
       static std::once_flag built;
       std::call_once(built, [] { build_tables(tab); });
       upload_tables_dg<double>(tab);
-      if (cudaGetLastError() != cudaSuccess || prepare_dg_kernels<double>() != cudaSuccess) {
-        sipg::set_global_error("table upload failed");
+      cudaError_t ue = cudaGetLastError();
+      if (ue == cudaSuccess) ue = prepare_dg_kernels<double>();
+      if (ue != cudaSuccess) {
+        sipg::set_global_error(std::string("table upload failed: ") + cudaGetErrorString(ue));
         return SIPG_ECUDA;
       }
       g_scratch_addr[dev] = p;
@@ -153,6 +173,11 @@ extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int de
   noalloc_prep_kernel<<<grid, bs, 0, s>>>(wcart, fwcart, tau, n, W, h[0], h[1], h[2], mesh->m[0], mesh->m[1],
                                           mesh->m[2], penalty_factor);
   note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    sipg::set_global_error(std::string("launch failed: ") + cudaGetErrorString(e));
+    return SIPG_ECUDA;
+  }
   DGArgs<double> a{};
   a.u = u_dev;
   a.out = v_dev;
@@ -168,8 +193,7 @@ extern "C" sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int de
   a.ncells = (int)E;
   for (int q = 0; q < 6; ++q) a.bc[q] = mesh->bc[q];
   a.mode = 0;
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_dg_eval<double>(n, false, a, s);
+  e = launch_dg_eval<double>(n, false, a, s);
   if (e == cudaSuccess) e = launch_dg_integrate<double>(n, false, a, s);
   if (e != cudaSuccess) {
     sipg::set_global_error(std::string("launch failed: ") + cudaGetErrorString(e));

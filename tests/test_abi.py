@@ -172,3 +172,32 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.stdout, r.stderr)
     assert r.stdout.startswith("%d " % native.EINVAL) and "degree" in r.stdout
+
+
+def test_noalloc_apply_rejects_before_device_work(lib):
+    """sipg_operator_apply_noalloc checks its arguments before touching a device: cell counts
+    whose integer product would wrap (2^21 cells per axis), meshes beyond its static scratch,
+    curved cells, and input and output ranges that overlap all give SIPG_EINVAL."""
+    import ctypes
+    from paper_1910_01900_gb300 import native
+
+    def mesh(m, deform=0):
+        ms = native.Mesh()
+        for d in range(3):
+            ms.m[d], ms.lo[d], ms.hi[d] = m, 0.0, 1.0
+        ms.deform, ms.amp, ms.mapping_degree = deform, 0.1 if deform else 0.0, 3
+        return ms
+
+    buf = (ctypes.c_double * 2)()
+    other = (ctypes.c_double * 2)()
+    u, v = ctypes.cast(buf, ctypes.c_void_p), ctypes.cast(other, ctypes.c_void_p)
+    for ms, deg, word in ((mesh(1 << 21), 1, b"64 MiB"), (mesh(64), 8, b"64 MiB"), (mesh(2, deform=1), 2, b"deform")):
+        st = lib.sipg_operator_apply_noalloc(ctypes.byref(ms), deg, 1.0, u, v, None)
+        assert st == native.EINVAL
+        assert word in lib.sipg_last_error(None)
+    # one cell of degree 1 has 8 values: v starting 4 values into u overlaps it
+    one = mesh(1)
+    st = lib.sipg_operator_apply_noalloc(ctypes.byref(one), 1, 1.0, u, ctypes.c_void_p(u.value + 32), None)
+    assert st == native.EINVAL and b"overlap" in lib.sipg_last_error(None)
+    st = lib.sipg_operator_apply_noalloc(ctypes.byref(one), 1, 1.0, u, u, None)
+    assert st == native.EINVAL and b"overlap" in lib.sipg_last_error(None)

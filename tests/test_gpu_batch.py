@@ -11,14 +11,11 @@ import sipg_inputs
 from oracle.dg import SIPG
 from oracle.mesh import Mesh
 from oracle.multigrid import CPHMultigrid, fcg
+from parity_check import close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
 PROBS = [dict(m=4, k=2), dict(m=(6, 4, 3), k=3), dict(m=4, k=5), dict(m=(2, 3, 2), k=8), dict(m=(7, 6, 5), k=1),
@@ -43,9 +40,9 @@ def test_batched_apply_equals_single_problem_and_oracle(deform):
     B.apply(us, vs)
     torch.cuda.synchronize()
     for i, p in enumerate(probs):
-        assert rel(vs[i].cpu().numpy(), refs[i].cpu().numpy()) <= 1e-14, i
+        assert close(vs[i].cpu().numpy(), refs[i].cpu().numpy()) <= 1e-14, i
         o = SIPG(Mesh(p["m"], deform=deform), p["k"]).apply(us[i].cpu().numpy())
-        assert rel(vs[i].cpu().numpy(), o) <= 1e-12, i
+        assert close(vs[i].cpu().numpy(), o) <= 1e-12, i
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -62,13 +59,15 @@ def test_batched_solve_equals_single_solves(precision):
         x = torch.zeros_like(bs[i])
         info = c.solve(bs[i], x, rtol=1e-10)
         assert infos[i].converged and infos[i].iterations == info.iterations, i
-        assert rel(xs[i].cpu().numpy(), x.cpu().numpy()) <= (1e-12 if precision == 0 else 1e-9), i
+        assert close(xs[i].cpu().numpy(), x.cpu().numpy()) <= (1e-12 if precision == 0 else 1e-9), i
     # and one of them against the oracle's solve
     mg = CPHMultigrid(Mesh(4), 3)
     bo = bs[0].cpu().numpy()
     xo, it, _ = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
-    assert infos[0].iterations == it or precision == 1
-    assert rel(xs[0].cpu().numpy(), xo) <= (1e-10 if precision == 0 else 1e-8)
+    # the FP32 cycle is the FP64 cycle rounded: a different (nearby) preconditioner, so its
+    # count may move by one where the residual crosses 1e-10 between two iterations
+    assert abs(infos[0].iterations - it) <= (0 if precision == 0 else 1)
+    assert close(xs[0].cpu().numpy(), xo) <= (1e-10 if precision == 0 else 1e-8)
 
 
 def test_seeded_uneven_batch_converges():
@@ -108,7 +107,7 @@ def test_32_right_hand_sides():
         x = torch.zeros_like(bs[r])
         info = c.solve(bs[r], x, rtol=1e-10)
         assert info.iterations == infos[r].iterations
-        assert rel(xs[r].cpu().numpy(), x.cpu().numpy()) <= 1e-9
+        assert close(xs[r].cpu().numpy(), x.cpu().numpy()) <= 1e-9
 
 
 @pytest.mark.parametrize("precision,deform,vec_dtype", [(0, 0, torch.float64), (1, 1, torch.float32),
@@ -131,7 +130,7 @@ def test_apply_multi_equals_single_applies(precision, deform, vec_dtype):
         ctx.apply(U[r].contiguous(), ref)
         torch.cuda.synchronize()
         assert torch.equal(V[r], ref), r
-        assert rel(V[r].cpu().numpy(), o.apply(U[r].cpu().numpy().astype(np.float64))) <= \
+        assert close(V[r].cpu().numpy(), o.apply(U[r].cpu().numpy().astype(np.float64))) <= \
             (1e-12 if dt == torch.float64 else 1e-5)
 
 
@@ -153,11 +152,11 @@ def test_solve_multi_equals_single_solves(precision):
         x = torch.zeros(n, dtype=torch.float64, device=DEV)
         info = single.solve(B[r].contiguous(), x, rtol=1e-10)
         assert infos[r].converged and infos[r].iterations == info.iterations, r
-        assert rel(X[r].cpu().numpy(), x.cpu().numpy()) <= (1e-12 if precision == 0 else 1e-9), r
+        assert close(X[r].cpu().numpy(), x.cpu().numpy()) <= (1e-12 if precision == 0 else 1e-9), r
     mg = CPHMultigrid(Mesh(m), k)
     bo = B[0].cpu().numpy()
     xo, it, _ = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
-    assert rel(X[0].cpu().numpy(), xo) <= (1e-10 if precision == 0 else 1e-8)
+    assert close(X[0].cpu().numpy(), xo) <= (1e-10 if precision == 0 else 1e-8)
     if precision == 0:
         assert infos[0].iterations == it
     # a second call with fewer right-hand sides reuses the work set
@@ -171,7 +170,7 @@ def test_solve_multi_equals_single_solves(precision):
     infos3 = ctx.solve_multi(B3, X3, rtol=1e-10)
     torch.cuda.synchronize()
     assert torch.equal(X3[:nrhs], X) and all(i.converged for i in infos3)
-    assert rel(X3[nrhs:].cpu().numpy(), -2.0 * X[:3].cpu().numpy()) <= 1e-9
+    assert close(X3[nrhs:].cpu().numpy(), -2.0 * X[:3].cpu().numpy()) <= 1e-9
 
 
 def test_solve_multi_zero_and_nan_rows():

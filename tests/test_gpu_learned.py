@@ -5,6 +5,7 @@ import pytest
 
 import sipg_inputs
 from oracle import mlp
+from parity_check import close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -60,13 +61,14 @@ def test_forward_and_gradients_match_cpu_network():
     ctx.mlp_forward(torch.as_tensor(X).to(DEV), Y)
     yref, _ = mlp.forward(X.astype(np.float64), Ws, bs, bf16=True)
     y = Y.cpu().numpy().reshape(B, sh["out_pad"])[:, :sh["out_dim"]]
-    assert np.linalg.norm(y - yref) / np.linalg.norm(yref) <= 1e-2
+    assert close(y, yref) <= 1e-2
     g, loss = ctx.mlp_gradients(torch.as_tensor(X).to(DEV), torch.as_tensor(T).to(DEV))
+    # the oracle network rounds the same operands to BF16 as the GPU's products read
     L, gW, gb = mlp.loss_and_grads(X.astype(np.float64), T.astype(np.float64), Ws, bs, bf16=True)
     assert abs(loss - L) <= 1e-2 * L
     gWs, gbs = _split(g, sh)
     for a, b in zip(gWs + gbs, gW + gb):
-        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 3e-2
+        assert close(a, b) <= 1e-2
 
 
 @pytest.mark.parametrize("k,B", [(4, 1), (4, 129), (5, 300), (6, 77)])
@@ -87,7 +89,7 @@ def test_forward_row_tails_and_widths(k, B):
     yref, _ = mlp.forward(X.astype(np.float64), Ws, bs, bf16=True)
     y = Y.cpu().numpy().reshape(B, sh["out_pad"])[:, :sh["out_dim"]]
     assert np.all(np.isfinite(y))
-    assert np.linalg.norm(y - yref) / np.linalg.norm(yref) <= 1e-2
+    assert close(y, yref) <= 1e-2
 
 
 def test_training_and_learned_solve():
@@ -99,7 +101,7 @@ def test_training_and_learned_solve():
     # what the network gains: one damped network step removes part of the residual the
     # post-smoother faces (after pre-smoothing and coarse-grid correction); 0.92 on this
     # small mesh, 0.75 on the 32^3 k=4 workload
-    assert 0 < info.damping and info.step_reduction < 0.99, (info.damping, info.step_reduction)
+    assert 0 < info.damping and info.step_reduction < 0.95, (info.damping, info.step_reduction)
     b = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_RHS)).to(DEV)
     x0 = torch.zeros_like(b)
     ref = ctx.solve(b, x0, rtol=1e-10)
@@ -107,13 +109,12 @@ def test_training_and_learned_solve():
     x1 = torch.zeros_like(b)
     got = ctx.solve(b, x1, rtol=1e-10, maxit=200)
     assert got.converged and got.learned == 1
-    err = (torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0)).item()
-    assert err <= 1e-8
+    assert close(x1, x0) <= 1e-8
     ctx.set_smoother(1)   # default: Chebyshev pre-smoothing, one network post-step
     x2 = torch.zeros_like(b)
     got2 = ctx.solve(b, x2, rtol=1e-10, maxit=200)
     assert got2.converged and got2.learned == 1
-    assert (torch.linalg.norm(x2 - x0) / torch.linalg.norm(x0)).item() <= 1e-8
+    assert close(x2, x0) <= 1e-8
     # what the network adds to the V-cycle: the energy norm of the error left by one cycle with
     # Chebyshev pre-smoothing and no post-smoothing (the cycle without the network), and by the
     # same cycle with one network post-step

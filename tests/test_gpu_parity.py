@@ -1,8 +1,11 @@
 """GPU parity: libsipg (through the C ABI) against the FP64 CPU oracle.
 
-Tolerances (relative 2-norm): FP64 <= 1e-12, FP32 <= 1e-5 for single operator
-applications; whole-cycle and solve comparisons use the bounds stated at each
-test (more operations, same arithmetic up to summation order).
+Every comparison is element by element (parity_check.close: the largest entry
+error against the largest reference entry, and the relative 2-norm, whichever
+is larger).  Tolerances: FP64 <= 1e-12, FP32 <= 1e-5 for single operator
+applications, transfers, diagonals and the coarse solve; whole-cycle and solve
+comparisons use the bounds stated at each test (more operations, same
+arithmetic up to summation order).
 """
 import numpy as np
 import pytest
@@ -13,6 +16,7 @@ from oracle.fe import FESpace
 from oracle.mesh import Mesh
 from oracle.multigrid import CPHMultigrid, chebyshev, fcg
 from oracle.transfer import c_transfer, fe_transfer
+from parity_check import close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -23,11 +27,6 @@ DEV = "cuda:0"
 def _ctx(*a, **kw):
     from paper_1910_01900_gb300 import Context
     return Context(*a, **kw)
-
-
-def rel(a, b):
-    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def gpu(x, dtype=torch.float64):
@@ -50,10 +49,10 @@ def test_operator_apply_fp64_fp32(k, deform):
     ref = SIPG(Mesh(m, lo=lo, hi=hi, deform=deform, bc=bc), k).apply(u)
     v = torch.empty(len(u), dtype=torch.float64, device=DEV)
     ctx.apply(gpu(u), v)
-    assert rel(v.cpu().numpy(), ref) <= 1e-12
+    assert close(v.cpu().numpy(), ref) <= 1e-12
     v32 = torch.empty(len(u), dtype=torch.float32, device=DEV)
     ctx.apply(gpu(u, torch.float32), v32)
-    assert rel(v32.cpu().numpy(), ref) <= 1e-5
+    assert close(v32.cpu().numpy(), ref) <= 1e-5
 
 
 def test_single_cell_and_pure_neumann():
@@ -62,7 +61,7 @@ def test_single_cell_and_pure_neumann():
         u = sipg_inputs.uniform(ctx.num_dofs(), 7)
         v = torch.empty(len(u), dtype=torch.float64, device=DEV)
         ctx.apply(gpu(u), v)
-        assert rel(v.cpu().numpy(), SIPG(Mesh(1), k).apply(u)) <= 1e-12
+        assert close(v.cpu().numpy(), SIPG(Mesh(1), k).apply(u)) <= 1e-12
     ctx = _ctx(3, 3, deform=1, bc=(1,) * 6, operator_only=True)
     one = torch.ones(ctx.num_dofs(), dtype=torch.float64, device=DEV)
     v = torch.empty_like(one)
@@ -106,11 +105,11 @@ def test_levels_diagonals_and_fe_apply(m, k, deform):
         for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
             v = torch.empty(lev.n, dtype=dt, device=DEV)
             ctx.level_apply(l, gpu(u, dt), v)
-            assert rel(v.cpu().numpy(), ref) <= tol, (l, dt)
+            assert close(v.cpu().numpy(), ref) <= tol, (l, dt)
         if l > 0:
             d = torch.empty(lev.n, dtype=torch.float64, device=DEV)
             ctx.inverse_diagonal(l, d)
-            assert rel(d.cpu().numpy(), lev.dinv) <= 1e-12
+            assert close(d.cpu().numpy(), lev.dinv) <= 1e-12
 
 
 @pytest.mark.parametrize("deform,bc", [(1, (0, 1, 0, 0, 1, 0)), (0, (1, 1, 0, 1, 1, 1))])
@@ -136,8 +135,8 @@ def test_assembled_low_degree_levels_match_matrix_free(deform, bc):
             ctx_a.level_apply(l, gpu(u, dt), va)
             ctx_f.level_apply(l, gpu(u, dt), vf)
             torch.cuda.synchronize()
-            assert rel(va.cpu().numpy(), ref) <= tol, (l, dt)
-            assert rel(vf.cpu().numpy(), ref) <= tol, (l, dt)
+            assert close(va.cpu().numpy(), ref) <= tol, (l, dt)
+            assert close(vf.cpu().numpy(), ref) <= tol, (l, dt)
         checked += 1
     assert checked == 2
     r = gpu(sipg_inputs.uniform(ctx_a.num_dofs(), 77))
@@ -146,7 +145,7 @@ def test_assembled_low_degree_levels_match_matrix_free(deform, bc):
     ctx_f.vcycle(r, zf)
     torch.cuda.synchronize()
     zo = mg.vcycle(r.cpu().numpy())
-    assert rel(za.cpu().numpy(), zo) <= 1e-12 and rel(zf.cpu().numpy(), zo) <= 1e-12
+    assert close(za.cpu().numpy(), zo) <= 1e-12 and close(zf.cpu().numpy(), zo) <= 1e-12
 
 
 @pytest.mark.parametrize("m,k,deform", [(6, 4, 0), (6, 5, 1), (8, 2, 0)])
@@ -157,7 +156,7 @@ def test_transfers_match_sparse_matrices(m, k, deform):
         r = sipg_inputs.uniform(mg.levels[l].n, 200 + l)
         rc = torch.empty(mg.levels[l - 1].n, dtype=torch.float64, device=DEV)
         ctx.restrict(l, gpu(r), rc)
-        assert rel(rc.cpu().numpy(), P.T @ r) <= 1e-12, l
+        assert close(rc.cpu().numpy(), P.T @ r) <= 1e-12, l
         xc = sipg_inputs.uniform(mg.levels[l - 1].n, 300 + l)
         sp = mg.levels[l - 1].space
         xc[sp.constrained] = 0.0
@@ -166,7 +165,7 @@ def test_transfers_match_sparse_matrices(m, k, deform):
             x0[mg.levels[l].space.constrained] = 0.0
         x = gpu(x0)
         ctx.prolongate_add(l, gpu(xc), x)
-        assert rel(x.cpu().numpy(), x0 + P @ xc) <= 1e-12, l
+        assert close(x.cpu().numpy(), x0 + P @ xc) <= 1e-12, l
 
 
 def test_coarse_solve_and_lambda_estimates():
@@ -176,7 +175,7 @@ def test_coarse_solve_and_lambda_estimates():
     b[mg.levels[0].space.constrained] = 0.0
     x = torch.empty(len(b), dtype=torch.float64, device=DEV)
     ctx.coarse_solve(gpu(b), x)
-    assert rel(x.cpu().numpy(), mg.coarse.solve(b)) <= 1e-12
+    assert close(x.cpu().numpy(), mg.coarse.solve(b)) <= 1e-12
     for l in range(1, len(mg.levels)):
         assert abs(ctx.lam(l) - mg.levels[l].lam) <= 1e-10 * mg.levels[l].lam, l
 
@@ -195,7 +194,7 @@ def test_chebyshev_smoother(level_from_top):
     ref = chebyshev(lev.apply, lev.dinv, b, x0, 1.7, 5)
     x = gpu(x0)
     ctx.smooth(l, gpu(b), x, 5)
-    assert rel(x.cpu().numpy(), ref) <= 1e-11
+    assert close(x.cpu().numpy(), ref) <= 1e-11
 
 
 @pytest.mark.parametrize("m,k,deform", [(4, 3, 0), (6, 3, 1), (4, 2, 1)])
@@ -205,10 +204,10 @@ def test_vcycle_fp64_and_fp32(m, k, deform):
     ref = mg.vcycle(r)
     z = torch.empty(len(r), dtype=torch.float64, device=DEV)
     ctx.vcycle(gpu(r), z)
-    assert rel(z.cpu().numpy(), ref) <= 1e-11
+    assert close(z.cpu().numpy(), ref) <= 1e-11
     ctx32 = _ctx(m, k, deform=deform, precision=1, lambda_override=2.2)
     ctx32.vcycle(gpu(r), z)
-    assert rel(z.cpu().numpy(), ref) <= 1e-5
+    assert close(z.cpu().numpy(), ref) <= 1e-5
 
 
 def test_fixed_iteration_fcg_matches_oracle():
@@ -219,7 +218,7 @@ def test_fixed_iteration_fcg_matches_oracle():
     x = torch.zeros(len(b), dtype=torch.float64, device=DEV)
     info = ctx.solve(gpu(b), x, fixed_iters=3)
     assert info.iterations == 3
-    assert rel(x.cpu().numpy(), ref) <= 1e-11
+    assert close(x.cpu().numpy(), ref) <= 1e-11
     assert abs(info.res_history[3] - hist[3]) <= 1e-9 * hist[3]
 
 
@@ -229,18 +228,18 @@ def test_solve_to_1e10_same_iterations_as_oracle(m, k, deform):
     b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
     ctx.rhs(b)
     bo = mg.levels[-1].space.rhs(lambda x: 3 * np.pi ** 2 * np.prod(np.sin(np.pi * x), axis=-1))
-    assert rel(b.cpu().numpy(), bo) <= 1e-12
+    assert close(b.cpu().numpy(), bo) <= 1e-12
     ref, it, hist = fcg(mg.levels[-1].apply, bo, np.zeros_like(bo), mg.vcycle, rtol=1e-10)
     x = torch.zeros_like(b)
     info = ctx.solve(b, x, rtol=1e-10)
     assert info.converged and info.iterations == it
-    assert rel(x.cpu().numpy(), ref) <= 1e-10
+    assert close(x.cpu().numpy(), ref) <= 1e-10
     # mixed precision: FP32 cycle, FP64 residual, same tolerance reached
     ctx32 = _ctx(m, k, deform=deform, precision=1)
     x32 = torch.zeros_like(b)
     info32 = ctx32.solve(b, x32, rtol=1e-10)
     assert info32.converged and abs(info32.iterations - it) <= 1
-    assert rel(x32.cpu().numpy(), ref) <= 1e-8
+    assert close(x32.cpu().numpy(), ref) <= 1e-8
 
 
 def test_solve_from_a_nonzero_start_vector():
@@ -255,10 +254,10 @@ def test_solve_from_a_nonzero_start_vector():
     info = ctx.solve(gpu(bo), x, rtol=1e-10)
     assert info.converged and info.iterations == it
     assert abs(info.r0_norm - hist[0]) <= 1e-12 * hist[0]
-    assert rel(x.cpu().numpy(), ref) <= 1e-10
+    assert close(x.cpu().numpy(), ref) <= 1e-10
     xz = torch.zeros_like(x)
     ctx.solve(gpu(bo), xz, rtol=1e-12)
-    assert rel(x.cpu().numpy(), xz.cpu().numpy()) <= 1e-6
+    assert close(x.cpu().numpy(), xz.cpu().numpy()) <= 1e-6
 
 
 def test_solve_host_round_trip_and_nan_rejected():
@@ -270,7 +269,7 @@ def test_solve_host_round_trip_and_nan_rejected():
     bh = b.cpu().numpy().copy()
     xh = np.zeros_like(bh)
     ctx.solve_host(bh, xh)
-    assert rel(xh, x.cpu().numpy()) <= 1e-13
+    assert close(xh, x.cpu().numpy()) <= 1e-13
     from paper_1910_01900_gb300 import SipgError
     bh[3] = np.nan
     with pytest.raises(SipgError):
@@ -288,7 +287,7 @@ def _sampled_apply_check(m, k, deform, cells, precision=0):
     ref = SIPG(Mesh(m, deform=deform), k).apply(u, cells=cells)
     n3 = (k + 1) ** 3
     sel = np.concatenate([np.arange(c * n3, (c + 1) * n3) for c in cells])
-    return rel(vv[sel], ref[sel])
+    return close(vv[sel], ref[sel])
 
 
 def test_full_size_curved16_k5_sampled():
@@ -318,7 +317,7 @@ def test_autotuned_tile_shapes_keep_parity(k, deform):
     for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
         v = torch.empty(len(u), dtype=dt, device=DEV)
         ctx.apply(gpu(u, dt), v)
-        assert rel(v.cpu().numpy(), ref) <= tol
+        assert close(v.cpu().numpy(), ref) <= tol
     from paper_1910_01900_gb300.csrc_info import max_cells_per_block
     for prec in (0, 1):
         for p in (0, 1):
@@ -336,7 +335,7 @@ def test_every_tile_width_gives_identical_results(k, deform):
     ref64 = torch.empty_like(u64)
     ctx.apply(u64, ref64)
     torch.cuda.synchronize()
-    assert rel(ref64.cpu().numpy(), SIPG(Mesh(m, deform=deform), k).apply(u64.cpu().numpy())) <= 1e-12
+    assert close(ref64.cpu().numpy(), SIPG(Mesh(m, deform=deform), k).apply(u64.cpu().numpy())) <= 1e-12
     for level in range(1, ctx.num_levels):
         kind, deg, _ = ctx.level_info(level)
         passes = (0, 1) if kind == 0 else (2,)
@@ -423,7 +422,7 @@ def test_other_p_sequences_match_oracle(rule, code):
     x = torch.zeros_like(b)
     info = ctx.solve(b, x, rtol=1e-10)
     assert info.iterations == it
-    assert rel(x.cpu().numpy(), ref) <= 1e-10
+    assert close(x.cpu().numpy(), ref) <= 1e-10
 
 
 @pytest.mark.parametrize("order,m,k", [("chp", 6, 2), ("pch", 6, 3), ("phc", 6, 2), ("hpc", 6, 2), ("cp", 4, 3),
@@ -443,7 +442,7 @@ def test_other_coarsening_orders_match_oracle(order, m, k):
     x = torch.zeros_like(b)
     info = ctx.solve(b, x, rtol=1e-10)
     assert info.iterations == it
-    assert rel(x.cpu().numpy(), ref) <= 1e-10
+    assert close(x.cpu().numpy(), ref) <= 1e-10
 
 
 def test_coarsening_without_c_is_rejected():
@@ -464,7 +463,7 @@ def test_iterative_coarse_solve_small_mesh():
     x = torch.empty(n0, dtype=torch.float64, device=DEV)
     ctx.coarse_solve(gpu(b0), x)
     torch.cuda.synchronize()
-    assert rel(x.cpu().numpy(), mg.coarse.solve(b0)) <= 1e-4
+    assert close(x.cpu().numpy(), mg.coarse.solve(b0)) <= 1e-4
     b = torch.empty(ctx.num_dofs(), dtype=torch.float64, device=DEV)
     ctx.rhs(b)
     xd = torch.zeros_like(b)
@@ -474,7 +473,7 @@ def test_iterative_coarse_solve_small_mesh():
         xc = torch.zeros_like(b)
         info = c.solve(b, xc, rtol=1e-10)
         assert info.converged and info.iterations <= dense.iterations + 2, (prec, info.iterations)
-        assert rel(xc.cpu().numpy(), xd.cpu().numpy()) <= 1e-6
+        assert close(xc.cpu().numpy(), xd.cpu().numpy()) <= 1e-6
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -503,4 +502,4 @@ def test_odd_mesh_with_large_coarse_level(precision):
         infos = ctx.solve_multi(B, X, rtol=1e-10, maxit=40)
         s.synchronize()
         assert all(i.converged for i in infos)
-        assert rel(X[1].cpu().numpy(), -0.5 * x.cpu().numpy()) <= 1e-6
+        assert close(X[1].cpu().numpy(), -0.5 * x.cpu().numpy()) <= 1e-6

@@ -52,3 +52,21 @@ def test_features_layout():
     assert np.all(F[1, n ** 3:n ** 3 + n * n] == cell0[:, :, n - 1].ravel())
     # boundary faces are zero
     assert np.all(F[0, n ** 3:n ** 3 + n * n] == 0)
+
+
+def test_bf16_gradients_stay_within_bf16_error_of_exact_ones():
+    """The BF16 mode rounds operands only: its gradients differ from the exact (FP64) ones by
+    a few BF16 ulps relative (2^-8 each), not by a dropped or transposed term."""
+    rng = np.random.default_rng(4)
+    sizes = [40, 32, 32, 20]
+    Ws, bs = mlp.init_params(sizes, 5)
+    for b in bs:
+        b[:] = rng.standard_normal(b.shape) * 0.1
+    X = rng.standard_normal((64, 40))
+    T = rng.standard_normal((64, 20))
+    L, gW, gb = mlp.loss_and_grads(X, T, Ws, bs)
+    Lq, gWq, gbq = mlp.loss_and_grads(X, T, Ws, bs, bf16=True)
+    assert abs(Lq - L) <= 2e-2 * L
+    for a, b in zip(gWq + gbq, gW + gb):
+        assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b)
+        assert np.linalg.norm(a - b) > 0          # the rounding is really applied
