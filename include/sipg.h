@@ -111,11 +111,19 @@ typedef struct {
                               this many unknowns (default 2197 = 13^3 nodes:
                               every mesh whose sizes halve down to <= 12
                               cells); larger coarse levels (odd or prime
-                              mesh sizes) get coarse_iters FP64 Jacobi-PCG
-                              iterations instead, an inexact coarse solve
-                              like the paper's AMG-CG (Section 3.2), which
-                              the flexible CG absorbs                        */
-  int coarse_iters;        /* default 50                                       */
+                              mesh sizes) are solved inexactly by the solver
+                              that coarse_solver names, which the flexible
+                              CG absorbs                                     */
+  int coarse_iters;        /* Jacobi-PCG iterations (coarse_solver 1), 50      */
+  int coarse_solver;       /* above coarse_dense_max (Section 3.3, "Coarse-
+                              grid solver"): 0 CG preconditioned by one
+                              smoothed-aggregation AMG V-cycle to
+                              coarse_rtol (default, the paper's coarse
+                              solver); 1 coarse_iters Jacobi-PCG iterations  */
+  double coarse_rtol;      /* relative residual of the AMG-CG, 1e-3            */
+  int coarse_maxit;        /* AMG-CG iterations launched per coarse solve
+                              (each one skips its work once coarse_rtol is
+                              met, so the solve stays capturable), 12       */
   void *stream;            /* cudaStream_t or NULL                             */
 } sipg_params;
 
@@ -192,9 +200,22 @@ sipg_status sipg_smooth(sipg_ctx *ctx, int level, const void *b_dev, void *x_dev
 sipg_status sipg_restrict(sipg_ctx *ctx, int level, const void *r_dev, void *rc_dev);
 sipg_status sipg_prolongate_add(sipg_ctx *ctx, int level, const void *xc_dev, void *x_dev);
 
-/* Coarse solve on level 0: x = A_0^-1 b in FP64 (dense direct solver that
- * replaces the paper's AMG, Section 3.3). */
+/* Coarse solve on level 0 in FP64 (Section 3.3, "Coarse-grid solver"): x =
+ * A_0^-1 b by the dense inverse up to coarse_dense_max unknowns, above it the
+ * inexact solve params.coarse_solver names (AMG-CG to coarse_rtol by default). */
 sipg_status sipg_coarse_solve(sipg_ctx *ctx, const double *b_dev, double *x_dev);
+
+/* What solves level 0: *kind = 0 dense inverse, 1 Jacobi-PCG, 2 AMG-CG; for
+ * AMG-CG *nlevels AMG levels with sizes[0..min(nlevels,10)-1] rows (sizes[0]
+ * = level 0's unknowns) and *last_iterations = CG iterations of the most
+ * recent coarse solve on the context's stream (synchronizes that stream).
+ * Any output pointer may be NULL. */
+sipg_status sipg_coarse_info(sipg_ctx *ctx, int *kind, int *nlevels, int sizes[10], int *last_iterations);
+
+/* One V-cycle of level 0's smoothed-aggregation AMG from x = 0 (Section 3.3):
+ * x = M_AMG^-1 b, FP64 device vectors of level 0's length.  EINVAL unless
+ * level 0 is solved by AMG-CG. */
+sipg_status sipg_coarse_amg_vcycle(sipg_ctx *ctx, const double *b_dev, double *x_dev);
 
 /* One V-cycle of Algorithm 2 with x = 0 on entry: z = M^-1 r.  r and z are
  * FP64 finest-level vectors; the cycle runs in params.precision. */
@@ -360,7 +381,8 @@ sipg_status sipg_fma_peak(int precision, void *stream, double *flops_per_s);
  * allocate once it runs.  Computes v = A u, the same FP64 operator as
  * sipg_operator_apply for affine cells (mesh->deform must be 0), with
  * penalty_factor as in sipg_params.  The caller passes the device vectors u
- * and v (length m0 m1 m2 (degree+1)^3, DG order, must not overlap); every
+ * and v (length m0 m1 m2 (degree+1)^3, DG order; overlapping ranges are
+ * rejected with SIPG_EINVAL); every
  * other buffer lives in one static device array of 64 MiB that each GPU
  * loading the library holds until the process exits.  Problems whose scratch
  * (3 (k+1)^3 + 12 (k+1)^2 + 1 doubles per cell, plus small tables) exceeds
@@ -372,7 +394,9 @@ sipg_status sipg_fma_peak(int precision, void *stream, double *flops_per_s);
  * results; calls ordered on one stream are safe.  Nothing in the array needs
  * to start at zero (every call rewrites what it reads).  Work is queued on
  * `stream` (cudaStream_t, NULL = legacy default stream); on failure
- * sipg_last_error(NULL) describes it. */
+ * sipg_last_error(NULL) describes it.  A CUDA error left pending by the
+ * caller's earlier work is cleared on entry (cudaGetLastError), so that it is
+ * not reported as this call's failure. */
 sipg_status sipg_operator_apply_noalloc(const sipg_mesh *mesh, int degree, double penalty_factor,
                                         const double *u_dev, double *v_dev, void *stream);
 

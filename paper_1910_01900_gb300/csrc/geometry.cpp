@@ -472,6 +472,62 @@ double l2_error_manufactured(const Mapping &map, int n, const double *x) {
   return std::sqrt(total);
 }
 
+namespace {
+
+// Q1 stiffness matrix of cell e with the 2-point Gauss rule and the cell's
+// mapping: K[i][j] = sum_q w_q |det J| grad N_i . grad N_j, local node i =
+// ix + 2 iy + 4 iz; gidx[i] = its node in the (m+1)^3 grid (x fastest).
+void q1_cell_matrix(const Mapping &map, const PointTable &tc, const Rules1D &r, int64_t e, double K[8][8],
+                    int gidx[8]) {
+  const MeshDesc &m = map.mesh;
+  const int grid[3] = {m.m[0] + 1, m.m[1] + 1, m.m[2] + 1};
+  double J[9 * 8];
+  int ijk[3];
+  map.cell_ijk(e, ijk);
+  map.eval(e, tc, nullptr, J);
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) K[i][j] = 0.0;
+  for (int qz = 0; qz < 2; ++qz)
+    for (int qy = 0; qy < 2; ++qy)
+      for (int qx = 0; qx < 2; ++qx) {
+        const int p = qx + 2 * (qy + 2 * qz);
+        const double *Jp = &J[p * 9];
+        const double det = det3(Jp);
+        double Ji[9];
+        inv3(Jp, det, Ji);
+        const double jxw = std::fabs(det) * r.wq[qx] * r.wq[qy] * r.wq[qz];
+        double gr[8][3];
+        for (int i = 0; i < 8; ++i) {
+          const int ix = i & 1, iy = (i >> 1) & 1, iz = i >> 2;
+          const double g0 = r.Sd[qx * 2 + ix] * r.S[qy * 2 + iy] * r.S[qz * 2 + iz];
+          const double g1 = r.S[qx * 2 + ix] * r.Sd[qy * 2 + iy] * r.S[qz * 2 + iz];
+          const double g2 = r.S[qx * 2 + ix] * r.S[qy * 2 + iy] * r.Sd[qz * 2 + iz];
+          for (int a = 0; a < 3; ++a) gr[i][a] = Ji[0 * 3 + a] * g0 + Ji[1 * 3 + a] * g1 + Ji[2 * 3 + a] * g2;
+        }
+        for (int i = 0; i < 8; ++i)
+          for (int j = 0; j < 8; ++j) K[i][j] += jxw * (gr[i][0] * gr[j][0] + gr[i][1] * gr[j][1] + gr[i][2] * gr[j][2]);
+      }
+  for (int i = 0; i < 8; ++i) {
+    const int ix = i & 1, iy = (i >> 1) & 1, iz = i >> 2;
+    gidx[i] = (ijk[0] + ix) + grid[0] * ((ijk[1] + iy) + grid[1] * (ijk[2] + iz));
+  }
+}
+
+// nodes of the (m+1)^3 grid on a Dirichlet side (strongly constrained)
+std::vector<char> q1_constrained(const MeshDesc &m, const int bc[6]) {
+  const int grid[3] = {m.m[0] + 1, m.m[1] + 1, m.m[2] + 1};
+  const int N = grid[0] * grid[1] * grid[2];
+  std::vector<char> c(N, 0);
+  for (int g = 0; g < N; ++g) {
+    const int gx = g % grid[0], gy = (g / grid[0]) % grid[1], gz = g / (grid[0] * grid[1]);
+    c[g] = (gx == 0 && bc[0] == 0) || (gx == grid[0] - 1 && bc[1] == 0) || (gy == 0 && bc[2] == 0) ||
+           (gy == grid[1] - 1 && bc[3] == 0) || (gz == 0 && bc[4] == 0) || (gz == grid[2] - 1 && bc[5] == 0);
+  }
+  return c;
+}
+
+}  // namespace
+
 void coarse_matrix(const Mapping &map, const int bc[6], std::vector<double> &A, int &N) {
   const MeshDesc &m = map.mesh;
   const int grid[3] = {m.m[0] + 1, m.m[1] + 1, m.m[2] + 1};
@@ -480,50 +536,83 @@ void coarse_matrix(const Mapping &map, const int bc[6], std::vector<double> &A, 
   const Rules1D &r = rules(2);
   const PointTable tc = map.table(cell_points(r));
   const int64_t E = (int64_t)m.m[0] * m.m[1] * m.m[2];
-  std::vector<double> J(9 * 8);
   for (int64_t e = 0; e < E; ++e) {
-    int ijk[3];
-    map.cell_ijk(e, ijk);
-    map.eval(e, tc, nullptr, J.data());
-    double K[8][8] = {};
-    for (int qz = 0; qz < 2; ++qz)
-      for (int qy = 0; qy < 2; ++qy)
-        for (int qx = 0; qx < 2; ++qx) {
-          const int p = qx + 2 * (qy + 2 * qz);
-          const double *Jp = &J[p * 9];
-          const double det = det3(Jp);
-          double Ji[9];
-          inv3(Jp, det, Ji);
-          const double jxw = std::fabs(det) * r.wq[qx] * r.wq[qy] * r.wq[qz];
-          double gr[8][3];
-          for (int i = 0; i < 8; ++i) {
-            const int ix = i & 1, iy = (i >> 1) & 1, iz = i >> 2;
-            const double g0 = r.Sd[qx * 2 + ix] * r.S[qy * 2 + iy] * r.S[qz * 2 + iz];
-            const double g1 = r.S[qx * 2 + ix] * r.Sd[qy * 2 + iy] * r.S[qz * 2 + iz];
-            const double g2 = r.S[qx * 2 + ix] * r.S[qy * 2 + iy] * r.Sd[qz * 2 + iz];
-            for (int a = 0; a < 3; ++a) gr[i][a] = Ji[0 * 3 + a] * g0 + Ji[1 * 3 + a] * g1 + Ji[2 * 3 + a] * g2;
-          }
-          for (int i = 0; i < 8; ++i)
-            for (int j = 0; j < 8; ++j) K[i][j] += jxw * (gr[i][0] * gr[j][0] + gr[i][1] * gr[j][1] + gr[i][2] * gr[j][2]);
-        }
+    double K[8][8];
     int gidx[8];
-    for (int i = 0; i < 8; ++i) {
-      const int ix = i & 1, iy = (i >> 1) & 1, iz = i >> 2;
-      gidx[i] = (ijk[0] + ix) + grid[0] * ((ijk[1] + iy) + grid[1] * (ijk[2] + iz));
-    }
+    q1_cell_matrix(map, tc, r, e, K, gidx);
     for (int i = 0; i < 8; ++i)
       for (int j = 0; j < 8; ++j) A[(size_t)gidx[i] * N + gidx[j]] += K[i][j];
   }
+  const std::vector<char> cons = q1_constrained(m, bc);
   for (int g = 0; g < N; ++g) {
-    const int gx = g % grid[0], gy = (g / grid[0]) % grid[1], gz = g / (grid[0] * grid[1]);
-    const bool c = (gx == 0 && bc[0] == 0) || (gx == grid[0] - 1 && bc[1] == 0) || (gy == 0 && bc[2] == 0) ||
-                   (gy == grid[1] - 1 && bc[3] == 0) || (gz == 0 && bc[4] == 0) || (gz == grid[2] - 1 && bc[5] == 0);
-    if (!c) continue;
+    if (!cons[g]) continue;
     for (int j = 0; j < N; ++j) {
       A[(size_t)g * N + j] = 0;
       A[(size_t)j * N + g] = 0;
     }
     A[(size_t)g * N + g] = 1.0;
+  }
+}
+
+void coarse_matrix_csr(const Mapping &map, const int bc[6], Csr &A) {
+  const MeshDesc &m = map.mesh;
+  const int grid[3] = {m.m[0] + 1, m.m[1] + 1, m.m[2] + 1};
+  const int N = grid[0] * grid[1] * grid[2];
+  const Rules1D &r = rules(2);
+  const PointTable tc = map.table(cell_points(r));
+  const int64_t E = (int64_t)m.m[0] * m.m[1] * m.m[2];
+  const std::vector<char> cons = q1_constrained(m, bc);
+  // the 27-point pattern of every node (neighbours within one grid step),
+  // columns ascending; values summed cell by cell in cell order
+  A.n = N;
+  A.ncols = N;
+  A.ptr.assign(N + 1, 0);
+  auto nb = [&](int g, int d) {   // neighbour offset d = (dx+1) + 3 (dy+1) + 9 (dz+1), -1 if outside
+    const int gx = g % grid[0], gy = (g / grid[0]) % grid[1], gz = g / (grid[0] * grid[1]);
+    const int x = gx + d % 3 - 1, y = gy + (d / 3) % 3 - 1, z = gz + d / 9 - 1;
+    if (x < 0 || y < 0 || z < 0 || x >= grid[0] || y >= grid[1] || z >= grid[2]) return -1;
+    return x + grid[0] * (y + grid[1] * z);
+  };
+  for (int g = 0; g < N; ++g) {
+    int cnt = 0;
+    if (cons[g]) cnt = 1;
+    else
+      for (int d = 0; d < 27; ++d) {
+        const int h = nb(g, d);
+        if (h >= 0 && (h == g || !cons[h])) ++cnt;
+      }
+    A.ptr[g + 1] = A.ptr[g] + cnt;
+  }
+  A.idx.assign(A.ptr[N], 0);
+  A.val.assign(A.ptr[N], 0.0);
+  for (int g = 0; g < N; ++g) {
+    int o = A.ptr[g];
+    if (cons[g]) {
+      A.idx[o] = g;
+      A.val[o] = 1.0;
+      continue;
+    }
+    for (int d = 0; d < 27; ++d) {   // d ascending = column ascending
+      const int h = nb(g, d);
+      if (h >= 0 && (h == g || !cons[h])) A.idx[o++] = h;
+    }
+  }
+  auto slot = [&](int row, int col) -> double * {
+    for (int o = A.ptr[row]; o < A.ptr[row + 1]; ++o)
+      if (A.idx[o] == col) return &A.val[o];
+    return nullptr;
+  };
+  for (int64_t e = 0; e < E; ++e) {
+    double K[8][8];
+    int gidx[8];
+    q1_cell_matrix(map, tc, r, e, K, gidx);
+    for (int i = 0; i < 8; ++i) {
+      if (cons[gidx[i]]) continue;
+      for (int j = 0; j < 8; ++j) {
+        if (cons[gidx[j]]) continue;
+        *slot(gidx[i], gidx[j]) += K[i][j];
+      }
+    }
   }
 }
 

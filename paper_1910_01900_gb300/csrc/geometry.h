@@ -43,6 +43,16 @@ void penalty(const Mapping &map, int n, double factor, std::vector<double> &tau)
 void manufactured_rhs(const Mapping &map, int n, const std::vector<double> &tau, std::vector<double> &b);
 double l2_error_manufactured(const Mapping &map, int n, const double *x_host);
 void coarse_matrix(const Mapping &map, const int bc[6], std::vector<double> &A, int &N);
+
+// Compressed sparse rows (columns ascending within a row), FP64.
+struct Csr {
+  int n = 0, ncols = 0;
+  std::vector<int> ptr, idx;
+  std::vector<double> val;
+};
+// The same FE_1 matrix as coarse_matrix in CSR: the 27-point pattern, constrained
+// rows identity and constrained columns left out.
+void coarse_matrix_csr(const Mapping &map, const int bc[6], Csr &A);
 bool cholesky_inverse(std::vector<double> &A, int N);
 double tridiag_max_eig(const std::vector<double> &diag, const std::vector<double> &off);
 uint64_t splitmix64(uint64_t x);

@@ -319,6 +319,16 @@ cudaError_t mlp_bf2f(const void *X, long n, float *Y, cudaStream_t s);
 // Kernel-launch accounting (every launch of the library increments it).
 void note_launch();
 unsigned long long launch_count();
+
+// Smoothed-aggregation AMG-CG coarse solver (amg.cu).
+struct Csr;
+struct AmgCoarse;
+AmgCoarse *amg_create(const Csr &A0, double rtol, int maxit, double cheb_lo, double cheb_hi, std::string *err);
+void amg_destroy(AmgCoarse *M);
+int amg_level_sizes(const AmgCoarse *M, int *sizes, int max);
+cudaError_t amg_vcycle(AmgCoarse *M, const double *b, double *x, cudaStream_t s);
+cudaError_t amg_solve(AmgCoarse *M, const double *b, double *x, cudaStream_t s);
+cudaError_t amg_last_iterations(AmgCoarse *M, int *iterations, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_dg_kernels();
 cudaError_t prepare_fe_kernels();

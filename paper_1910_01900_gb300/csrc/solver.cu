@@ -10,6 +10,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <stdexcept>
 #include <string>
 #include <tuple>
 
@@ -34,6 +35,7 @@ struct sipg_ctx {
   // iterations on it (p, q work vectors in both precisions)
   bool coarse_cg = false;
   double *cg_p = nullptr, *cg_q = nullptr;   // FP64 search and product vectors of the coarse CG
+  AmgCoarse *amg = nullptr;                  // coarse_solver 0: the AMG-CG instead of Jacobi-PCG
   double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fv = nullptr, *fx = nullptr, *fb = nullptr;
   double *scal = nullptr, *partials = nullptr;
   unsigned *counter = nullptr;
@@ -385,12 +387,16 @@ void coarse_cg_solve(sipg_ctx *c, const T *b_all, T *x_all) {
   c->nv = 1;   // one vector at a time (level-0 operator on single vectors)
   try {
     for (int v = 0; v < nv; ++v) {
+      auto fp64 = [&](const double *b, double *x) {
+        if (c->amg) CK(amg_solve(c->amg, b, x, c->stream));
+        else coarse_cg_fp64(c, b, x);
+      };
       if constexpr (std::is_same<T, double>::value) {
-        coarse_cg_fp64(c, b_all + v * n, x_all + v * n);
+        fp64(b_all + v * n, x_all + v * n);
       } else {
         double *bd = lvec<double>(c, 0, 0), *xd = lvec<double>(c, 0, 1);
         CK((launch_cast<double, T>(bd, b_all + v * n, n, c->stream)));
-        coarse_cg_fp64(c, bd, xd);
+        fp64(bd, xd);
         CK((launch_cast<T, double>(x_all + v * n, xd, n, c->stream)));
       }
     }
@@ -905,8 +911,20 @@ void setup(sipg_ctx *c) {
   if (c->coarse_cg) {
     const int64_t n0 = c->lv[0].ndofs;
     c->n0 = (int)n0;
-    c->cg_p = dalloc<double>(c, n0);
-    c->cg_q = dalloc<double>(c, n0);
+    if (P.coarse_solver == 0) {   // AMG-CG on the FE_1 matrix of the coarsest mesh
+      Csr A;
+      Mapping cmap(specs.back().md);
+      coarse_matrix_csr(cmap, M.bc, A);
+      std::string err;
+      c->amg = amg_create(A, P.coarse_rtol, P.coarse_maxit, P.cheb_lo, P.cheb_hi, &err);
+      if (!c->amg) {
+        if (err.find("cudaMalloc") != std::string::npos) throw std::runtime_error("AMG setup: " + err);
+        throw_inval("AMG setup: " + err);
+      }
+    } else {
+      c->cg_p = dalloc<double>(c, n0);
+      c->cg_q = dalloc<double>(c, n0);
+    }
   } else {
     std::vector<double> A;
     int N;
@@ -1403,6 +1421,9 @@ void sipg_default_params(sipg_params *p) {
   p->fe_assemble = 1;
   p->coarse_dense_max = 2197;
   p->coarse_iters = 50;
+  p->coarse_solver = 0;
+  p->coarse_rtol = 1e-3;
+  p->coarse_maxit = 12;
   p->stream = nullptr;
 }
 
@@ -1424,6 +1445,9 @@ sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_c
     if (P.precision != 0 && P.precision != 1) throw_inval("precision must be 0 or 1");
     if (P.cheb_degree < 1 || P.eig_iters < 1 || P.p_coarsen < 0 || P.p_coarsen > 2 || P.smoother != 0)
       throw_inval("unsupported smoother parameters");
+    if (P.coarse_solver < 0 || P.coarse_solver > 1 || !(P.coarse_rtol > 0 && P.coarse_rtol < 1) ||
+        P.coarse_maxit < 1 || P.coarse_maxit > 1000)
+      throw_inval("coarse_solver must be 0 or 1, coarse_rtol in (0, 1) and coarse_maxit in 1..1000");
     for (int s = 0; s < 6; ++s)
       if (M.bc[s] != 0 && M.bc[s] != 1) throw_inval("bc must be 0 (Dirichlet) or 1 (Neumann)");
     const double cells = (double)M.m[0] * M.m[1] * M.m[2];
@@ -1437,6 +1461,7 @@ sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_c
   });
   if (st != SIPG_OK) {
     if (!c->err.empty()) g_create_err = c->err;
+    amg_destroy(c->amg);
     for (void *p : c->allocs) cudaFree(p);
     return st;
   }
@@ -1452,6 +1477,7 @@ sipg_status sipg_destroy(sipg_ctx *c) {
   for (auto &g : c->vgraph_l)
     if (g) cudaGraphExecDestroy(g);
   if (c->mv.graph) cudaGraphExecDestroy(c->mv.graph);
+  amg_destroy(c->amg);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
   return SIPG_OK;
@@ -1588,6 +1614,31 @@ sipg_status sipg_coarse_solve(sipg_ctx *c, const double *b, double *x) {
   return guarded(c, [&]() -> sipg_status {
     if (c->coarse_cg) coarse_cg_solve<double>(c, b, x);
     else CK((launch_dense_gemv<double, double>(c->Ainv, b, x, c->n0, c->stream)));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_coarse_info(sipg_ctx *c, int *kind, int *nlevels, int sizes[10], int *last_iterations) {
+  if (!c || !c->solver) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    const int k = !c->coarse_cg ? 0 : (c->amg ? 2 : 1);
+    if (kind) *kind = k;
+    int nl = 0, sz[10] = {0};
+    if (c->amg) nl = amg_level_sizes(c->amg, sz, 10);
+    if (nlevels) *nlevels = nl;
+    if (sizes)
+      for (int i = 0; i < 10; ++i) sizes[i] = sz[i];
+    int it = 0;
+    if (c->amg && last_iterations) CK(amg_last_iterations(c->amg, &it, c->stream));
+    if (last_iterations) *last_iterations = it;
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_coarse_amg_vcycle(sipg_ctx *c, const double *b, double *x) {
+  if (!c || !b || !x || !c->solver || !c->amg) return SIPG_EINVAL;
+  return guarded(c, [&]() -> sipg_status {
+    CK(amg_vcycle(c->amg, b, x, c->stream));
     return SIPG_OK;
   });
 }

@@ -19,7 +19,7 @@ EXPORTS = [
     "sipg_default_params", "sipg_create", "sipg_destroy", "sipg_last_error", "sipg_num_levels",
     "sipg_num_dofs", "sipg_level_info", "sipg_lambda", "sipg_rhs", "sipg_operator_apply",
     "sipg_level_apply", "sipg_inverse_diagonal", "sipg_smooth", "sipg_restrict", "sipg_prolongate_add",
-    "sipg_coarse_solve", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
+    "sipg_coarse_solve", "sipg_coarse_info", "sipg_coarse_amg_vcycle", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
     "sipg_operator_apply_noalloc", "sipg_launch_count", "sipg_batch_create", "sipg_batch_destroy",
     "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_solve", "sipg_tile_shape", "sipg_set_tile_shape", "sipg_solve_multi",
     "sipg_operator_apply_multi",
@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("operator_only", ctypes.c_int), ("coarsening", ctypes.c_char * 8),
                 ("autotune", ctypes.c_int), ("fe_assemble", ctypes.c_int),
                 ("coarse_dense_max", ctypes.c_int), ("coarse_iters", ctypes.c_int),
+                ("coarse_solver", ctypes.c_int), ("coarse_rtol", ctypes.c_double), ("coarse_maxit", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -90,6 +91,9 @@ def lib():
         L.sipg_restrict.argtypes = [vp, i32, vp, vp]
         L.sipg_prolongate_add.argtypes = [vp, i32, vp, vp]
         L.sipg_coarse_solve.argtypes = [vp, vp, vp]
+        L.sipg_coarse_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i32)]
+        L.sipg_coarse_amg_vcycle.argtypes = [vp, vp, vp]
         L.sipg_vcycle.argtypes = [vp, vp, vp]
         L.sipg_solve.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveInfo)]
         L.sipg_solve_host.argtypes = [vp, vp, vp, dbl, i32, ctypes.POINTER(SolveInfo)]
@@ -157,7 +161,7 @@ def make_mesh(m, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(
 
 def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
                 operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None,
-                coarse_dense_max=None, coarse_iters=None):
+                coarse_dense_max=None, coarse_iters=None, coarse_solver=None, coarse_rtol=None, coarse_maxit=None):
     prm = Params()
     lib().sipg_default_params(ctypes.byref(prm))
     prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
@@ -172,6 +176,12 @@ def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iter
         prm.coarse_dense_max = int(coarse_dense_max)
     if coarse_iters is not None:
         prm.coarse_iters = int(coarse_iters)
+    if coarse_solver is not None:
+        prm.coarse_solver = int(coarse_solver)
+    if coarse_rtol is not None:
+        prm.coarse_rtol = float(coarse_rtol)
+    if coarse_maxit is not None:
+        prm.coarse_maxit = int(coarse_maxit)
     prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return prm
 
@@ -182,7 +192,8 @@ class Context:
     def __init__(self, m, degree, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,
                  precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
                  operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None,
-                 coarse_dense_max=None, coarse_iters=None, _handle=None):
+                 coarse_dense_max=None, coarse_iters=None, coarse_solver=None, coarse_rtol=None, coarse_maxit=None,
+                 _handle=None):
         L = lib()
         mesh, mm = make_mesh(m, deform, amp, lo, hi, bc)
         self.degree, self.precision = int(degree), int(precision)
@@ -194,7 +205,7 @@ class Context:
             return
         prm = make_params(degree, precision, penalty_factor, cheb_degree, eig_iters, lambda_override,
                           operator_only, stream, autotune, p_coarsen, coarsening, fe_assemble,
-                          coarse_dense_max, coarse_iters)
+                          coarse_dense_max, coarse_iters, coarse_solver, coarse_rtol, coarse_maxit)
         h = ctypes.c_void_p()
         st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
         if st != OK:
@@ -285,6 +296,19 @@ class Context:
         import torch
         n = self.num_dofs(0)
         self._check(lib().sipg_coarse_solve(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
+
+    def coarse_info(self):
+        """(kind, AMG level sizes, CG iterations of the last coarse solve); kind 0 dense
+        inverse, 1 Jacobi-PCG, 2 AMG-CG."""
+        kind, nl, it = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        sizes = (ctypes.c_int * 10)()
+        self._check(lib().sipg_coarse_info(self.h, ctypes.byref(kind), ctypes.byref(nl), sizes, ctypes.byref(it)))
+        return kind.value, [sizes[i] for i in range(min(nl.value, 10))], it.value
+
+    def coarse_amg_vcycle(self, b, x):
+        import torch
+        n = self.num_dofs(0)
+        self._check(lib().sipg_coarse_amg_vcycle(self.h, _ptr(b, torch.float64, n), _ptr(x, torch.float64, n)))
 
     def vcycle(self, r, z):
         import torch
@@ -428,6 +452,9 @@ def operator_apply_noalloc(m, degree, u, v, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.
     for s in range(6):
         mesh.bc[s] = int(bc[s])
     n = mm[0] * mm[1] * mm[2] * (int(degree) + 1) ** 3
+    pu, pv = u.data_ptr(), v.data_ptr()
+    if pu < pv + 8 * n and pv < pu + 8 * n:
+        raise ValueError("u and v overlap")
     st = lib().sipg_operator_apply_noalloc(ctypes.byref(mesh), int(degree), float(penalty_factor),
                                            _ptr(u, torch.float64, n), _ptr(v, torch.float64, n),
                                            ctypes.c_void_p(stream.cuda_stream if stream is not None else 0))

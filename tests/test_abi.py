@@ -54,7 +54,8 @@ def test_default_params_and_create_rejects_bad_input(lib):
     good, _ = native.make_mesh(4)
     for field, value, word in (("penalty_factor", -1.0, b"penalty"), ("penalty_factor", 0.0, b"penalty"),
                                ("precision", 2, b"precision"), ("cheb_degree", 0, b"smoother"),
-                               ("p_coarsen", 3, b"smoother")):
+                               ("p_coarsen", 3, b"smoother"), ("coarse_solver", 2, b"coarse_solver"),
+                               ("coarse_rtol", 0.0, b"coarse_rtol"), ("coarse_maxit", 0, b"coarse_maxit")):
         q = native.Params()
         lib.sipg_default_params(ctypes.byref(q))
         setattr(q, field, value)
@@ -106,6 +107,8 @@ def test_null_handles_and_bad_arguments_are_rejected_before_device_work(lib):
         "sipg_restrict": (N, 1, N, N),
         "sipg_prolongate_add": (N, 1, N, N),
         "sipg_coarse_solve": (N, N, N),
+        "sipg_coarse_info": (N, N, N, N, N),
+        "sipg_coarse_amg_vcycle": (N, N, N),
         "sipg_vcycle": (N, N, N),
         "sipg_solve": (N, N, N, 1e-10, 10, 0, N),
         "sipg_solve_host": (N, N, N, 1e-10, 10, N),

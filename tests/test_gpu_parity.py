@@ -452,10 +452,11 @@ def test_coarsening_without_c_is_rejected():
 
 
 def test_iterative_coarse_solve_small_mesh():
-    """A coarsest level above coarse_dense_max gets fixed Jacobi-PCG iterations instead of the
-    dense inverse: forced here on a small mesh, where 50 iterations nearly solve it exactly."""
+    """With coarse_solver = 1 a coarsest level above coarse_dense_max gets fixed Jacobi-PCG
+    iterations instead of the dense inverse: forced here on a small mesh, where 50 iterations
+    nearly solve it exactly."""
     m, k = 4, 3
-    ctx = _ctx(m, k, coarse_dense_max=0, coarse_iters=50)
+    ctx = _ctx(m, k, coarse_dense_max=0, coarse_iters=50, coarse_solver=1)
     mg = CPHMultigrid(Mesh(m), k)
     n0 = ctx.num_dofs(0)
     b0 = sipg_inputs.uniform(n0, 61)
@@ -469,23 +470,23 @@ def test_iterative_coarse_solve_small_mesh():
     xd = torch.zeros_like(b)
     dense = _ctx(m, k).solve(b, xd, rtol=1e-10)
     for prec in (0, 1):
-        c = _ctx(m, k, precision=prec, coarse_dense_max=0, coarse_iters=50)
+        c = _ctx(m, k, precision=prec, coarse_dense_max=0, coarse_iters=50, coarse_solver=1)
         xc = torch.zeros_like(b)
         info = c.solve(b, xc, rtol=1e-10)
         assert info.converged and info.iterations <= dense.iterations + 2, (prec, info.iterations)
         assert close(xc.cpu().numpy(), xd.cpu().numpy()) <= 1e-6
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_odd_mesh_with_large_coarse_level(precision):
+@pytest.mark.parametrize("precision,coarse_solver", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_odd_mesh_with_large_coarse_level(precision, coarse_solver):
     """m = 17 cannot be halved: the coarsest FE_1 level has 18^3 = 5832 unknowns, above the
-    dense limit, and is solved by Jacobi-PCG; the solve (on a stream, so the V-cycle with the
-    coarse iteration is captured as a CUDA graph) still reaches 1e-10 and so does a block of
-    right-hand sides."""
+    dense limit, and is solved by AMG-CG (coarse_solver 0) or Jacobi-PCG (1); the solve (on a
+    stream, so the V-cycle with the coarse iteration is captured as a CUDA graph) still
+    reaches 1e-10 and so does a block of right-hand sides."""
     s = torch.cuda.Stream()
     m, k = 17, 2
     with torch.cuda.stream(s):
-        ctx = _ctx(m, k, deform=1, precision=precision, stream=s)
+        ctx = _ctx(m, k, deform=1, precision=precision, stream=s, coarse_solver=coarse_solver)
         assert ctx.num_dofs(0) == 18 ** 3
         b = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_RHS)).to(DEV)
         x = torch.zeros_like(b)
