@@ -25,6 +25,9 @@ Layout (each function cites the passage of the paper it follows):
 * ``multigrid`` -- Chebyshev-Jacobi (Algorithm 3), eigenvalue estimate by 20 CG
                    iterations, V-cycle (Algorithm 2), CG (Algorithm 1) and
                    flexible CG, dense Cholesky coarse solve.
+* ``unstructured`` -- SIPG operator on general hexahedral meshes (connectivity
+                   from shared vertices, face points paired by physical
+                   position, per-face boundary conditions).
 * ``amg``       -- smoothed-aggregation AMG and the AMG-preconditioned CG
                    coarse-grid solver (Section 3.3, "Coarse-grid solver").
 * ``mlp``       -- CPU reference of the learned per-element smoother network.
