@@ -67,6 +67,29 @@ typedef struct {
   int bc[6];
 } sipg_mesh;
 
+/* Unstructured hexahedral mesh (Section 2; Section 5.3: the paper's nozzle
+ * and lung meshes are unstructured hexahedra with Dirichlet and Neumann
+ * boundary parts).  Host arrays, read during sipg_create_unstructured only:
+ * vertices [nverts][3]; cells [ncells][8] vertex ids, local vertex i + 2 j +
+ * 4 k at the reference corner (i, j, k) of [0,1]^3, the cell map being the
+ * trilinear interpolant of the 8 vertices; face_bc [ncells][6] for the local
+ * face f = 2 d + s (the face xi_d = s): 0 Dirichlet, 1 Neumann on boundary
+ * faces, ignored on interior faces (NULL: every boundary face Dirichlet).
+ * Two cells are neighbours through a face whose four vertex ids both hold;
+ * any relative orientation of the two cells is allowed.  deform = 1 applies
+ * x_i += amp * prod_j sin(pi (x_j-lo_j)/(hi_j-lo_j)) to the trilinear image,
+ * interpolated at degree 3 on the cell's GL points (as sipg_mesh). */
+typedef struct {
+  int nverts;
+  const double *vertices;
+  int ncells;
+  const int *cells;
+  const int *face_bc;
+  int deform;
+  double amp;
+  double lo[3], hi[3];
+} sipg_hex_mesh;
+
 /* Method parameters (Sections 2 and 3).  Defaults from sipg_default_params. */
 typedef struct {
   int degree;              /* k = p in the paper, 1..8                         */
@@ -153,6 +176,18 @@ void sipg_default_params(sipg_params *p);
  * <= 0, or no Dirichlet side when a solver will be used (the solver calls
  * then return EINVAL). */
 sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_ctx **out);
+
+/* Setup on an unstructured hexahedral mesh (see sipg_hex_mesh): the DG level
+ * only (params->operator_only must be 1; the multigrid hierarchy needs the
+ * box), for sipg_operator_apply, sipg_level_apply on level 0, sipg_time_apply
+ * and the tile-shape calls.  DoF order: cell-major in the given cell order,
+ * nodes of a cell lexicographic in its own reference coordinates (xi_0
+ * fastest).  The operator is the one of Section 2 with tau_e from each cell's
+ * own face areas and volume; on an interior face each side integrates with
+ * its own geometry at the shared points.  EINVAL for vertex ids out of range,
+ * a face shared by more than two cells, a singular cell map, or a face whose
+ * corners match no symmetry of the square. */
+sipg_status sipg_create_unstructured(const sipg_hex_mesh *mesh, const sipg_params *params, sipg_ctx **out);
 sipg_status sipg_destroy(sipg_ctx *ctx);
 const char *sipg_last_error(const sipg_ctx *ctx);
 

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsipg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["dg_f64.cu", "dg_f32.cu", "fe_kernels.cu", "vec_kernels.cu", "solver.cu", "batch.cu", "mlp.cu", "noalloc.cu", "amg.cu", "rules.cpp", "geometry.cpp"]
+SOURCES = ["dg_f64.cu", "dg_f32.cu", "fe_kernels.cu", "vec_kernels.cu", "solver.cu", "batch.cu", "mlp.cu", "noalloc.cu", "amg.cu", "rules.cpp", "geometry.cpp", "unstructured.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp"]
 

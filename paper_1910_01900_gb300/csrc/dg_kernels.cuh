@@ -31,6 +31,18 @@
 
 namespace sipg {
 
+// Face point of the neighbour that sits at the own face point l = q1 + N q2
+// (unstructured meshes): orientation code bit 0 swaps the two face
+// directions, bits 1 and 2 reverse the first and second of them.
+template <int N>
+__device__ __forceinline__ int face_perm(const int code, const int l) {
+  const int q1 = l % N, q2 = l / N;
+  int a = (code & 1) ? q2 : q1, b = (code & 1) ? q1 : q2;
+  if (code & 2) a = N - 1 - a;
+  if (code & 4) b = N - 1 - b;
+  return a + N * b;
+}
+
 template <typename T>
 struct VecPtrs {
   const T *u;
@@ -42,7 +54,7 @@ struct VecPtrs {
 // Evaluation pass for the cells cell0 .. cell0+ncta-1 of one problem, on a
 // thread block of blockDim.x >= ncta * N^2 threads with 4 ncta N^3 values of
 // shared memory at sm.  Shared by the per-problem and the batched kernels.
-template <typename T, int N, bool CURVED>
+template <typename T, int N, bool CURVED, bool UNSTR = false>
 __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T> &v, const int cell0, const int ncta, T *sm) {
   constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
   const int NT = blockDim.x;
@@ -82,7 +94,12 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
   }
   if (!act) return;
   const int cell = cell0 + cl;
-  const int ijk[3] = {cell % a.m[0], (cell / a.m[0]) % a.m[1], cell / (a.m[0] * a.m[1])};
+  int ijk[3] = {0, 0, 0};
+  if constexpr (!UNSTR) {
+    ijk[0] = cell % a.m[0];
+    ijk[1] = (cell / a.m[0]) % a.m[1];
+    ijk[2] = cell / (a.m[0] * a.m[1]);
+  }
   const Tables<T> &t = tab<T>();
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
@@ -123,12 +140,18 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
         gr0[b] = g0;
         gr1[b] = g1;
       }
-      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-      const size_t nfp = (size_t)a.m[t1] * a.m[t2];
-      const size_t f0 = (size_t)ijk[d] * nfp + ijk[t1] + (size_t)a.m[t1] * ijk[t2];
-      const size_t f1 = f0 + nfp;
-      const T *c0 = a.fc[d] + (f0 * 2 + 1) * 3 * N2 + l;   // this cell is the upper cell of plane i_d
-      const T *c1 = a.fc[d] + (f1 * 2 + 0) * 3 * N2 + l;   // and the lower cell of plane i_d+1
+      const T *c0, *c1;
+      if constexpr (UNSTR) {   // own side's J^-1 n of the faces xi_d = 0 and xi_d = 1
+        c0 = a.fc[0] + ((size_t)cell * 6 + 2 * d) * 3 * N2 + l;
+        c1 = c0 + 3 * N2;
+      } else {
+        const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        const size_t nfp = (size_t)a.m[t1] * a.m[t2];
+        const size_t f0 = (size_t)ijk[d] * nfp + ijk[t1] + (size_t)a.m[t1] * ijk[t2];
+        const size_t f1 = f0 + nfp;
+        c0 = a.fc[d] + (f0 * 2 + 1) * 3 * N2 + l;   // this cell is the upper cell of plane i_d
+        c1 = a.fc[d] + (f1 * 2 + 0) * 3 * N2 + l;   // and the lower cell of plane i_d+1
+      }
       q0 = c0[0] * gr0[0] + c0[N2] * gr0[1] + c0[2 * N2] * gr0[2];
       q1 = c1[0] * gr1[0] + c1[N2] * gr1[1] + c1[2 * N2] * gr1[2];
     }
@@ -141,7 +164,7 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
 }
 
 // Integration pass (same thread and shared-memory contract as the evaluation).
-template <typename T, int N, bool CURVED>
+template <typename T, int N, bool CURVED, bool UNSTR = false>
 __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecPtrs<T> &v, const int cell0, const int ncta,
                                                   T *sm) {
   constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
@@ -204,7 +227,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
 
   const int cell = cell0 + cl;
   int ijk[3] = {0, 0, 0};
-  if (act) {
+  if (act && !UNSTR) {
     ijk[0] = cell % a.m[0];
     ijk[1] = (cell / a.m[0]) % a.m[1];
     ijk[2] = cell / (a.m[0] * a.m[1]);
@@ -226,6 +249,32 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
       for (int s = 0; s < 2; ++s) {
         const T *tr = v.trace + ((size_t)cell * 6 + 2 * d + s) * 2 * N2 + l;
         const T uo = tr[0], qo = tr[N2];
+        if constexpr (UNSTR) {
+          // neighbour, its local face and the orientation of the shared face
+          const size_t cf = (size_t)cell * 6 + 2 * d + s;
+          const int2 nf = a.ufn[cf];
+          const T dA = a.fdA[0][cf * N2 + l];
+          const T *c = a.fc[0] + cf * 3 * N2 + l;
+          cvec[s][0] = c[0];
+          cvec[s][1] = c[N2];
+          cvec[s][2] = c[2 * N2];
+          if (nf.x >= 0) {
+            const T *tn = v.trace + ((size_t)nf.x * 6 + (nf.y & 7)) * 2 * N2 + face_perm<N>(nf.y >> 3, l);
+            const T un = tn[0], qn = tn[N2];
+            const T tau_f = max(tau_e, a.tau[nf.x]);
+            const T jump = uo - un;
+            const T hdA = T(0.5) * dA;
+            A[s] = fma(dA * tau_f, jump, -hdA * (qo - qn));
+            B[s] = -hdA * jump;
+          } else if (nf.x == -1) {
+            A[s] = fma(T(2) * dA * tau_e, uo, -dA * qo);
+            B[s] = -dA * uo;
+          } else {
+            A[s] = T(0);
+            B[s] = T(0);
+          }
+          continue;
+        }
         T dA;
         const size_t face = (size_t)(ijk[d] + s) * nfp + ftan;
         if constexpr (CURVED) {
@@ -382,6 +431,24 @@ __global__ void __launch_bounds__(kCellThreads, kMinCellBlocks<T>) dg_integrate_
   const int cell0 = grp * cb;
   dg_integrate_body<T, N, CURVED>(a, vec_ptrs(a, vec), cell0, min(cb, a.ncells - cell0),
                                   reinterpret_cast<T *>(smem_raw));
+}
+
+// Unstructured meshes: single-vector passes with general (curved) cell and
+// face geometry and the neighbour of every local face from a.ufn.
+template <typename T, int N>
+__global__ void __launch_bounds__(kCellThreads, kMinCellBlocks<T>) dg_eval_unstr_kernel(const DGArgs<T> a, const int cb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * cb;
+  dg_eval_body<T, N, true, true>(a, vec_ptrs(a, 0), cell0, min(cb, a.ncells - cell0), reinterpret_cast<T *>(smem_raw));
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kCellThreads, kMinCellBlocks<T>) dg_integrate_unstr_kernel(const DGArgs<T> a,
+                                                                                            const int cb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * cb;
+  dg_integrate_body<T, N, true, true>(a, vec_ptrs(a, 0), cell0, min(cb, a.ncells - cell0),
+                                      reinterpret_cast<T *>(smem_raw));
 }
 
 // Diagonal of the DG operator (setup, FP64), one thread per DoF: the cell

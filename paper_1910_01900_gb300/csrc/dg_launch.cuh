@@ -13,7 +13,13 @@ static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s, in
   const int64_t grid = (int64_t)((a.ncells + cb - 1) / cb) * a.nv;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  if (a.nv > 1) {
+  if (a.ufn) {   // unstructured mesh: general geometry, single vector
+    if (!CURVED || a.nv != 1) return cudaErrorInvalidValue;
+    if (integrate)
+      dg_integrate_unstr_kernel<T, N><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+    else
+      dg_eval_unstr_kernel<T, N><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
+  } else if (a.nv > 1) {
     if (integrate)
       dg_integrate_kernel<T, N, CURVED, true><<<(unsigned)grid, cb * N * N, smem, s>>>(a, cb);
     else
@@ -52,7 +58,9 @@ static cudaError_t prep_dg_n() {
         cudaFuncSetAttribute(dg_integrate_kernel<T, N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
         cudaFuncSetAttribute(dg_integrate_kernel<T, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
         cudaFuncSetAttribute(dg_eval_kernel<T, N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-        cudaFuncSetAttribute(dg_eval_kernel<T, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)})
+        cudaFuncSetAttribute(dg_eval_kernel<T, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_integrate_unstr_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        cudaFuncSetAttribute(dg_eval_unstr_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)})
     if (r != cudaSuccess) e = r;
   return e;
 }

@@ -1,6 +1,7 @@
 // Host-side setup of the discretization data; see geometry.cpp.
 #pragma once
 #include <array>
+#include <string>
 #include <vector>
 
 #include "sipg_internal.h"
@@ -54,6 +55,24 @@ struct Csr {
 // rows identity and constrained columns left out.
 void coarse_matrix_csr(const Mapping &map, const int bc[6], Csr &A);
 bool cholesky_inverse(std::vector<double> &A, int N);
+
+// Unstructured hexahedral mesh (host arrays; see unstructured.cpp).
+struct UMeshIn {
+  int nverts = 0, ncells = 0;
+  const double *vertices = nullptr;   // [nverts][3]
+  const int *cells = nullptr;         // [ncells][8], local vertex i + 2 j + 4 k at corner (i, j, k)
+  const int *face_bc = nullptr;       // [ncells][6] or null (all Dirichlet)
+  int deform = 0;
+  double amp = 0.1, lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+};
+// DG-level data of an unstructured mesh: metric [cell][6][n^3], fdA
+// [cell][6][n^2], fc [cell][6][3][n^2], tau [cell], ufn [cell][6][2] (see
+// DGArgs::ufn).
+struct UGeometry {
+  std::vector<double> metric, fdA, fc, tau;
+  std::vector<int> ufn;
+};
+bool build_unstructured(const UMeshIn &in, int n, double penalty_factor, UGeometry &g, std::string &err);
 double tridiag_max_eig(const std::vector<double> &diag, const std::vector<double> &off);
 uint64_t splitmix64(uint64_t x);
 double uniform_pm1(uint64_t seed, uint64_t i);

@@ -517,6 +517,34 @@ cudaError_t mlp_gemm(const void *A, long sam, long sak, const void *B, long sbk,
   return cudaGetLastError();
 }
 
+// Y[c][r] = X[r][c] for r < rows, c < cols (bf16), and Y[c][r] = 0 for rows
+// <= r < ldy: the K-contiguous (transposed, zero-padded) operands of the
+// weight-gradient products, whose contraction runs over the batch rows.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *X, int rows, int cols, long ldx, __nv_bfloat16 *Y,
+                                      int ldy) {
+  __shared__ __nv_bfloat16 t[32][34];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int j = ty; j < 32; j += 8) {
+    const int r = r0 + j, c = c0 + tx;
+    t[j][tx] = (r < rows && c < cols) ? X[(long)r * ldx + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int c = c0 + j, r = r0 + tx;
+    if (c < cols && r < ldy) Y[(long)c * ldy + r] = t[tx][j];
+  }
+}
+
+cudaError_t mlp_transpose_bf16(const void *X, int rows, int cols, long ldx, void *Y, int ldy, cudaStream_t s) {
+  if (rows < 0 || cols < 1 || ldy < rows) return cudaErrorInvalidValue;
+  if (ldy == 0) return cudaSuccess;
+  const dim3 grid((ldy + 31) / 32, (cols + 31) / 32), block(32, 8);
+  transpose_bf16_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, rows, cols, ldx, (__nv_bfloat16 *)Y, ldy);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t mlp_gemm_tc(const void *A, long lda, const void *Bt, long ldb, int M, int N, int K, const float *bias,
                         int relu, float *Cf, void *Cb, long ldc, cudaStream_t s) {
   if (M <= 0) return cudaSuccess;

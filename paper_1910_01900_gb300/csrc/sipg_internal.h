@@ -73,6 +73,12 @@ struct DGArgs {
   // (trace); dinv and the geometry are shared
   int nv = 1;
   int64_t vs = 0, gs = 0, ts = 0;
+  // unstructured meshes (null on the structured box): per cell and local face
+  // f = 2 d + s (the face xi_d = s), x = neighbour cell or -1 (Dirichlet) /
+  // -2 (Neumann), y = neighbour's local face | orientation code << 3; the
+  // face geometry is then per cell and local face: fdA[0] [cell][6][n^2],
+  // fc[0] [cell][6][3][n^2] (own side J^-1 n, n the outward unit normal)
+  const int2 *ufn = nullptr;
 };
 
 // Arguments of the FE cell pass and the node gather pass.
@@ -113,6 +119,7 @@ struct Level {
   void *fdA[2][3] = {{nullptr}}, *fc[2][3] = {{nullptr}};
   void *fwcart[2] = {nullptr, nullptr};
   void *tau[2] = {nullptr, nullptr};
+  int2 *ufn = nullptr;   // unstructured face neighbours (DGArgs::ufn)
   void *dinv[2] = {nullptr, nullptr};
   double lambda = 0;
   // cells per thread block of the cell kernels, [precision][DG evaluation,
@@ -295,6 +302,7 @@ cudaError_t mlp_transpose_weights(const void *Pb, long oW1, long oW2, long oW3, 
 // reads and clears the flag a tensor-core GEMM sets when its MMA completion
 // wait ran out (the CTA then wrote no output)
 cudaError_t mlp_tc_status(int *timed_out);
+cudaError_t mlp_transpose_bf16(const void *X, int rows, int cols, long ldx, void *Y, int ldy, cudaStream_t s);
 template <typename T>
 cudaError_t mlp_gather(const T *r, int n, const int m[3], const int *cells, int c0, int nc, void *X, int ldx,
                        float *scale, cudaStream_t s);

@@ -20,6 +20,7 @@
 using namespace sipg;
 
 struct sipg_ctx {
+  bool unstructured = false;   // built by sipg_create_unstructured (operator only)
   sipg_mesh mesh{};
   sipg_params prm{};
   MeshDesc md{};
@@ -59,6 +60,7 @@ struct sipg_ctx {
     // inference / training buffers for up to `rows` rows
     long rows = 0;
     void *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dH = nullptr;
+    void *TA = nullptr, *TB = nullptr;   // transposed operands of the weight gradients [feature][row]
     float *Y = nullptr, *dYf = nullptr, *scale = nullptr;
     double *loss = nullptr;
     double rho_cheb = 1.0;  // average rate of the Chebyshev cycle (judge of the learned one)
@@ -178,6 +180,7 @@ DGArgs<T> dg_args(sipg_ctx *c, const Level &L) {
   }
   a.fwcart = (const T *)L.fwcart[pi];
   a.tau = (const T *)L.tau[pi];
+  a.ufn = L.ufn;
   a.ncells = (int)L.ncells;
   for (int s = 0; s < 6; ++s) a.bc[s] = c->mesh.bc[s];
   // FP64 is bound by its arithmetic: store the gradient once; FP32 is bound
@@ -696,29 +699,49 @@ void autotune_level(sipg_ctx *c, int l, int pass) {
   g_tune[key] = best_cb;
 }
 
+// 1D tables into every translation unit's constant memory, shared-memory
+// opt-ins of the cell kernels (once per process and device use)
+void init_device_tables() {
+  static Tables<double> td;
+  static Tables<float> tf;
+  static std::once_flag built;
+  std::call_once(built, [] {
+    build_tables(td);
+    build_tables(tf);
+  });
+  upload_tables_dg<double>(td);
+  upload_tables_dg<float>(tf);
+  upload_tables_fe<double>(td);
+  upload_tables_fe<float>(tf);
+  upload_tables_batch<double>(td);
+  upload_tables_batch<float>(tf);
+  CK(cudaGetLastError());
+  CK(prepare_dg_kernels<double>());
+  CK(prepare_dg_kernels<float>());
+  CK(prepare_fe_kernels());
+}
+
+// Default tile widths of every level: the compiled default, lowered on
+// meshes that would give fewer blocks than SMs, so that every SM gets cells
+// (GB300 runs two FP64 FMAs per clock per SM: an FP64 pass over 64 cells in 4
+// blocks of 16 would use 4 of the 152 SMs).
+void default_tile_widths(sipg_ctx *c) {
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  for (Level &L : c->lv)
+    for (int pi = 0; pi < 2; ++pi)
+      for (int pass = 0; pass < 3; ++pass) {
+        int cb = dg_cells_per_block<double>(L.n);
+        if (nsm > 0 && (L.ncells + cb - 1) / cb < nsm) cb = (int)std::max<int64_t>(1, (L.ncells + nsm - 1) / nsm);
+        L.cb[pi][pass] = L.cb0[pi][pass] = cb;
+      }
+}
+
 void setup(sipg_ctx *c) {
   const sipg_mesh &M = c->mesh;
   const sipg_params &P = c->prm;
-  {
-    static Tables<double> td;
-    static Tables<float> tf;
-    static bool built = false;
-    if (!built) {
-      build_tables(td);
-      build_tables(tf);
-      built = true;
-    }
-    upload_tables_dg<double>(td);
-    upload_tables_dg<float>(tf);
-    upload_tables_fe<double>(td);
-    upload_tables_fe<float>(tf);
-    upload_tables_batch<double>(td);
-    upload_tables_batch<float>(tf);
-    CK(cudaGetLastError());
-    CK(prepare_dg_kernels<double>());
-    CK(prepare_dg_kernels<float>());
-    CK(prepare_fe_kernels());
-  }
+  init_device_tables();
   MeshDesc md{};
   for (int d = 0; d < 3; ++d) {
     md.m[d] = M.m[d];
@@ -826,23 +849,7 @@ void setup(sipg_ctx *c) {
   c->dg_grad[1] = dalloc<float>(c, dg_grad_len);
   c->dg_trace[1] = dalloc<float>(c, dg_trace_len);
   CK(cudaDeviceSynchronize());   // geometry uploads (legacy stream) complete before stream work
-  {
-    // Default tile widths: the compiled default, lowered on meshes that would
-    // give fewer blocks than SMs, so that every SM gets cells (GB300 runs two
-    // FP64 FMAs per clock per SM: an FP64 pass over 64 cells in 4 blocks of
-    // 16 would use 4 of the 152 SMs).
-    int dev = 0, nsm = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    for (Level &L : c->lv)
-      for (int pi = 0; pi < 2; ++pi)
-        for (int pass = 0; pass < 3; ++pass) {
-          int cb = dg_cells_per_block<double>(L.n);
-          if (nsm > 0 && (L.ncells + cb - 1) / cb < nsm)
-            cb = (int)std::max<int64_t>(1, (L.ncells + nsm - 1) / nsm);
-          L.cb[pi][pass] = L.cb0[pi][pass] = cb;
-        }
-  }
+  default_tile_widths(c);
   if (P.autotune) {
     // the finest DG level always; the other cell-kernel levels of the solver
     for (int l = c->solver ? 1 : c->L; l <= c->L; ++l) {
@@ -942,6 +949,56 @@ void setup(sipg_ctx *c) {
   c->fv = dalloc<double>(c, N);
   c->fx = dalloc<double>(c, N);
   c->fb = dalloc<double>(c, N);
+  CK(cudaDeviceSynchronize());
+}
+
+// Operator-only context on an unstructured hexahedral mesh: one DG level with
+// per-cell geometry and face neighbours (unstructured.cpp).
+void setup_unstructured(sipg_ctx *c, const UMeshIn &in) {
+  const sipg_params &P = c->prm;
+  init_device_tables();
+  UGeometry g;
+  std::string err;
+  if (!build_unstructured(in, P.degree + 1, P.penalty_factor, g, err)) throw_inval(err);
+  c->solver = false;
+  c->lv.assign(1, Level());
+  c->L = 0;
+  Level &L = c->lv[0];
+  L.kind = 0;
+  L.deg = P.degree;
+  L.n = P.degree + 1;
+  L.curved = true;
+  L.m[0] = in.ncells;
+  L.ncells = in.ncells;
+  const int64_t n3 = (int64_t)L.n * L.n * L.n;
+  L.ndofs = L.ncells * n3;
+  upload2(c, g.metric, L.metric);
+  void *o[2];
+  upload2(c, g.fdA, o);
+  L.fdA[0][0] = o[0];
+  L.fdA[1][0] = o[1];
+  upload2(c, g.fc, o);
+  L.fc[0][0] = o[0];
+  L.fc[1][0] = o[1];
+  upload2(c, g.tau, L.tau);
+  L.ufn = (int2 *)dalloc<int>(c, (int64_t)g.ufn.size());
+  CK(cudaMemcpy(L.ufn, g.ufn.data(), g.ufn.size() * sizeof(int), cudaMemcpyHostToDevice));
+  c->dg_grad[0] = dalloc<double>(c, L.ncells * 3 * n3);
+  c->dg_trace[0] = dalloc<double>(c, L.ncells * 12 * (int64_t)L.n * L.n);
+  c->dg_grad[1] = dalloc<float>(c, L.ncells * 3 * n3);
+  c->dg_trace[1] = dalloc<float>(c, L.ncells * 12 * (int64_t)L.n * L.n);
+  CK(cudaDeviceSynchronize());
+  default_tile_widths(c);
+  if (P.autotune) {
+    autotune_level<double>(c, 0, 0);
+    autotune_level<double>(c, 0, 1);
+    autotune_level<float>(c, 0, 0);
+    autotune_level<float>(c, 0, 1);
+  }
+  c->scal = dalloc<double>(c, 64);
+  c->partials = dalloc<double>(c, 2 * 304);
+  c->counter = dalloc<unsigned>(c, 4);
+  CK(cudaMemset(c->counter, 0, 4 * sizeof(unsigned)));
   CK(cudaDeviceSynchronize());
 }
 
@@ -1119,6 +1176,9 @@ void net_setup(sipg_ctx *c, long rows) {
     N.Y = dalloc<float>(c, rows * N.No);
     N.dYf = dalloc<float>(c, rows * N.No);
     N.scale = dalloc<float>(c, rows);
+    const long rp = (rows + 15) / 16 * 16;
+    N.TA = dalloc<uint16_t>(c, rp * std::max(N.Fp, N.H));
+    N.TB = dalloc<uint16_t>(c, rp * std::max(N.H, N.No));
     N.rows = rows;
   }
 }
@@ -1150,6 +1210,31 @@ void net_gradients(sipg_ctx *c, const void *X, long ldx, const float *T, long ld
   cudaStream_t s = c->stream;
   net_forward(c, X, ldx, B);
   CK(mlp_mse_grad(N.Y, T, ldt, B, N.n3, N.No, N.dY, N.dYf, N.loss, s));
+  if (N.No <= 256) {
+    // every product on the tcgen05 tensor cores: the back-propagated errors
+    // dY W3^T and dH W2^T read the stored weights as K-contiguous operands;
+    // the weight gradients contract over the batch rows, so both of their
+    // operands are transposed (zero-padded to a multiple of 16 rows) first
+    const int Bp = (B + 15) / 16 * 16;
+    CK(mlp_transpose_bf16(N.H2, B, N.H, N.H, N.TA, Bp, s));
+    CK(mlp_transpose_bf16(N.dY, B, N.No, N.No, N.TB, Bp, s));
+    CK(mlp_gemm_tc(N.TA, Bp, N.TB, Bp, N.H, N.No, Bp, nullptr, 0, N.G + N.oW3, nullptr, N.No, s));
+    CK(mlp_colsum(N.dYf, 0, B, N.No, N.No, N.G + N.ob3, s));
+    CK(mlp_gemm_tc(N.dY, N.No, bf(N.Pb, N.oW3), N.No, B, N.H, N.No, nullptr, 0, nullptr, N.dH, N.H, s));
+    CK(mlp_relu_mask(N.dH, N.H2, (long)B * N.H, s));
+    CK(mlp_transpose_bf16(N.H1, B, N.H, N.H, N.TA, Bp, s));
+    CK(mlp_transpose_bf16(N.dH, B, N.H, N.H, N.TB, Bp, s));
+    CK(mlp_gemm_tc(N.TA, Bp, N.TB, Bp, N.H, N.H, Bp, nullptr, 0, N.G + N.oW2, nullptr, N.H, s));
+    CK(mlp_colsum(N.dH, 1, B, N.H, N.H, N.G + N.ob2, s));
+    CK(mlp_gemm_tc(N.dH, N.H, bf(N.Pb, N.oW2), N.H, B, N.H, N.H, nullptr, 0, nullptr, N.H2, N.H, s));
+    CK(mlp_relu_mask(N.H2, N.H1, (long)B * N.H, s));
+    CK(mlp_transpose_bf16(X, B, N.Fp, ldx, N.TA, Bp, s));
+    CK(mlp_transpose_bf16(N.H2, B, N.H, N.H, N.TB, Bp, s));
+    CK(mlp_gemm_tc(N.TA, Bp, N.TB, Bp, N.Fp, N.H, Bp, nullptr, 0, N.G + N.oW1, nullptr, N.H, s));
+    CK(mlp_colsum(N.H2, 1, B, N.H, N.H, N.G + N.ob1, s));
+    return;
+  }
+  // outputs wider than one tensor-core tile (degree >= 6): mma.sync products
   CK(mlp_gemm(N.H2, 1, N.H, N.dY, N.No, 1, N.H, N.No, B, nullptr, 0, N.G + N.oW3, nullptr, N.No, 0, s));
   CK(mlp_colsum(N.dYf, 0, B, N.No, N.No, N.G + N.ob3, s));
   CK(mlp_gemm(N.dY, N.No, 1, bf(N.Pb, N.oW3), 1, N.No, B, N.H, N.No, nullptr, 0, nullptr, N.dH, N.H, 0, s));
@@ -1469,6 +1554,56 @@ sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_c
   return SIPG_OK;
 }
 
+sipg_status sipg_create_unstructured(const sipg_hex_mesh *mesh, const sipg_params *params, sipg_ctx **out) {
+  if (!out) return SIPG_EINVAL;
+  *out = nullptr;
+  auto c = std::make_unique<sipg_ctx>();
+  sipg_status st = guarded(nullptr, [&]() -> sipg_status {
+    if (!mesh || !params) throw_inval("null mesh or params");
+    const sipg_params &P = *params;
+    if (P.degree < 1 || P.degree > 8) throw_inval("degree must be in 1..8");
+    if (!(P.penalty_factor > 0)) throw_inval("penalty factor must be positive");
+    if (!P.operator_only) throw_inval("unstructured meshes: operator_only must be 1 (no multigrid hierarchy)");
+    if (mesh->ncells < 1 || mesh->nverts < 8 || !mesh->vertices || !mesh->cells)
+      throw_inval("unstructured mesh: need vertices (>= 8) and cells (>= 1)");
+    for (int64_t i = 0; i < (int64_t)mesh->ncells * 8; ++i)
+      if (mesh->cells[i] < 0 || mesh->cells[i] >= mesh->nverts) throw_inval("unstructured mesh: vertex id out of range");
+    if (mesh->face_bc)
+      for (int64_t i = 0; i < (int64_t)mesh->ncells * 6; ++i)
+        if (mesh->face_bc[i] != 0 && mesh->face_bc[i] != 1)
+          throw_inval("unstructured mesh: face_bc must be 0 (Dirichlet) or 1 (Neumann)");
+    if (mesh->deform && !(mesh->hi[0] > mesh->lo[0] && mesh->hi[1] > mesh->lo[1] && mesh->hi[2] > mesh->lo[2]))
+      throw_inval("unstructured mesh: deformation box extents must be positive");
+    if ((double)mesh->ncells * std::pow(P.degree + 1.0, 3) > 2.0e9) throw_inval("problem too large");
+    c->prm = P;
+    c->unstructured = true;
+    c->stream = (cudaStream_t)P.stream;
+    for (int s = 0; s < 6; ++s) c->mesh.bc[s] = 0;
+    UMeshIn in;
+    in.nverts = mesh->nverts;
+    in.ncells = mesh->ncells;
+    in.vertices = mesh->vertices;
+    in.cells = mesh->cells;
+    in.face_bc = mesh->face_bc;
+    in.deform = mesh->deform;
+    in.amp = mesh->amp;
+    for (int d = 0; d < 3; ++d) {
+      in.lo[d] = mesh->lo[d];
+      in.hi[d] = mesh->hi[d];
+    }
+    t_err = &c->err;
+    setup_unstructured(c.get(), in);
+    return SIPG_OK;
+  });
+  if (st != SIPG_OK) {
+    if (!c->err.empty()) g_create_err = c->err;
+    for (void *p : c->allocs) cudaFree(p);
+    return st;
+  }
+  *out = c.release();
+  return SIPG_OK;
+}
+
 sipg_status sipg_destroy(sipg_ctx *c) {
   if (!c) return SIPG_EINVAL;
   cudaStreamSynchronize(c->stream);
@@ -1514,7 +1649,7 @@ sipg_status sipg_lambda(const sipg_ctx *c, int level, double *lambda) {
 }
 
 sipg_status sipg_rhs(sipg_ctx *c, int kind, double *b) {
-  if (!c || !b || kind != 0) return SIPG_EINVAL;
+  if (!c || !b || kind != 0 || c->unstructured) return SIPG_EINVAL;
   return guarded(c, [&]() -> sipg_status {
     const Level &F = c->lv[c->L];
     Mapping map(c->md);
@@ -1527,7 +1662,7 @@ sipg_status sipg_rhs(sipg_ctx *c, int kind, double *b) {
 }
 
 sipg_status sipg_l2_error(sipg_ctx *c, int kind, const double *x, double *err) {
-  if (!c || !x || !err || kind != 0) return SIPG_EINVAL;
+  if (!c || !x || !err || kind != 0 || c->unstructured) return SIPG_EINVAL;
   return guarded(c, [&]() -> sipg_status {
     const Level &F = c->lv[c->L];
     std::vector<double> h(F.ndofs);

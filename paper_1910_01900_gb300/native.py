@@ -16,7 +16,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ECUDA", "ENOMEM", "ENOTCONV", "EBREAKDOWN", "ET
 
 # every entry point the header declares (checked by the CPU test suite)
 EXPORTS = [
-    "sipg_default_params", "sipg_create", "sipg_destroy", "sipg_last_error", "sipg_num_levels",
+    "sipg_default_params", "sipg_create", "sipg_create_unstructured", "sipg_destroy", "sipg_last_error", "sipg_num_levels",
     "sipg_num_dofs", "sipg_level_info", "sipg_lambda", "sipg_rhs", "sipg_operator_apply",
     "sipg_level_apply", "sipg_inverse_diagonal", "sipg_smooth", "sipg_restrict", "sipg_prolongate_add",
     "sipg_coarse_solve", "sipg_coarse_info", "sipg_coarse_amg_vcycle", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
@@ -41,6 +41,12 @@ class Mesh(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("deform", ctypes.c_int), ("amp", ctypes.c_double), ("mapping_degree", ctypes.c_int),
                 ("bc", ctypes.c_int * 6)]
+
+
+class HexMesh(ctypes.Structure):
+    _fields_ = [("nverts", ctypes.c_int), ("vertices", ctypes.c_void_p), ("ncells", ctypes.c_int),
+                ("cells", ctypes.c_void_p), ("face_bc", ctypes.c_void_p), ("deform", ctypes.c_int),
+                ("amp", ctypes.c_double), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
 
 
 class Params(ctypes.Structure):
@@ -76,6 +82,7 @@ def lib():
         L.sipg_default_params.argtypes = [ctypes.POINTER(Params)]
         L.sipg_default_params.restype = None
         L.sipg_create.argtypes = [ctypes.POINTER(Mesh), ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        L.sipg_create_unstructured.argtypes = [ctypes.POINTER(HexMesh), ctypes.POINTER(Params), ctypes.POINTER(vp)]
         L.sipg_destroy.argtypes = [vp]
         L.sipg_last_error.argtypes = [vp]
         L.sipg_last_error.restype = ctypes.c_char_p
@@ -433,6 +440,39 @@ class Context:
         self._check(lib().sipg_time_apply(self.h, precision, _ptr(u, u.dtype, n), _ptr(v, u.dtype, n),
                                           int(repeats), ctypes.byref(te), ctypes.byref(ti)))
         return te.value, ti.value
+
+
+def create_unstructured(vertices, cells, degree, face_bc=None, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0),
+                        hi=(1.0, 1.0, 1.0), penalty_factor=1.0, stream=None, autotune=False):
+    """Operator context on an unstructured hexahedral mesh (sipg_create_unstructured).
+
+    vertices (nv, 3) float64, cells (E, 8) int (local vertex i + 2j + 4k at reference
+    corner (i, j, k)), face_bc (E, 6) int or None.  Returns a Context whose apply,
+    level_apply(0, ...), time_apply and tile-shape calls work; the solver calls do not.
+    """
+    import numpy as np
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    C = np.ascontiguousarray(cells, dtype=np.int32)
+    if V.ndim != 2 or V.shape[1] != 3 or C.ndim != 2 or C.shape[1] != 8:
+        raise ValueError("vertices must be (nv, 3) and cells (E, 8)")
+    F = None if face_bc is None else np.ascontiguousarray(face_bc, dtype=np.int32)
+    if F is not None and F.shape != (C.shape[0], 6):
+        raise ValueError("face_bc must be (E, 6)")
+    hm = HexMesh()
+    hm.nverts, hm.vertices = V.shape[0], V.ctypes.data
+    hm.ncells, hm.cells = C.shape[0], C.ctypes.data
+    hm.face_bc = F.ctypes.data if F is not None else None
+    hm.deform, hm.amp = int(deform), float(amp)
+    for d in range(3):
+        hm.lo[d], hm.hi[d] = float(lo[d]), float(hi[d])
+    prm = make_params(degree, 0, penalty_factor, operator_only=True, stream=stream, autotune=autotune)
+    h = ctypes.c_void_p()
+    st = lib().sipg_create_unstructured(ctypes.byref(hm), ctypes.byref(prm), ctypes.byref(h))
+    if st != OK:
+        raise SipgError(st, lib().sipg_last_error(None).decode())
+    ctx = Context(1, degree, stream=stream, _handle=h)
+    ctx._owned = True
+    return ctx
 
 
 def operator_apply_noalloc(m, degree, u, v, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(0,) * 6,

@@ -92,6 +92,7 @@ def test_null_handles_and_bad_arguments_are_rejected_before_device_work(lib):
     N = None
     calls = {
         "sipg_create": (N, N, N),
+        "sipg_create_unstructured": (N, N, N),
         "sipg_destroy": (N,),
         "sipg_num_levels": (N, N),
         "sipg_num_dofs": (N, 0, N),
@@ -204,3 +205,37 @@ def test_noalloc_apply_rejects_before_device_work(lib):
     assert st == native.EINVAL and b"overlap" in lib.sipg_last_error(None)
     st = lib.sipg_operator_apply_noalloc(ctypes.byref(one), 1, 1.0, u, u, None)
     assert st == native.EINVAL and b"overlap" in lib.sipg_last_error(None)
+
+
+def test_unstructured_setup_rejects_bad_input_before_device_work(lib):
+    """sipg_create_unstructured checks its parameters and mesh arrays before any device work:
+    operator_only must be 1 (no multigrid hierarchy on unstructured meshes), vertex ids must be
+    in range and face conditions 0 or 1."""
+    import ctypes
+
+    import numpy as np
+
+    import sipg_inputs
+    from paper_1910_01900_gb300 import native
+    V, C, F, _, _ = sipg_inputs.scrambled_box((2, 1, 1), 3)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+
+    def attempt(cells, face_bc, operator_only):
+        Cc = np.ascontiguousarray(cells, dtype=np.int32)
+        Fc = np.ascontiguousarray(face_bc, dtype=np.int32)
+        hm = native.HexMesh()
+        hm.nverts, hm.vertices, hm.ncells, hm.cells = len(V), V.ctypes.data, len(Cc), Cc.ctypes.data
+        hm.face_bc = Fc.ctypes.data
+        p = native.Params()
+        lib.sipg_default_params(ctypes.byref(p))
+        p.degree, p.operator_only = 2, operator_only
+        h = ctypes.c_void_p()
+        return lib.sipg_create_unstructured(ctypes.byref(hm), ctypes.byref(p), ctypes.byref(h))
+
+    assert attempt(C, F, 0) == native.EINVAL and b"operator_only" in lib.sipg_last_error(None)
+    bad = C.copy()
+    bad[0, 5] = -1
+    assert attempt(bad, F, 1) == native.EINVAL and b"vertex id" in lib.sipg_last_error(None)
+    badf = F.copy()
+    badf[1, 2] = 3
+    assert attempt(C, badf, 1) == native.EINVAL and b"face_bc" in lib.sipg_last_error(None)
