@@ -44,10 +44,13 @@ METRIC = "SIPG apply DoF/s & %roofline; solve s/MDoF to 1e-10 rel. res. vs plain
 
 # DRAM bytes per launch of the solve's dominant kernel, per DoF: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of dg_integrate_kernel<double,5,
-# Cartesian> on this workload (one captured launch of a solve on the same mesh;
-# the capture command is printed in the line's traffic_source).
-DOMINANT_DRAM_BYTES_PER_DOF = None
-DOMINANT_NCU_COMMAND = None
+# Cartesian> on this workload's mesh (177,383,680 + 18,509,312 bytes over
+# 4,096,000 DoF in one captured launch; the command is in traffic_source).
+DOMINANT_DRAM_BYTES_PER_DOF = (177383680 + 18509312) / 4096000
+DOMINANT_NCU_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                        "--clock-control none -k regex:dg_integrate -s 4 -c 1 python -m "
+                        "paper_1910_01900_gb300.sweep --k 4 --curved 0 --precision 0 --m 32 --repeats 2 "
+                        "(dram bytes of one launch on the workload's 32^3 k=4 mesh)")
 
 # The oracle's bounded samples: the workload's degree and geometry on a cube
 # with fewer cells per axis (one oracle V-cycle on the full 32^3 mesh takes

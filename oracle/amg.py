@@ -32,11 +32,12 @@ matrix A_0 whose constrained rows are identity rows:
 6. Levels are added while the matrix has more than ``coarse_max`` rows and the
    aggregation still shrinks it; the last one is solved by dense Cholesky.
 
-The V-cycle smooths every level above the last with ``smooth_deg`` steps of
-Chebyshev-Jacobi (Algorithm 3, the same smoother as the geometric levels, on
-[0.06, 1.2] lambda with lambda from 10 Jacobi-PCG Lanczos steps) before and
-after the coarse correction (the paper uses one ILU(0) sweep, a sequential
-smoother; a polynomial smoother is the parallel counterpart).  The coarse-grid
+The V-cycle smooths every level above the last with ``smooth_deg`` = 3 steps
+of Chebyshev-Jacobi (Algorithm 3, the same smoother as the geometric levels,
+on [0.06, 1.2] lambda with lambda from 10 Jacobi-PCG Lanczos steps) before and
+after the coarse correction: the AMG V-cycle with Chebyshev(3,3) smoothing of
+the paper's lung runs (Table Lung); its other runs use one ILU(0) sweep, a
+sequential smoother whose data-parallel counterpart is the polynomial one.  The coarse-grid
 solve is CG (Algorithm 1) preconditioned by one such V-cycle from x = 0 until
 ||r|| <= rtol ||b||.
 """
@@ -134,7 +135,7 @@ class AMGLevel:
 class SmoothedAggregationAMG:
     """Hierarchy of steps 1-6 and its V-cycle; levels[0] is the finest."""
 
-    def __init__(self, A, coarse_max=500, smooth_deg=2, max_levels=10):
+    def __init__(self, A, coarse_max=500, smooth_deg=3, max_levels=10):
         self.smooth_deg = smooth_deg
         self.levels = [AMGLevel(A)]
         while self.levels[-1].n > coarse_max and len(self.levels) < max_levels:
@@ -192,7 +193,7 @@ def pcg(A, b, precond, rtol=1e-3, maxit=200):
 class AMGCoarseSolver:
     """The coarse-grid solve: CG preconditioned by one smoothed-aggregation V-cycle to rtol."""
 
-    def __init__(self, A, rtol=1e-3, coarse_max=500, smooth_deg=2):
+    def __init__(self, A, rtol=1e-3, coarse_max=500, smooth_deg=3):
         self.A = sp.csr_matrix(A)
         self.rtol = rtol
         self.amg = SmoothedAggregationAMG(self.A, coarse_max=coarse_max, smooth_deg=smooth_deg)

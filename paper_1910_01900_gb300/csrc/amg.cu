@@ -19,9 +19,11 @@
 //              aggregation stops shrinking it; the last level gets the
 //              explicit inverse of its Cholesky factor.
 //   smoother   Chebyshev-Jacobi (Algorithm 3, the geometric levels' smoother)
-//              of degree kSmoothDeg on [cheb_lo, cheb_hi] lambda, lambda from 10
-//              Jacobi-PCG Lanczos steps; the paper's ILU(0) is a sequential
-//              sweep, a polynomial smoother is its data-parallel counterpart.
+//              of degree 3 before and after the coarse correction, on
+//              [cheb_lo, cheb_hi] lambda, lambda from 10 Jacobi-PCG Lanczos
+//              steps: the AMG smoothing of the paper's lung runs (Table Lung);
+//              its other runs use an ILU(0) sweep, a sequential smoother whose
+//              data-parallel counterpart is the polynomial one.
 //
 // Solve (device, FP64): CG from x = 0 until ||r|| <= rtol ||b|| or maxit
 // iterations.  The iteration count is fixed at launch so that the whole solve
@@ -47,7 +49,7 @@ constexpr double kTie = 1e-12;
 constexpr int kCoarseMax = 500;
 constexpr int kMaxLevels = 10;
 constexpr int kEigIters = 10;
-constexpr int kSmoothDeg = 2;
+constexpr int kSmoothDeg = 3;
 constexpr int kRedBlocksA = 64, kRedThreadsA = 256;
 constexpr int kRowsPerBlock = 8;   // one warp per row
 
