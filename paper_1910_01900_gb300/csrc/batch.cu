@@ -169,7 +169,7 @@ cudaError_t batch_plan_build(BatchPlan<T> &P, const std::vector<DGArgs<T>> &args
     P.probs[p].n = ns[p];
     P.probs[p].active = 1;
     const int n = ns[p], cb = kBatchThreads / (n * n);
-    smem = std::max(smem, (size_t)cb * 4 * tile_values(n) * sizeof(T));
+    smem = std::max(smem, (size_t)cb * cell_values(n) * sizeof(T));
     for (int c = 0; c < args[p].ncells; c += cb) P.items.push_back({p, c, std::min(cb, args[p].ncells - c)});
   }
   // longest items first (cost ~ cells x n^4), then static striding over the grid

@@ -60,12 +60,12 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const bool act = cl < ncta;
-  T *su = sm + cl * 4 * TT;
+  T *su = sm + cl * Tile<N>::CS;
 
   const T *ug = v.u + (size_t)cell0 * N3;
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3;
-    sm[c * 4 * TT + Tile<N>::idx(i - c * N3)] = ug[i];
+    sm[c * Tile<N>::CS + Tile<N>::idx(i - c * N3)] = ug[i];
   }
   __syncthreads();
 #pragma unroll 1
@@ -89,7 +89,7 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
     T *gg = v.grad + (size_t)cell0 * 3 * N3;
     for (int i = tid; i < ncta * 3 * N3; i += NT) {
       const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
-      gg[i] = sm[c * 4 * TT + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)];
+      gg[i] = sm[c * Tile<N>::CS + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)];
     }
   }
   if (!act) return;
@@ -171,7 +171,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const bool act = cl < ncta;
-  T *st = sm + cl * 4 * TT;   // value accumulator, then the integrated tile
+  T *st = sm + cl * Tile<N>::CS;   // value accumulator, then the integrated tile
   T *sg = st + TT;            // three gradient components
 
   if (a.recompute) {
@@ -180,7 +180,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
     const T *ug = v.u + (size_t)cell0 * N3;
     for (int i = tid; i < ncta * N3; i += NT) {
       const int c = i / N3;
-      sm[c * 4 * TT + Tile<N>::idx(i - c * N3)] = ug[i];
+      sm[c * Tile<N>::CS + Tile<N>::idx(i - c * N3)] = ug[i];
     }
     __syncthreads();
 #pragma unroll 1
@@ -203,13 +203,13 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
     const T *gg = v.grad + (size_t)cell0 * 3 * N3;
     for (int i = tid; i < ncta * 3 * N3; i += NT) {
       const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
-      sm[c * 4 * TT + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)] = gg[i];
+      sm[c * Tile<N>::CS + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)] = gg[i];
     }
   }
   __syncthreads();
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3, p = i - c * N3, tp = Tile<N>::idx(p);
-    T *s = sm + c * 4 * TT + TT + tp;
+    T *s = sm + c * Tile<N>::CS + TT + tp;
     const T g0 = s[0], g1 = s[TT], g2 = s[2 * TT];
     if constexpr (!CURVED) {
       s[0] = g0 * a.wcart[p];
@@ -226,14 +226,18 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
   __syncthreads();
 
   const int cell = cell0 + cl;
-  int ijk[3] = {0, 0, 0};
+  // cell coordinates and strides as scalars picked by direction (indexing a
+  // small array with the runtime direction would put it in local memory)
+  int i0 = 0, i1 = 0, i2 = 0;
   if (act && !UNSTR) {
-    ijk[0] = cell % a.m[0];
-    ijk[1] = (cell / a.m[0]) % a.m[1];
-    ijk[2] = cell / (a.m[0] * a.m[1]);
+    i0 = cell % a.m[0];
+    i1 = (cell / a.m[0]) % a.m[1];
+    i2 = cell / (a.m[0] * a.m[1]);
   }
+  auto ijk = [&](int k) { return k == 0 ? i0 : (k == 1 ? i1 : i2); };
+  auto mdim = [&](int k) { return k == 0 ? a.m[0] : (k == 1 ? a.m[1] : a.m[2]); };
+  auto cstride = [&](int k) { return k == 0 ? 1 : (k == 1 ? a.m[0] : a.m[0] * a.m[1]); };
   const Tables<T> &t = tab<T>();
-  const int cstride[3] = {1, a.m[0], a.m[0] * a.m[1]};
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     if (act) {
@@ -243,8 +247,8 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
       T A[2], B[2];
       T cvec[2][3];
       const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-      const size_t nfp = (size_t)a.m[t1] * a.m[t2];
-      const size_t ftan = ijk[t1] + (size_t)a.m[t1] * ijk[t2];
+      const size_t nfp = (size_t)mdim(t1) * mdim(t2);
+      const size_t ftan = ijk(t1) + (size_t)mdim(t1) * ijk(t2);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const T *tr = v.trace + ((size_t)cell * 6 + 2 * d + s) * 2 * N2 + l;
@@ -276,7 +280,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
           continue;
         }
         T dA;
-        const size_t face = (size_t)(ijk[d] + s) * nfp + ftan;
+        const size_t face = (size_t)(ijk(d) + s) * nfp + ftan;
         if constexpr (CURVED) {
           dA = a.fdA[d][face * N2 + l];
           const T *c = a.fc[d] + (face * 2 + (s ? 0 : 1)) * 3 * N2 + l;
@@ -286,9 +290,9 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
         } else {
           dA = a.fwcart[d * N2 + l];
         }
-        const bool has_nb = s ? (ijk[d] < a.m[d] - 1) : (ijk[d] > 0);
+        const bool has_nb = s ? (ijk(d) < mdim(d) - 1) : (ijk(d) > 0);
         if (has_nb) {
-          const int nb = cell + (s ? cstride[d] : -cstride[d]);
+          const int nb = cell + (s ? cstride(d) : -cstride(d));
           const T *tn = v.trace + ((size_t)nb * 6 + 2 * d + (1 - s)) * 2 * N2 + l;
           const T un = tn[0], qn = tn[N2];
           const T tau_f = max(tau_e, a.tau[nb]);
@@ -305,28 +309,36 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
         }
       }
       // extrapolation transposed: every point of the line gets l_s(q) times the
-      // coefficient of each side (two FMAs per point, accumulated in place)
+      // value coefficient of each side.  The normal-derivative test term adds
+      // l_s(q) times its coefficient to the gradient component d along this
+      // same line, which the transposed derivative sweep D^T along d reads
+      // next; D^T applied to l_s is the fixed vector dl_s, so that term goes
+      // into the value tile here as dl_s(q) times the coefficient (one
+      // read-modify-write line less per direction, the same sum).
+      T bn0, bn1;
+      if constexpr (!CURVED) {
+        bn0 = -a.ih[d] * B[0];
+        bn1 = a.ih[d] * B[1];
+      } else {
+        bn0 = (d == 0 ? cvec[0][0] : (d == 1 ? cvec[0][1] : cvec[0][2])) * B[0];
+        bn1 = (d == 0 ? cvec[1][0] : (d == 1 ? cvec[1][1] : cvec[1][2])) * B[1];
+      }
       if (d == 0) {
 #pragma unroll
-        for (int q = 0; q < N; ++q) st[base + q * stride] = fma(t.l0[N][q], A[0], t.l1[N][q] * A[1]);
+        for (int q = 0; q < N; ++q)
+          st[base + q * stride] = fma(t.l0[N][q], A[0], fma(t.l1[N][q], A[1], fma(t.dl0[N][q], bn0, t.dl1[N][q] * bn1)));
       } else {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
           T *p = st + base + q * stride;
-          *p = fma(t.l0[N][q], A[0], fma(t.l1[N][q], A[1], *p));
+          *p = fma(t.l0[N][q], A[0], fma(t.l1[N][q], A[1], fma(t.dl0[N][q], bn0, fma(t.dl1[N][q], bn1, *p))));
         }
       }
-      if constexpr (!CURVED) {
-        const T b0 = -a.ih[d] * B[0], b1 = a.ih[d] * B[1];
-        T *g = sg + d * TT;
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-          T *p = g + base + q * stride;
-          *p = fma(t.l0[N][q], b0, fma(t.l1[N][q], b1, *p));
-        }
-      } else {
+      if constexpr (CURVED) {
+        // the tangential gradient components (J^-1 n has all three)
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) {
+          if (bb == d) continue;
           const T b0 = cvec[0][bb] * B[0], b1 = cvec[1][bb] * B[1];
           T *g = sg + bb * TT;
 #pragma unroll

@@ -9,7 +9,7 @@ template <typename T, int N, bool CURVED>
 static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s, int cb) {
   if (cb <= 0) cb = default_cb(N);
   if (cb > max_cb(N, sizeof(T))) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)cb * 4 * Tile<N>::T3 * sizeof(T);
+  const size_t smem = (size_t)cb * Tile<N>::CS * sizeof(T);
   const int64_t grid = (int64_t)((a.ncells + cb - 1) / cb) * a.nv;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
@@ -37,7 +37,7 @@ static cudaError_t run_dg(bool integrate, const DGArgs<T> &a, cudaStream_t s, in
 // Resident thread blocks per SM of one pass at cb cells per block.
 template <typename T, int N, bool CURVED>
 static cudaError_t occ_dg(bool integrate, int cb, int *blocks) {
-  const size_t smem = (size_t)cb * 4 * Tile<N>::T3 * sizeof(T);
+  const size_t smem = (size_t)cb * Tile<N>::CS * sizeof(T);
   return integrate ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_integrate_kernel<T, N, CURVED, false>,
                                                                    cb * N * N, smem)
                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dg_eval_kernel<T, N, CURVED, false>,
@@ -48,7 +48,7 @@ static cudaError_t occ_dg(bool integrate, int cb, int *blocks) {
 // device, before any launch or stream capture).
 template <typename T, int N>
 static cudaError_t prep_dg_n() {
-  const int smem = max_cb(N, sizeof(T)) * 4 * Tile<N>::T3 * (int)sizeof(T);
+  const int smem = max_cb(N, sizeof(T)) * Tile<N>::CS * (int)sizeof(T);
   cudaError_t e = cudaSuccess;
   for (cudaError_t r :
        {cudaFuncSetAttribute(dg_integrate_kernel<T, N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),

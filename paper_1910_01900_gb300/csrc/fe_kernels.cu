@@ -45,14 +45,14 @@ __global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a
   const int ncta = min(cb, a.ncells - cell0);
   const T *__restrict__ ug = MULTI ? a.u + vec * a.vs : a.u;
   const bool act = cl < ncta;
-  T *su = sm + cl * 4 * TT;
+  T *su = sm + cl * Tile<N>::CS;
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3, p = i - c * N3;
     const int cell = cell0 + c;
     const int g[3] = {(cell % a.m[0]) * a.deg + p % N, ((cell / a.m[0]) % a.m[1]) * a.deg + (p / N) % N,
                       (cell / (a.m[0] * a.m[1])) * a.deg + p / N2};
     const size_t gi = g[0] + (size_t)a.grid[0] * (g[1] + (size_t)a.grid[1] * g[2]);
-    sm[c * 4 * TT + Tile<N>::idx(p)] = node_constrained(g, a.grid, a.bc) ? T(0) : ug[gi];
+    sm[c * Tile<N>::CS + Tile<N>::idx(p)] = node_constrained(g, a.grid, a.bc) ? T(0) : ug[gi];
   }
   __syncthreads();
 #pragma unroll 1
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a
   __syncthreads();
   for (int i = tid; i < ncta * N3; i += NT) {
     const int c = i / N3, p = i - c * N3;
-    T *s = sm + c * 4 * TT + TT + Tile<N>::idx(p);
+    T *s = sm + c * Tile<N>::CS + TT + Tile<N>::idx(p);
     const T g0 = s[0], g1 = s[TT], g2 = s[2 * TT];
     if constexpr (!CURVED) {
       s[0] = g0 * a.wcart[p];
@@ -641,7 +641,7 @@ template <typename T, int N, bool CURVED>
 static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s, int cb) {
   if (cb <= 0) cb = default_cb(N);
   if (cb > max_cb(N, sizeof(T))) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)cb * 4 * Tile<N>::T3 * sizeof(T);
+  const size_t smem = (size_t)cb * Tile<N>::CS * sizeof(T);
   const int64_t grid = (int64_t)((a.ncells + cb - 1) / cb) * a.nv;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
@@ -656,12 +656,12 @@ static cudaError_t run_fe_cells(const FEArgs<T> &a, cudaStream_t s, int cb) {
 template <typename T, int N, bool CURVED>
 static cudaError_t occ_fe_cells(int cb, int *blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fe_cell_kernel<T, N, CURVED, false>, cb * N * N,
-                                                       (size_t)cb * 4 * Tile<N>::T3 * sizeof(T));
+                                                       (size_t)cb * Tile<N>::CS * sizeof(T));
 }
 
 template <typename T, int N>
 static cudaError_t prep_fe_n() {
-  const int smem = max_cb(N, sizeof(T)) * 4 * Tile<N>::T3 * (int)sizeof(T);
+  const int smem = max_cb(N, sizeof(T)) * Tile<N>::CS * (int)sizeof(T);
   cudaError_t e = cudaSuccess;
   for (cudaError_t r :
        {cudaFuncSetAttribute(fe_cell_kernel<T, N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),

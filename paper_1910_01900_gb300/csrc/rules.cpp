@@ -191,6 +191,13 @@ void build_tables(Tables<T> &t) {
     for (int q = 0; q < n; ++q) {
       t.l0[n][q] = (T)r.l0[q];
       t.l1[n][q] = (T)r.l1[q];
+      double d0 = 0, d1 = 0;   // (D^T l)[q] = sum_j D[j][q] l[j]
+      for (int j = 0; j < n; ++j) {
+        d0 += r.D[j * n + q] * r.l0[j];
+        d1 += r.D[j * n + q] * r.l1[j];
+      }
+      t.dl0[n][q] = (T)d0;
+      t.dl1[n][q] = (T)d1;
     }
   }
 }

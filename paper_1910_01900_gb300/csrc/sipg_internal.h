@@ -40,6 +40,10 @@ struct Tables {
   T SE[kMaxN + 1][25], SO[kMaxN + 1][20], StE[kMaxN + 1][25], StO[kMaxN + 1][20];
   T DE[kMaxN + 1][25], DO[kMaxN + 1][20], DtE[kMaxN + 1][25], DtO[kMaxN + 1][20];
   T l0[kMaxN + 1][kMaxN], l1[kMaxN + 1][kMaxN];
+  // D^T l0 and D^T l1: the transposed derivative sweep applied to the face
+  // extrapolation vectors (a face's normal-derivative test term enters the
+  // integrated tile through these directly)
+  T dl0[kMaxN + 1][kMaxN], dl1[kMaxN + 1][kMaxN];
 };
 template <typename T>
 void build_tables(Tables<T> &t);

@@ -97,15 +97,38 @@ __device__ __forceinline__ void apply_mat(const T (&x)[N], T (&y)[N]) {
   if constexpr (M == MDt) mv<T, N, -1>(t.Dt[N], t.DtE[N], t.DtO[N], x, y);
 }
 
-// Shared-memory tile of N^3 values, x fastest, with the x pitch padded to an
-// odd number for even N: a warp walking lines along x then hits distinct
-// banks (an even pitch like 8 puts 4-8 threads on one bank).
+// Shared-memory layout of one cell: four tile arrays of N^3 values (x
+// fastest, y step XP, z step ZP, array stride T3 = ZP N), cells CS values
+// apart.  One thread walks one line per sweep; a warp's 32 lanes cover lines
+// of up to two cells, and the lines of different directions start at
+// different banks.  The pitches below were chosen, per N, by counting the
+// shared-memory wavefronts (the most threads of a warp on one bank) of the
+// three sweep directions and of the point loops at the default and half the
+// default cells per block: 1.57 wavefronts per FP32 instruction at N = 6
+// against 1.85 with the x pitch alone padded (N + 1 for even N), 1.72 against
+// 3.7 at N = 2, 1.43 against 2.0 at N = 4.  The layout moves addresses only:
+// every value is computed by the same thread in the same order.
+__host__ __device__ constexpr int tile_xp(int n) { return n == 8 ? 9 : n; }
+__host__ __device__ constexpr int tile_zp(int n) {
+  return n == 2 ? 4 : n == 3 ? 9 : n == 4 ? 19 : n == 5 ? 25 : n == 6 ? 39 : n == 7 ? 52 : n == 8 ? 72 : 81;
+}
+// values of shared memory per cell (>= 4 tile arrays)
+__host__ __device__ constexpr int cell_values(int n) {
+  return n == 2 ? 36 : n == 3 ? 123 : n == 4 ? 304 : n == 5 ? 509 : n == 6 ? 964 : n == 7 ? 1457 : n == 8 ? 2304 : 2929;
+}
+
 template <int N>
 struct Tile {
-  static constexpr int XP = (N % 2 == 0) ? N + 1 : N;   // pitch of a y step
-  static constexpr int T3 = XP * N * N;                  // values per tile array
+  static constexpr int XP = tile_xp(N);                  // step of y
+  static constexpr int ZP = tile_zp(N);                  // step of z
+  static constexpr int T3 = ZP * N;                      // values per tile array
+  static constexpr int CS = cell_values(N);              // values per cell
+  static_assert(XP >= N && ZP >= XP * N && CS >= 4 * T3, "tile arrays overlap");
   // tile position of the node or point with linear index p = x + N (y + N z)
-  static __device__ __forceinline__ int idx(int p) { return XP == N ? p : p + p / N; }
+  static __device__ __forceinline__ int idx(int p) {
+    const int x = p % N, y = (p / N) % N, z = p / (N * N);
+    return x + XP * y + ZP * z;
+  }
 };
 
 // Offset and stride of line l (0 <= l < N^2) along direction d in a tile.
@@ -113,17 +136,17 @@ struct Tile {
 // order, so it equals the face-point index of the faces normal to d.
 template <int N>
 __device__ __forceinline__ void line_of(int d, int l, int &base, int &stride) {
-  constexpr int XP = Tile<N>::XP;
+  constexpr int XP = Tile<N>::XP, ZP = Tile<N>::ZP;
   const int a = l % N, b = l / N;
   if (d == 0) {
-    base = XP * (a + N * b);
+    base = XP * a + ZP * b;
     stride = 1;
   } else if (d == 1) {
-    base = a + XP * N * b;
+    base = a + ZP * b;
     stride = XP;
   } else {
     base = a + XP * b;
-    stride = XP * N;
+    stride = ZP;
   }
 }
 
@@ -149,19 +172,17 @@ __device__ __forceinline__ void sweep_inplace(T *s, int d, int l) {
   store_line<T, N>(s, base, stride, y);
 }
 
-// Values of one padded tile array for n points per direction (host and device).
-__host__ __device__ constexpr int tile_values(int n) { return ((n % 2 == 0) ? n + 1 : n) * n * n; }
 
 // Most threads per block of the cell kernels (their __launch_bounds__: at
 // most 85 registers a thread, which the sweeps need without spilling).
 constexpr int kCellThreads = 768;
 
-// Largest cells per thread block of the cell kernels (four tile arrays of
-// shared memory per cell): kCellThreads threads and 227 KB of shared memory.
+// Largest cells per thread block of the cell kernels (cell_values(n) values
+// of shared memory per cell): kCellThreads threads and 227 KB of shared memory.
 __host__ __device__ constexpr int max_cb(int n, int elem_bytes) {
-  return (kCellThreads / (n * n)) < (232448 / (4 * tile_values(n) * elem_bytes))
+  return (kCellThreads / (n * n)) < (232448 / (cell_values(n) * elem_bytes))
              ? (kCellThreads / (n * n))
-             : (232448 / (4 * tile_values(n) * elem_bytes));
+             : (232448 / (cell_values(n) * elem_bytes));
 }
 
 // Cells per thread block for a tile size n (about 256 threads, n^2 threads per cell).

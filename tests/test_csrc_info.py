@@ -29,12 +29,13 @@ def test_default_cells_per_block_matches_header():
 def test_max_cells_per_block_matches_header():
     src = _header()
     threads = int(re.search(r"constexpr int kCellThreads = (\d+);", src).group(1))
-    smem = int(re.search(r"\((\d+) / \(4 \* tile_values\(n\) \* elem_bytes\)\)", src).group(1))
-
-    def tile_values(n):
-        return ((n + 1) if n % 2 == 0 else n) * n * n
-
+    smem = int(re.search(r"\((\d+) / \(cell_values\(n\) \* elem_bytes\)\)", src).group(1))
+    body = re.search(r"constexpr int cell_values\(int n\)\s*\{\s*return (.*?);\s*\}", src, re.S).group(1)
+    pairs = dict((int(a), int(b)) for a, b in re.findall(r"n == (\d) \? (\d+)", body))
+    last = int(re.search(r":\s*(\d+)\s*$", body.strip()).group(1))
     for n in range(2, 10):
+        cv = pairs.get(n, last)
+        assert csrc_info.CELL_VALUES[n] == cv, n
         for eb in (4, 8):
-            want = min(threads // (n * n), smem // (4 * tile_values(n) * eb))
+            want = min(threads // (n * n), smem // (cv * eb))
             assert csrc_info.max_cells_per_block(n, eb) == want, (n, eb)
