@@ -326,6 +326,256 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const TcArgs g, const uint
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// The whole network in one kernel (hidden width 256, output width <= 256):
+// one CTA per 128-row tile runs the three layers back to back.  The tile's
+// hidden activations never leave the SM: each layer's FP32 accumulator sits
+// in tensor memory, the epilogue (bias, ReLU, BF16) writes it into a 64 KB
+// shared-memory tile in the K-major core-matrix layout that the next layer's
+// MMAs read as their A operand.  The weights (and the first layer's
+// features) are packed in global memory in that same layout, one contiguous
+// block per K chunk of 32 (mlp_pack_core), so that a pipeline stage is one
+// or two bulk copies (cp.async.bulk, the TMA engine) completed on the
+// stage's "full" mbarrier; one thread issues the copies and the MMAs and
+// commits each MMA batch to the stage's "empty" mbarrier, which the refill
+// of that stage waits on.  Every wait is bounded: a CTA that runs out
+// drains what it issued (bounded), writes nothing, frees its tensor memory
+// and sets the flag the host turns into SIPG_ETIMEOUT.  Optionally the
+// hidden activations also go to global memory (training keeps them for the
+// backward pass).
+constexpr int FZ_H = 256;
+constexpr int FZ_T = 256;                                  // threads: eight warps
+constexpr int FZ_KC = 32;                                  // K per chunk
+constexpr int FZ_S = 6;                                    // stages
+constexpr int FZ_P = 4;                                    // chunks in flight ahead of the MMAs
+constexpr int FZ_STAGE_A = TC_M * FZ_KC * 2;               // 8 KB of features
+constexpr int FZ_STAGE = FZ_STAGE_A + FZ_H * FZ_KC * 2;    // + 16 KB of weights
+constexpr int FZ_HTILE = TC_M * FZ_H * 2;                  // 64 KB hidden tile: 4 K-chunks of 64
+constexpr int FZ_SMEM = FZ_S * FZ_STAGE + FZ_HTILE;        // 208 KB: one CTA per SM
+
+// byte offset of the 16-byte piece (row r, K group g) in a core-matrix block
+// of kc columns (8-row x 16-byte core matrices, K groups adjacent at 128 B)
+__host__ __device__ __forceinline__ uint32_t fz_core_off(int r, int g, int kc) {
+  return (uint32_t)(((r >> 3) * (kc >> 3) + g) * 128 + (r & 7) * 16);
+}
+
+// dst = src [rows][K] (row stride ld) in blocks of rt rows x FZ_KC columns,
+// block (tile t, chunk j) at (t * nch + j) * rt * FZ_KC elements, inside a
+// block the core-matrix layout of fz_core_off; rows >= rows and columns >= K
+// are zero.  One thread per 16-byte piece.
+__global__ void pack_core_kernel(const __nv_bfloat16 *src, long ld, int rows, int K, int rt, int nch, int ntiles,
+                                 __nv_bfloat16 *dst) {
+  const long pieces = (long)ntiles * rt * nch * (FZ_KC / 8);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < pieces; i += (long)gridDim.x * blockDim.x) {
+    const int g = (int)(i % (FZ_KC / 8));
+    long rem = i / (FZ_KC / 8);
+    const int j = (int)(rem % nch);
+    rem /= nch;
+    const int rr = (int)(rem % rt), t = (int)(rem / rt);
+    const int row = t * rt + rr, k0 = j * FZ_KC + 8 * g;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (row < rows && k0 < K) v = *reinterpret_cast<const uint4 *>(src + (long)row * ld + k0);
+    unsigned char *blk = reinterpret_cast<unsigned char *>(dst + ((long)t * nch + j) * rt * FZ_KC);
+    *reinterpret_cast<uint4 *>(blk + fz_core_off(rr, g, FZ_KC)) = v;
+  }
+}
+
+struct FusedArgs {
+  const __nv_bfloat16 *Xc;  // features packed in 128-row tiles, nch1 chunks per tile
+  int M, nch1, No;
+  const __nv_bfloat16 *W1c, *W2c, *W3c;   // packed weights: 256 x (32 nch1), 256 x 256, No x 256
+  const float *b1, *b2, *b3;
+  float *Y;                 // [M][ldy] fp32 outputs (bias, no ReLU)
+  long ldy;
+  __nv_bfloat16 *H1, *H2;   // [M][256] hidden activations or null
+};
+
+__device__ __forceinline__ void fz_expect(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void fz_bulk(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(FZ_T) mlp_fused_tc_kernel(const FusedArgs g) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long full[FZ_S], empty[FZ_S];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ float sbias[3][FZ_H];
+  const uint32_t s0 = smem_u32(tc_smem);
+  const uint32_t sH = smem_u32(tc_smem + FZ_S * FZ_STAGE);
+  unsigned char *hptr = tc_smem + FZ_S * FZ_STAGE;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_M;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < FZ_S; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail = 0;
+  }
+  for (int j = tid; j < 3 * FZ_H; j += FZ_T) {   // the biases, read by every epilogue
+    const int l = j / FZ_H, col = j - l * FZ_H;
+    const float *bsrc = l == 0 ? g.b1 : (l == 1 ? g.b2 : g.b3);
+    sbias[l][col] = (l < 2 || col < g.No) ? bsrc[col] : 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  // chunk c (numbered across the layers) uses stage c % FZ_S; its copies
+  // complete phase c / FZ_S of full[stage], its MMAs that of empty[stage]
+  auto wait_full = [&](int c) { return tc_wait(smem_u32(&full[c % FZ_S]), (uint32_t)((c / FZ_S) & 1)); };
+  auto wait_empty = [&](int c) { return tc_wait(smem_u32(&empty[c % FZ_S]), (uint32_t)((c / FZ_S) & 1)); };
+  int cbase = 0, produced = -1, issued = -1;
+  for (int layer = 0; layer < 3; ++layer) {
+    const int N = layer == 2 ? g.No : FZ_H;
+    const int nch = layer == 0 ? g.nch1 : FZ_H / FZ_KC;
+    const __nv_bfloat16 *Wc = layer == 0 ? g.W1c : (layer == 1 ? g.W2c : g.W3c);
+    const float *bias = sbias[layer];
+    if (tid == 0 && !fail) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                             ((uint32_t)(TC_M >> 4) << 24);
+      auto produce = [&](int i) {   // chunk i of this layer (stage (cbase + i) % FZ_S)
+        const int c = cbase + i, b = c % FZ_S;
+        const uint32_t a0 = s0 + (uint32_t)b * FZ_STAGE, b0 = a0 + FZ_STAGE_A;
+        const uint32_t bytes_b = (uint32_t)N * FZ_KC * 2;
+        fz_expect(smem_u32(&full[b]), bytes_b + (layer == 0 ? FZ_STAGE_A : 0u));
+        if (layer == 0) fz_bulk(a0, g.Xc + ((long)blockIdx.x * g.nch1 + i) * TC_M * FZ_KC, FZ_STAGE_A, smem_u32(&full[b]));
+        fz_bulk(b0, Wc + (long)i * N * FZ_KC, bytes_b, smem_u32(&full[b]));
+        produced = c;
+      };
+      // the stages of this layer's first chunks were last read by batches
+      // before cbase, all complete (the previous layer waited for cbase - 1)
+      for (int i = 0; i < FZ_P && i < nch; ++i) produce(i);
+      for (int i = 0; i < nch; ++i) {
+        const int c = cbase + i, b = c % FZ_S;
+        if (!wait_full(c)) {
+          fail = 1;
+          break;
+        }
+        const uint32_t a0 = s0 + (uint32_t)b * FZ_STAGE, b0 = a0 + FZ_STAGE_A;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int kk = 0; kk < FZ_KC; kk += 16) {
+          uint64_t ad;
+          if (layer == 0) {
+            ad = tc_desc(a0 + (kk >> 3) * 128, 128, (FZ_KC / 8) * 128);
+          } else {   // the hidden tile, K-chunks of 64 columns
+            const int k = i * FZ_KC + kk;
+            ad = tc_desc(sH + (uint32_t)(k / TC_KC) * (TC_M * TC_KC * 2) + ((k % TC_KC) >> 3) * 128, 128,
+                         (TC_KC / 8) * 128);
+          }
+          const uint64_t bd = tc_desc(b0 + (kk >> 3) * 128, 128, (FZ_KC / 8) * 128);
+          const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&empty[b]))
+                     : "memory");
+        issued = c;
+        if (i + FZ_P < nch) {
+          const int prev = c + FZ_P - FZ_S;   // the batch that last read the stage of chunk i + FZ_P
+          if (prev >= 0 && !wait_empty(prev)) {
+            fail = 1;
+            break;
+          }
+          produce(i + FZ_P);
+        }
+      }
+    }
+    __syncthreads();
+    // the layer's MMAs complete in issue order: its last batch covers them all
+    int ok = !fail;
+    if (ok) ok = __syncthreads_and(tc_wait(smem_u32(&empty[(cbase + nch - 1) % FZ_S]),
+                                           (uint32_t)(((cbase + nch - 1) / FZ_S) & 1)) ? 1 : 0);
+    if (!ok) {
+      if (tid == 0) {
+        fail = 1;
+        // bounded drains: the copies and MMAs this CTA issued must land before it exits
+        for (int c = (produced - FZ_S + 1 > 0 ? produced - FZ_S + 1 : 0); c <= produced; ++c) (void)wait_full(c);
+        if (issued >= 0) (void)wait_empty(issued);
+      }
+      __syncthreads();
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // warps w and w + 4 read the same 32 accumulator lanes (rows), the even
+    // and the odd 32-column groups, one tensor-memory load of 32 columns each
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane, gm = m0 + r;
+    for (int c32 = half * 32; c32 < N; c32 += 64) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c32;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int h16 = 0; h16 < 2; ++h16) {
+        const int c0 = c32 + 16 * h16;
+        if (c0 >= N) break;
+        float x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          x[j] = __uint_as_float(v[16 * h16 + j]) + bias[c0 + j];
+          if (layer < 2) x[j] = fmaxf(x[j], 0.f);
+        }
+        if (layer < 2) {
+          uint32_t w[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) w[q] = pack2(__float2bfloat16(x[2 * q]), __float2bfloat16(x[2 * q + 1]));
+          // the next layer's A operand: K chunk c0 / 64, 16-byte groups (c0 % 64) / 8 and + 1
+          const int ch = c0 / TC_KC, gq = (c0 % TC_KC) / 8;
+          unsigned char *hb = hptr + (size_t)ch * (TC_M * TC_KC * 2);
+          *reinterpret_cast<uint4 *>(hb + tc_core_off(r, gq)) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4 *>(hb + tc_core_off(r, gq + 1)) = make_uint4(w[4], w[5], w[6], w[7]);
+          __nv_bfloat16 *Hg = layer == 0 ? g.H1 : g.H2;
+          if (Hg && gm < g.M) {
+            uint4 *dst = reinterpret_cast<uint4 *>(Hg + (long)gm * FZ_H + c0);
+            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          }
+        } else if (gm < g.M) {
+          float4 *dst = reinterpret_cast<float4 *>(g.Y + (long)gm * g.ldy + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        }
+      }
+    }
+    // the hidden tile (generic-proxy stores) is read next by the tensor core,
+    // and the accumulator columns just read are overwritten by its MMAs
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    cbase += nch;
+  }
+  if (fail && tid == 0) atomicExch(&g_tc_timeout, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+}
+
 // Weights transposed for the forward GEMM: Wt[n][k] = W[k][n] for the three
 // layers (W1 [Fp][H], W2 [H][H], W3 [H][No] in the parameter vector).
 __global__ void transpose_weights_kernel(const __nv_bfloat16 *Pb, long oW1, long oW2, long oW3, int Fp, int H,
@@ -541,6 +791,48 @@ cudaError_t mlp_transpose_bf16(const void *X, int rows, int cols, long ldx, void
   if (ldy == 0) return cudaSuccess;
   const dim3 grid((ldy + 31) / 32, (cols + 31) / 32), block(32, 8);
   transpose_bf16_kernel<<<grid, block, 0, s>>>((const __nv_bfloat16 *)X, rows, cols, ldx, (__nv_bfloat16 *)Y, ldy);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Pack a [rows][K] bf16 matrix (row stride ld) into blocks of rt rows x 32
+// columns in the tensor cores' core-matrix layout (see pack_core_kernel).
+cudaError_t mlp_pack_core(const void *src, long ld, int rows, int K, int rt, void *dst, cudaStream_t s) {
+  if (rows < 0 || K < 1 || rt < 8 || rt % 8 || ld % 8 || ((uintptr_t)src & 15) || ((uintptr_t)dst & 15))
+    return cudaErrorInvalidValue;
+  const int nch = (K + FZ_KC - 1) / FZ_KC, ntiles = (rows + rt - 1) / rt;
+  const long pieces = (long)ntiles * rt * nch * (FZ_KC / 8);
+  if (pieces == 0) return cudaSuccess;
+  const int grid = (int)std::min<long>((pieces + 255) / 256, 152L * 16);
+  pack_core_kernel<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)src, ld, rows, K, rt, nch, ntiles,
+                                        (__nv_bfloat16 *)dst);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// The three layers in one launch (see mlp_fused_tc_kernel): Xc the features
+// packed in 128-row tiles of ceil(Fp / 32) chunks, Wc the packed weights
+// [256][32 ceil(Fp / 32)], [256][256], [No][256] at oC1, oC2, oC3.
+cudaError_t mlp_forward_fused(const void *Xc, int M, int Fp, int No, const void *Wc, long oC1, long oC2, long oC3,
+                              const float *b1, const float *b2, const float *b3, float *Y, long ldy, void *H1,
+                              void *H2, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  if (Fp < 16 || No < 16 || No > 256 || No % 16 || ldy % 4 || ((uintptr_t)Xc & 15) || ((uintptr_t)Y & 15) ||
+      ((uintptr_t)H1 & 15) || ((uintptr_t)H2 & 15) || (oC1 % 8) || (oC2 % 8) || (oC3 % 8) || ((uintptr_t)Wc & 15))
+    return cudaErrorInvalidValue;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    e = cudaFuncSetAttribute(mlp_fused_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FZ_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const __nv_bfloat16 *P = (const __nv_bfloat16 *)Wc;
+  FusedArgs g{(const __nv_bfloat16 *)Xc, M, (Fp + FZ_KC - 1) / FZ_KC, No, P + oC1, P + oC2, P + oC3, b1, b2, b3,
+              Y, ldy, (__nv_bfloat16 *)H1, (__nv_bfloat16 *)H2};
+  mlp_fused_tc_kernel<<<(M + TC_M - 1) / TC_M, FZ_T, FZ_SMEM, s>>>(g);
   note_launch();
   return cudaGetLastError();
 }

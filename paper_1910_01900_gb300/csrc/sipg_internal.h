@@ -307,6 +307,10 @@ cudaError_t mlp_transpose_weights(const void *Pb, long oW1, long oW2, long oW3, 
 // wait ran out (the CTA then wrote no output)
 cudaError_t mlp_tc_status(int *timed_out);
 cudaError_t mlp_transpose_bf16(const void *X, int rows, int cols, long ldx, void *Y, int ldy, cudaStream_t s);
+cudaError_t mlp_pack_core(const void *src, long ld, int rows, int K, int rt, void *dst, cudaStream_t s);
+cudaError_t mlp_forward_fused(const void *Xc, int M, int Fp, int No, const void *Wc, long oC1, long oC2, long oC3,
+                              const float *b1, const float *b2, const float *b3, float *Y, long ldy, void *H1,
+                              void *H2, cudaStream_t s);
 template <typename T>
 cudaError_t mlp_gather(const T *r, int n, const int m[3], const int *cells, int c0, int nc, void *X, int ldx,
                        float *scale, cudaStream_t s);

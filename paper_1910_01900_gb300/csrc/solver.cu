@@ -57,6 +57,11 @@ struct sipg_ctx {
     void *Pb = nullptr;    // bf16 copy of P
     void *Pt = nullptr;    // bf16 weights transposed (K contiguous) for the tensor-core forward pass
     long oT1 = 0, oT2 = 0, oT3 = 0;
+    // packed operands of the fused forward (hidden width 256, outputs <= 256):
+    // weights in K chunks of 32 at oC1..oC3, features of up to `rows` rows
+    void *Wc = nullptr, *Xc = nullptr;
+    long oC1 = 0, oC2 = 0, oC3 = 0;
+    int Fc = 0;   // first layer's K rounded up to whole chunks
     // inference / training buffers for up to `rows` rows
     long rows = 0;
     void *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dH = nullptr;
@@ -1120,9 +1125,17 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
 // for the Chebyshev smoother on the finest level.  Not in the paper.
 
 // the transposed BF16 weights follow every change of the BF16 weights
+inline const void *bf(const void *base, long off) { return (const uint16_t *)base + off; }
+inline void *bfm(void *base, long off) { return (uint16_t *)base + off; }
+
 void net_weights_updated(sipg_ctx *c) {
   auto &N = c->net;
   CK(mlp_transpose_weights(N.Pb, N.oW1, N.oW2, N.oW3, N.Fp, N.H, N.No, N.Pt, c->stream));
+  if (N.Wc) {   // the fused forward's operand blocks (core-matrix layout, K chunks of 32)
+    CK(mlp_pack_core(bf(N.Pt, N.oT1), N.Fp, N.H, N.Fp, N.H, bfm(N.Wc, N.oC1), c->stream));
+    CK(mlp_pack_core(bf(N.Pt, N.oT2), N.H, N.H, N.H, N.H, bfm(N.Wc, N.oC2), c->stream));
+    CK(mlp_pack_core(bf(N.Pt, N.oT3), N.H, N.No, N.H, N.No, bfm(N.Wc, N.oC3), c->stream));
+  }
 }
 
 void net_setup(sipg_ctx *c, long rows) {
@@ -1149,6 +1162,13 @@ void net_setup(sipg_ctx *c, long rows) {
     N.oT2 = (long)N.H * N.Fp;
     N.oT3 = N.oT2 + (long)N.H * N.H;
     N.Pt = dalloc<uint16_t>(c, N.oT3 + (long)N.No * N.H);
+    if (N.H == 256 && N.No <= 256) {
+      N.Fc = (N.Fp + 31) / 32 * 32;
+      N.oC1 = 0;
+      N.oC2 = (long)N.H * N.Fc;
+      N.oC3 = N.oC2 + (long)N.H * N.H;
+      N.Wc = dalloc<uint16_t>(c, N.oC3 + (long)N.No * N.H);
+    }
     N.loss = dalloc<double>(c, 2);
     // He-uniform initial weights from the counter-based generator, zero biases
     std::vector<float> h(N.np, 0.f);
@@ -1169,6 +1189,7 @@ void net_setup(sipg_ctx *c, long rows) {
   }
   if (rows > N.rows) {
     N.X = dalloc<uint16_t>(c, rows * N.Fp);
+    if (N.Wc) N.Xc = dalloc<uint16_t>(c, (rows + 127) / 128 * 128 * (long)N.Fc);
     N.H1 = dalloc<uint16_t>(c, rows * N.H);
     N.H2 = dalloc<uint16_t>(c, rows * N.H);
     N.dH = dalloc<uint16_t>(c, rows * N.H);
@@ -1183,13 +1204,18 @@ void net_setup(sipg_ctx *c, long rows) {
   }
 }
 
-inline const void *bf(const void *base, long off) { return (const uint16_t *)base + off; }
-inline void *bfm(void *base, long off) { return (uint16_t *)base + off; }
 
-// Y = net(X) for B rows of X (bf16, row stride ldx elements)
-void net_forward(sipg_ctx *c, const void *X, long ldx, int B) {
+// Y = net(X) for B rows of X (bf16, row stride ldx elements); the hidden
+// activations land in N.H1 and N.H2 when keep_hidden (the backward pass reads them)
+void net_forward(sipg_ctx *c, const void *X, long ldx, int B, bool keep_hidden = true) {
   auto &N = c->net;
   cudaStream_t s = c->stream;
+  if (N.Wc) {   // the whole network in one tensor-core kernel, operands packed for bulk copies
+    CK(mlp_pack_core(X, ldx, B, N.Fp, 128, N.Xc, s));
+    CK(mlp_forward_fused(N.Xc, B, N.Fp, N.No, N.Wc, N.oC1, N.oC2, N.oC3, N.P + N.ob1, N.P + N.ob2, N.P + N.ob3, N.Y,
+                         N.No, keep_hidden ? N.H1 : nullptr, keep_hidden ? N.H2 : nullptr, s));
+    return;
+  }
   // one layer: out = act(in W + b) with W [K][Nout]; on the tcgen05 tensor
   // cores (transposed weights) when the output width fits one MMA tile
   auto layer = [&](const void *in, long ld, long oW, long oT, int K, int Nout, const float *bias, int relu,
@@ -1264,7 +1290,7 @@ void learned_smooth(sipg_ctx *c, const T *b, T *x, int steps, bool zero_start) {
       r = (const T *)F.vr[pi];
     }
     CK(mlp_gather<T>(r, F.n, F.m, nullptr, 0, E, N.X, N.Fp, N.scale, c->stream));
-    net_forward(c, N.X, N.Fp, E);
+    net_forward(c, N.X, N.Fp, E, false);
     CK(mlp_correct<T>(x, N.n3, 0, E, N.Y, N.No, N.scale, N.cscale, c->stream));
   }
 }
