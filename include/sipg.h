@@ -399,8 +399,10 @@ sipg_status sipg_tile_shape(const sipg_ctx *ctx, int level, int precision, int p
  * the context's captured V-cycle graphs (they hold the old launch shapes). */
 sipg_status sipg_set_tile_shape(sipg_ctx *ctx, int level, int precision, int pass, int cells_per_block);
 
-/* Number of kernel launches (and CUDA-graph launches) the library has issued
- * in this process so far, all contexts together.  For launch accounting. */
+/* Number of kernels the library has launched in this process so far, all
+ * contexts together: a kernel inside a replayed CUDA graph counts once per
+ * replay (in a graph of conditional nodes, only the bodies that ran); a
+ * capture itself launches nothing.  For launch accounting. */
 sipg_status sipg_launch_count(unsigned long long *n);
 
 /* Peak arithmetic probe: runs an independent-FMA loop on every SM for the

@@ -234,6 +234,10 @@ cudaError_t launch_fcg_update_xr(double *x, double *r, const double *p, const do
                                  const double *sc, double *partials, unsigned *counter, double *out,
                                  cudaStream_t s);
 cudaError_t launch_fcg_update_p(double *p, const double *z, const double *sc, int64_t n, cudaStream_t s);
+// device-gated flexible-CG steps (vec_kernels.cu): prm points to {double rtol; int maxit, fixed;}
+cudaError_t launch_fcg_check(const double *sc, double *hist, int *st, const void *prm, cudaGraphConditionalHandle next,
+                             cudaStream_t s);
+cudaError_t launch_fcg_cond(const int *st, cudaGraphConditionalHandle h, cudaStream_t s);
 // coarse-level Jacobi-PCG with device-resident FP64 scalars (cycle precision T)
 template <typename T>
 cudaError_t launch_cg_dot(const T *x, const T *y, int64_t n, double *partials, unsigned *counter, double *out,

@@ -98,6 +98,19 @@ struct sipg_ctx {
   int use_learned = 0;       // current cycle uses the learned smoother
   cudaGraphExec_t vgraph_l[2] = {nullptr, nullptr};   // graphs of the learned cycle
   int vcalls_l[2] = {0, 0};
+  // Flexible-CG iterations gated on the device (non-default stream,
+  // Chebyshev cycle, one vector): a chunk of kFcgChunk iterations captured
+  // once per cycle precision, each iteration two conditional (IF) nodes whose
+  // conditions the iteration's own kernels set; the host reads the state once
+  // per chunk.  State and parameters in device memory (see fcg_check_kernel).
+  cudaGraphExec_t fcg_graph[2] = {nullptr, nullptr};
+  int *fcg_state = nullptr;
+  double *fcg_hist = nullptr;
+  void *fcg_prm = nullptr;
+  cudaStream_t cap_stream = nullptr;   // captures the bodies of the conditional nodes
+  std::vector<long long> fcg_kA, fcg_kB;   // kernels in each iteration's two bodies
+  // kernels captured into each graph, added to the launch count per replay
+  std::map<cudaGraphExec_t, long long> graph_kernels;
 };
 
 static std::string g_create_err;
@@ -105,7 +118,19 @@ static std::string g_create_err;
 void sipg::set_global_error(const std::string &msg) { g_create_err = msg; }
 
 static std::atomic<unsigned long long> g_launches{0};
-void sipg::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// while a stream capture runs on this thread, launches go to its tally
+static thread_local long long *t_capture_tally = nullptr;
+void sipg::note_launch() {
+  if (t_capture_tally) ++*t_capture_tally;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+static void note_kernels(long long k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+// counts the launches noted in its scope into *tally instead of the total
+struct CaptureTally {
+  long long *prev;
+  explicit CaptureTally(long long *tally) : prev(t_capture_tally) { t_capture_tally = tally; }
+  ~CaptureTally() { t_capture_tally = prev; }
+};
 unsigned long long sipg::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
@@ -479,7 +504,7 @@ void precondition(sipg_ctx *c) {
   }
   if (*gslot) {
     CK(cudaGraphLaunch(*gslot, c->stream));
-    note_launch();
+    note_kernels(c->graph_kernels[*gslot]);
     return;
   }
   if (c->stream == nullptr || (*calls)++ < 1) {
@@ -487,8 +512,10 @@ void precondition(sipg_ctx *c) {
     return;
   }
   cudaGraph_t g = nullptr;
+  long long kernels = 0;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   try {
+    CaptureTally tally(&kernels);
     vcycle_body(c, r, z);
   } catch (...) {
     cudaStreamEndCapture(c->stream, &g);
@@ -501,8 +528,9 @@ void precondition(sipg_ctx *c) {
   cudaGraphDestroy(g);
   CK(e);
   *gslot = ex;
+  c->graph_kernels[ex] = kernels;
   CK(cudaGraphLaunch(ex, c->stream));
-  note_launch();
+  note_kernels(kernels);
 }
 
 double read_scalar(sipg_ctx *c, int slot) {
@@ -1007,6 +1035,104 @@ void setup_unstructured(sipg_ctx *c, const UMeshIn &in) {
   CK(cudaDeviceSynchronize());
 }
 
+constexpr int kFcgChunk = 8;
+
+// a conditional IF node on the capture of s, depending on what s captured so
+// far; returns its body graph (to be filled by a capture on another stream)
+cudaGraph_t add_if_node(cudaStream_t s, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphNodeParams prm{};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = cudaGraphCondTypeIf;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &prm));
+  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return prm.conditional.phGraph_out[0];
+}
+
+// Capture kFcgChunk flexible-CG iterations on the context's vectors (x in
+// fx, r in fr, p in fp, v = A p in fv, z in fz).  Iteration i: IF A_i {
+// v = A p; p.Ap; x, r update; check (sets B_i) } then IF B_i { z = M^-1 r
+// (the V-cycle); r.z, z.Ap; p = z + beta p; set A_{i+1} }.  Conditions
+// default to 0 at every launch, so after the check that ends the solve
+// nothing more runs.
+void build_fcg_chunk(sipg_ctx *c) {
+  const int pi = c->prm.precision;
+  if (c->fcg_graph[pi]) return;
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  const int64_t N = c->lv[c->L].ndofs;
+  cudaStream_t s = c->stream, s2 = c->cap_stream;
+  cudaGraph_t G = nullptr;
+  CK(cudaGraphCreate(&G, 0));
+  std::vector<cudaGraphConditionalHandle> hA(kFcgChunk), hB(kFcgChunk);
+  for (int i = 0; i < kFcgChunk; ++i) {
+    CK(cudaGraphConditionalHandleCreate(&hA[i], G, 0, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&hB[i], G, 0, cudaGraphCondAssignDefault));
+  }
+  c->fcg_kA.assign(kFcgChunk, 0);
+  c->fcg_kB.assign(kFcgChunk, 0);
+  long long k0 = 0;
+  auto body = [&](cudaGraph_t b, long long *tally, auto &&fn) {
+    c->stream = s2;
+    CK(cudaStreamBeginCaptureToGraph(s2, b, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      CaptureTally t(tally);
+      fn();
+    } catch (...) {
+      cudaGraph_t o;
+      cudaStreamEndCapture(s2, &o);
+      c->stream = s;
+      throw;
+    }
+    cudaGraph_t o;
+    CK(cudaStreamEndCapture(s2, &o));
+    c->stream = s;
+  };
+  CK(cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  try {
+    {
+      CaptureTally t(&k0);
+      CK(launch_fcg_cond(c->fcg_state, hA[0], s));
+    }
+    for (int i = 0; i < kFcgChunk; ++i) {
+      body(add_if_node(s, hA[i]), &c->fcg_kA[i], [&]() {
+        apply_level<double>(c, c->L, c->fp, c->fv, 0);
+        CK(launch_dot2(c->fp, c->fv, nullptr, nullptr, N, c->partials, c->counter, c->scal + 2, s2));
+        CK(launch_fcg_update_xr(c->fx, c->fr, c->fp, c->fv, N, c->scal, c->partials, c->counter, c->scal + 3, s2));
+        CK(launch_fcg_check(c->scal, c->fcg_hist, c->fcg_state, c->fcg_prm, hB[i], s2));
+      });
+      body(add_if_node(s, hB[i]), &c->fcg_kB[i], [&]() {
+        vcycle_body(c, c->fr, c->fz);
+        CK(launch_dot2(c->fr, c->fz, c->fz, c->fv, N, c->partials, c->counter, c->scal + 0, s2));
+        CK(launch_fcg_update_p(c->fp, c->fz, c->scal, N, s2));
+        if (i + 1 < kFcgChunk) CK(launch_fcg_cond(c->fcg_state, hA[i + 1], s2));
+      });
+    }
+  } catch (...) {
+    c->stream = s;
+    cudaGraph_t o;
+    cudaStreamEndCapture(s, &o);
+    if (o) cudaGraphDestroy(o);
+    cudaGraphDestroy(G);
+    throw;
+  }
+  cudaGraph_t out = nullptr;
+  CK(cudaStreamEndCapture(s, &out));
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, out, 0);
+  cudaGraphDestroy(out);
+  CK(e);
+  c->fcg_graph[pi] = ex;
+  c->graph_kernels[ex] = k0;   // per launch; the bodies are counted as they run
+}
+
 // Flexible CG (Algorithm 1 structure) preconditioned by one V-cycle.
 sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int maxit, int fixed,
                        sipg_solve_info *info) {
@@ -1045,7 +1171,68 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
   double rn = r0;
   const bool fixed_mode = fixed > 0;
   int fell_back = 0;
-  while (true) {
+  // (a solve that ends before its first iteration stays on the host path)
+  const bool on_device = !c->use_learned && c->nv == 1 && s != nullptr && r0 > 0.0 &&
+                         (fixed_mode || (rtol < 1.0 && maxit > 0));
+  if (on_device) {
+    // iterations gated on the device, kFcgChunk per graph launch and host read
+    if (!c->fcg_state) {
+      c->fcg_state = dalloc<int>(c, 4);
+      c->fcg_hist = dalloc<double>(c, 260);
+      c->fcg_prm = dalloc<double>(c, 2);
+    }
+    struct {
+      double rtol;
+      int maxit, fixed;
+    } prm{rtol, maxit, fixed};
+    const int st0[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(c->fcg_prm, &prm, sizeof(prm), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->fcg_state, st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->scal + 20, &r0, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (x != c->fx) CK(cudaMemcpyAsync(c->fx, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    build_fcg_chunk(c);
+    int hs[4] = {0, 0, 0, 0};
+    // every chunk that does not end the solve advances it by kFcgChunk
+    // iterations, and the device ends it at maxit: the bound below is never
+    // reached unless the device state stopped moving
+    const int max_launches = (fixed_mode ? fixed : maxit) / kFcgChunk + 2;
+    for (int launches = 0;; ++launches) {
+      if (launches >= max_launches) {
+        c->err = "flexible CG on the device made no progress";
+        throw Fail{SIPG_ECUDA};
+      }
+      CK(cudaGraphLaunch(c->fcg_graph[c->prm.precision], s));
+      note_kernels(c->graph_kernels[c->fcg_graph[c->prm.precision]]);
+      CK(cudaMemcpyAsync(hs, c->fcg_state, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hs[1]) break;
+    }
+    if (x != c->fx) CK(cudaMemcpyAsync(x, c->fx, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    it = hs[0];
+    // kernels of the bodies that ran: the first step of iterations 1..it,
+    // the preconditioning step of all but the last
+    for (int j = 0; j < it; ++j) note_kernels(c->fcg_kA[j % kFcgChunk] + (j + 1 < it ? c->fcg_kB[j % kFcgChunk] : 0));
+    // a breakdown is counted as an iteration without a recorded residual
+    const int done_it = hs[2] == 1 ? it - 1 : it;
+    std::vector<double> h(std::min(done_it, 256) + 1);
+    CK(cudaMemcpyAsync(h.data(), c->fcg_hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double rr_last = 0;
+    CK(cudaMemcpyAsync(&rr_last, c->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int j = 1; j < (int)h.size(); ++j) hist.push_back(h[j]);
+    if (hs[2] == 1) {
+      c->err = "flexible CG breakdown: p^T A p <= 0 or a non-finite scalar";
+      st = SIPG_EBREAKDOWN;
+      rn = hist.back();
+    } else {
+      rn = std::sqrt(rr_last);   // (the history stops at 256 iterations)
+      if (hs[2] == 2) st = SIPG_ENOTCONV;
+    }
+  }
+  // otherwise (the learned cycle, whose fallback the host decides per
+  // iteration; the legacy default stream, which cannot be captured): one host
+  // read per iteration
+  while (!on_device) {
     if (fixed_mode) {
       if (it >= fixed) break;
     } else if (rn <= rtol * r0 || r0 == 0.0) {
@@ -1637,7 +1824,10 @@ sipg_status sipg_destroy(sipg_ctx *c) {
     if (g) cudaGraphExecDestroy(g);
   for (auto &g : c->vgraph_l)
     if (g) cudaGraphExecDestroy(g);
+  for (auto &g : c->fcg_graph)
+    if (g) cudaGraphExecDestroy(g);
   if (c->mv.graph) cudaGraphExecDestroy(c->mv.graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   amg_destroy(c->amg);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
@@ -1897,7 +2087,8 @@ sipg_status sipg_set_tile_shape(sipg_ctx *c, int level, int precision, int pass,
   for (int p = 0; p < 2; ++p) {
     if (c->vgraph[p]) cudaGraphExecDestroy(c->vgraph[p]);
     if (c->vgraph_l[p]) cudaGraphExecDestroy(c->vgraph_l[p]);
-    c->vgraph[p] = c->vgraph_l[p] = nullptr;
+    if (c->fcg_graph[p]) cudaGraphExecDestroy(c->fcg_graph[p]);
+    c->vgraph[p] = c->vgraph_l[p] = c->fcg_graph[p] = nullptr;
     c->vcalls[p] = c->vcalls_l[p] = 0;
   }
   if (c->mv.graph) cudaGraphExecDestroy(c->mv.graph);

@@ -172,6 +172,64 @@ cudaError_t launch_fcg_update_p(double *p, const double *z, const double *sc, in
   return cudaGetLastError();
 }
 
+// ------------------------------------------ flexible CG steps gated on the device
+// State of a solve kept in device memory so that chunks of iterations run as
+// one captured graph whose steps are conditional nodes: st[0] iterations,
+// st[1] done, st[2] status (0 ok, 1 breakdown, 2 maxit reached); prm: the
+// relative tolerance, maxit, the fixed iteration count (0: to the tolerance);
+// the initial residual norm in sc[20]; hist[j] = ||r_j|| for j <= 256.  The
+// test ||r|| <= rtol ||r_0|| is the host loop's, in the same arithmetic.
+struct FcgParams {
+  double rtol;
+  int maxit, fixed;
+};
+
+// After x += alpha p, r -= alpha v (sc[3] = r.r): count the iteration, record
+// ||r||, decide convergence or breakdown, and set the condition of the
+// preconditioning step that follows (1: the solve goes on).
+__global__ void fcg_check_kernel(const double *sc, double *hist, int *st, const FcgParams *prm,
+                                 cudaGraphConditionalHandle next) {
+  const int it = st[0] + 1;
+  st[0] = it;
+  int done = 0;
+  const double pv = sc[2], rr = sc[3];
+  if (!(pv > 0) || !isfinite(sc[0]) || !isfinite(rr)) {
+    st[2] = 1;
+    done = 1;
+  } else {
+    const double rn = sqrt(rr);
+    if (it <= 256) hist[it] = rn;
+    if (prm->fixed > 0) {
+      done = it >= prm->fixed;
+    } else if (rn <= prm->rtol * sc[20]) {
+      done = 1;
+    } else if (it >= prm->maxit) {
+      st[2] = 2;
+      done = 1;
+    }
+  }
+  st[1] = done;
+  cudaGraphSetConditional(next, done ? 0u : 1u);
+}
+
+// The condition of an iteration's first step: 1 while the solve is not done.
+__global__ void fcg_cond_kernel(const int *st, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, st[1] ? 0u : 1u);
+}
+
+cudaError_t launch_fcg_check(const double *sc, double *hist, int *st, const void *prm, cudaGraphConditionalHandle next,
+                             cudaStream_t s) {
+  fcg_check_kernel<<<1, 1, 0, s>>>(sc, hist, st, (const FcgParams *)prm, next);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fcg_cond(const int *st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  fcg_cond_kernel<<<1, 1, 0, s>>>(st, h);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ------------------------------------------ coarse-level Jacobi-PCG
 // Kernels of a fixed number of preconditioned CG iterations on vectors of the
 // cycle's precision with FP64 scalars that stay in device memory (so the
