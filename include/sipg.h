@@ -307,7 +307,17 @@ sipg_status sipg_time_apply(sipg_ctx *ctx, int precision, const void *u_dev, voi
  * operators of all problems run as one persistent launch per pass (a fixed
  * grid walking a work list of (problem, cell block) items, longest first);
  * the flexible-CG iterations run in lockstep with batched inner products and
- * updates and each problem's V-cycle (a CUDA graph) on its own stream. */
+ * updates (blocks per problem in proportion to its size).  On a non-default
+ * stream, when every problem's hierarchy starts with a DG level above a
+ * matrix-free FE level of the same degree (cph), the V-cycles of all problems
+ * are one captured graph: the Chebyshev steps, residuals and c-transfers of
+ * those two levels are shared batched launches over all problems; below them
+ * each problem's own cycle is a branch of the graph; a problem of 2^21 DoF or
+ * more keeps its whole cycle as a branch beside the shared launches.  The
+ * lockstep iteration then runs in captured chunks gated on the device (one
+ * host read per chunk).  Otherwise each problem's V-cycle (a CUDA graph) runs
+ * on its own stream and the host reads the scalars every iteration.  Every
+ * problem's numbers are those of its own single-problem kernels either way. */
 typedef struct sipg_batch sipg_batch;
 sipg_status sipg_batch_create(int nprob, const sipg_mesh *meshes, const sipg_params *params, sipg_batch **out);
 sipg_status sipg_batch_destroy(sipg_batch *batch);
@@ -316,6 +326,11 @@ const char *sipg_batch_last_error(const sipg_batch *batch);
 sipg_status sipg_batch_context(sipg_batch *batch, int i, sipg_ctx **ctx);
 /* v[i] = A_i u[i] (FP64, finest level) for every problem: two launches total. */
 sipg_status sipg_batch_apply(sipg_batch *batch, const double *const *u_dev, double *const *v_dev);
+/* z[i] = M_i^-1 r[i] (FP64 in and out): one V-cycle (Algorithm 2) of every
+ * problem, through the batched cycle where it applies (above).  Each z[i]
+ * equals sipg_vcycle on problem i's context bit for bit.  EINVAL for a NULL
+ * array or entry. */
+sipg_status sipg_batch_vcycle(sipg_batch *batch, const double *const *r_dev, double *const *z_dev);
 /* Solve A_i x[i] = b[i] for every problem to ||r||/||r0|| <= rtol (x[i] holds
  * the start vector); infos (array of nprob, may be NULL) gets each problem's
  * history.  Status as sipg_solve, worst over the problems. */

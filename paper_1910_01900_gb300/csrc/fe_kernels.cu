@@ -29,21 +29,15 @@ __device__ __forceinline__ bool node_constrained(const int g[3], const int grid[
          (g[2] == 0 && bc[4] == 0) || (g[2] == grid[2] - 1 && bc[5] == 0);
 }
 
-// cb cells per thread block (a launch parameter, cb N^2 threads); MULTI:
-// several vectors, block b = cell group b / nv of vector b % nv (compiled
-// apart from the single-vector kernel, whose offsets would cost registers)
-template <typename T, int N, bool CURVED, bool MULTI>
-__global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a, const int cb) {
+// The cell pass on cells cell0 .. cell0 + ncta - 1 of one vector (input ug,
+// element buffer ebv), one line of N points per thread, N^2 threads per cell
+// (threads beyond ncta N^2 only join the barriers).
+template <typename T, int N, bool CURVED>
+__device__ __forceinline__ void fe_cell_body(const FEArgs<T> &a, const T *__restrict__ ug, T *__restrict__ ebv,
+                                             const int cell0, const int ncta, T *sm) {
   constexpr int N2 = N * N, N3 = N2 * N, TT = Tile<N>::T3;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sm = reinterpret_cast<T *>(smem_raw);
   const int NT = blockDim.x;
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
-  // block -> (cell group, vector); the vectors of one group are neighbours
-  const int grp = MULTI ? blockIdx.x / a.nv : blockIdx.x, vec = MULTI ? blockIdx.x - grp * a.nv : 0;
-  const int cell0 = grp * cb;
-  const int ncta = min(cb, a.ncells - cell0);
-  const T *__restrict__ ug = MULTI ? a.u + vec * a.vs : a.u;
   const bool act = cl < ncta;
   T *su = sm + cl * Tile<N>::CS;
   for (int i = tid; i < ncta * N3; i += NT) {
@@ -119,9 +113,23 @@ __global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a
     load_line<T, N>(su, base, stride, x);
   }
   apply_mat<T, N, MSt>(x, y);
-  T *eb = (MULTI ? a.ebuf + vec * a.es : a.ebuf) + (size_t)(cell0 + cl) * N3 + l;
+  T *eb = ebv + (size_t)(cell0 + cl) * N3 + l;
 #pragma unroll
   for (int q = 0; q < N; ++q) eb[q * N2] = y[q];
+}
+
+// cb cells per thread block (a launch parameter, cb N^2 threads); MULTI:
+// several vectors, block b = cell group b / nv of vector b % nv (compiled
+// apart from the single-vector kernel, whose offsets would cost registers)
+template <typename T, int N, bool CURVED, bool MULTI>
+__global__ void __launch_bounds__(kCellThreads) fe_cell_kernel(const FEArgs<T> a, const int cb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  // block -> (cell group, vector); the vectors of one group are neighbours
+  const int grp = MULTI ? blockIdx.x / a.nv : blockIdx.x, vec = MULTI ? blockIdx.x - grp * a.nv : 0;
+  const int cell0 = grp * cb;
+  fe_cell_body<T, N, CURVED>(a, MULTI ? a.u + vec * a.vs : a.u, MULTI ? a.ebuf + vec * a.es : a.ebuf, cell0,
+                             min(cb, a.ncells - cell0), sm);
 }
 
 // Cell-local diagonal of the FE operator (setup, FP64): one thread per (cell, node).
@@ -241,47 +249,60 @@ __global__ void fe_stencil_assemble_kernel(const FEArgs<double> a, const double 
   coef[idx] = sum;
 }
 
-// Stencil apply with the gather's epilogue (modes 0, 1, 2), one thread per
-// node, vector blockIdx.y.  Neighbours outside the grid or on a Dirichlet
-// plane are skipped (their coefficients are zero).
+// Stencil apply with the gather's epilogue (modes 0, 1, 2), vector
+// blockIdx.y.  SL = 4 (P = 1) or 8 (P = 2, 3) consecutive lanes share a node:
+// lane z < W sums the W^2 offsets of slab z of the (2P+1)^3 stencil (all its
+// loads issued together), the node's lanes add their sums by shuffles and the
+// first lane writes the row.  Neighbours outside the grid or on a Dirichlet
+// plane are skipped (their coefficients are zero).  Spreading a row over
+// lanes shortens each thread's chain of dependent loads: these levels are
+// small and bound by latency.
 template <typename T, int P>
-__global__ void fe_stencil_apply_kernel(const FEArgs<T> a, const T *__restrict__ coef) {
-  constexpr int W = 2 * P + 1;
+__global__ void __launch_bounds__(256) fe_stencil_apply_kernel(const FEArgs<T> a, const T *__restrict__ coef) {
+  constexpr int W = 2 * P + 1, SL = P == 1 ? 4 : 8;
   const long ng = (long)a.grid[0] * a.grid[1] * a.grid[2];
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= ng) return;
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int z = (int)(t % SL);
+  const long gid = t / SL;
+  const bool live = gid < ng && z < W;
   const int64_t vo = blockIdx.y * a.vs;
   const T *__restrict__ u = a.u + vo;
-  const int g[3] = {(int)(gid % a.grid[0]), (int)((gid / a.grid[0]) % a.grid[1]),
-                    (int)(gid / ((long)a.grid[0] * a.grid[1]))};
-  bool ok[3][W];
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      const int h = g[d] + k - P;
-      ok[d][k] = h >= 0 && h < a.grid[d] && !(h == 0 && a.bc[2 * d] == 0) &&
-                 !(h == a.grid[d] - 1 && a.bc[2 * d + 1] == 0);
-    }
-  const long sy = a.grid[0], sz = (long)a.grid[0] * a.grid[1];
-  // all loads first, unconditionally (a skipped neighbour reads the node
-  // itself), so that they are in flight together; then the sum, skipping by
-  // selection
-  constexpr int W3 = W * W * W;
-  T cf[W3], uv[W3];
-#pragma unroll
-  for (int o = 0; o < W3; ++o) {
-    const int x = o % W, yy = (o / W) % W, z = o / (W * W);
-    const bool take = ok[0][x] && ok[1][yy] && ok[2][z];
-    cf[o] = coef[(long)o * ng + gid];
-    uv[o] = u[take ? gid + (x - P) + (yy - P) * sy + (z - P) * sz : gid];
-  }
   T y = T(0);
-#pragma unroll
-  for (int o = 0; o < W3; ++o) {
-    const int x = o % W, yy = (o / W) % W, z = o / (W * W);
-    y = (ok[0][x] && ok[1][yy] && ok[2][z]) ? fma(cf[o], uv[o], y) : y;
+  int g[3] = {0, 0, 0};
+  if (gid < ng) {
+    g[0] = (int)(gid % a.grid[0]);
+    g[1] = (int)((gid / a.grid[0]) % a.grid[1]);
+    g[2] = (int)(gid / ((long)a.grid[0] * a.grid[1]));
   }
+  if (live) {
+    auto ok = [&](int d, int k) {
+      const int h = g[d] + k - P;
+      return h >= 0 && h < a.grid[d] && !(h == 0 && a.bc[2 * d] == 0) && !(h == a.grid[d] - 1 && a.bc[2 * d + 1] == 0);
+    };
+    if (ok(2, z)) {
+      const long sy = a.grid[0], sz = (long)a.grid[0] * a.grid[1];
+      const long base = gid + (long)(z - P) * sz;
+      T cf[W * W], uv[W * W];
+      // loads first (a skipped neighbour reads the node itself), then the sum
+#pragma unroll
+      for (int yy = 0; yy < W; ++yy)
+#pragma unroll
+        for (int x = 0; x < W; ++x) {
+          const int o = x + W * (yy + W * z);
+          const bool take = ok(0, x) && ok(1, yy);
+          cf[x + W * yy] = coef[(long)o * ng + gid];
+          uv[x + W * yy] = u[take ? base + (x - P) + (yy - P) * sy : gid];
+        }
+#pragma unroll
+      for (int yy = 0; yy < W; ++yy)
+#pragma unroll
+        for (int x = 0; x < W; ++x)
+          y = (ok(0, x) && ok(1, yy)) ? fma(cf[x + W * yy], uv[x + W * yy], y) : y;
+    }
+  }
+#pragma unroll
+  for (int w = SL / 2; w > 0; w >>= 1) y += __shfl_xor_sync(0xffffffffu, y, w, SL);
+  if (gid >= ng || z != 0) return;
   if (node_constrained(g, a.grid, a.bc)) y = u[gid];   // identity row
   const long gv = vo + gid;
   if (a.mode == 0) {
@@ -298,13 +319,9 @@ __global__ void fe_stencil_apply_kernel(const FEArgs<T> a, const T *__restrict__
 
 // Node pass: out[g] = sum over the cells sharing node g of ebuf, then the epilogue.
 template <typename T>
-__global__ void fe_gather_kernel(const FEArgs<T> a) {
-  const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= total) return;
-  // vector blockIdx.y
-  const T *__restrict__ ebuf = a.ebuf + blockIdx.y * a.es;
-  const int64_t vo = blockIdx.y * a.vs;
+__device__ __forceinline__ void fe_gather_node(const FEArgs<T> &a, const long gid, const int vec) {
+  const T *__restrict__ ebuf = a.ebuf + vec * a.es;
+  const int64_t vo = vec * a.vs;
   const int n = a.deg + 1, n2 = n * n, n3 = n2 * n;
   const int g[3] = {(int)(gid % a.grid[0]), (int)((gid / a.grid[0]) % a.grid[1]),
                     (int)(gid / ((long)a.grid[0] * a.grid[1]))};
@@ -356,19 +373,85 @@ __global__ void fe_gather_kernel(const FEArgs<T> a) {
   }
 }
 
+template <typename T>
+__global__ void fe_gather_kernel(const FEArgs<T> a) {
+  const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  fe_gather_node<T>(a, gid, blockIdx.y);   // vector blockIdx.y
+}
+
 // c-transfer prolongation: x_dg[cell][i] += x_fe[node(cell, i)]  (injection).
 template <typename T>
-__global__ void c_prolongate_add_kernel(const FEArgs<T> a, const T *xc, T *xdg, const int64_t dg_stride) {
+__device__ __forceinline__ void c_prolongate_dof(const FEArgs<T> &a, const T *xc, T *xdg, const long idx) {
   const int n = a.deg + 1, n2 = n * n, n3 = n2 * n;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)a.ncells * n3) return;
-  xc += blockIdx.y * a.vs;   // vector blockIdx.y
-  xdg += blockIdx.y * dg_stride;
   const int cell = (int)(idx / n3), p = (int)(idx - (long)cell * n3);
   const int g[3] = {(cell % a.m[0]) * a.deg + p % n, ((cell / a.m[0]) % a.m[1]) * a.deg + (p / n) % n,
                     (cell / (a.m[0] * a.m[1])) * a.deg + p / n2};
   if (node_constrained(g, a.grid, a.bc)) return;
   xdg[idx] += xc[g[0] + (size_t)a.grid[0] * (g[1] + (size_t)a.grid[1] * g[2])];
+}
+
+template <typename T>
+__global__ void c_prolongate_add_kernel(const FEArgs<T> a, const T *xc, T *xdg, const int64_t dg_stride) {
+  const int n = a.deg + 1;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)a.ncells * n * n * n) return;
+  c_prolongate_dof<T>(a, xc + blockIdx.y * a.vs, xdg + blockIdx.y * dg_stride, idx);   // vector blockIdx.y
+}
+
+// ------------------------------------------------ batched launches (many problems)
+// One launch of a pass for the same level of several independent problems:
+// block b runs item b, which names the problem (its task: the pass's
+// arguments for that problem) and the cells or nodes it covers.  The bodies
+// are the single-problem ones, so every problem's result is bit for bit the
+// one its own launch gives.  A problem whose flexible-CG system has left the
+// iteration (segs[p].active == 0) is skipped.
+
+template <typename T, bool CURVED>
+__global__ void __launch_bounds__(kBatchCellThreads) fe_cell_batched_kernel(const FETask<T> *__restrict__ tasks,
+                                                                          const WorkItem *__restrict__ items,
+                                                                          const Seg *__restrict__ segs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  const WorkItem w = items[blockIdx.x];
+  if (segs && !segs[w.p].active) return;
+  const FETask<T> &P = tasks[w.p];
+  switch (P.a.deg + 1) {
+#define SIPG_FEB_CASE(NN) \
+  case NN:                \
+    fe_cell_body<T, NN, CURVED>(P.a, P.a.u, P.a.ebuf, w.cell0, w.ncta, sm); \
+    break;
+    SIPG_FEB_CASE(2)
+    SIPG_FEB_CASE(3)
+    SIPG_FEB_CASE(4)
+    SIPG_FEB_CASE(5)
+    SIPG_FEB_CASE(6)
+    SIPG_FEB_CASE(7)
+    SIPG_FEB_CASE(8)
+    SIPG_FEB_CASE(9)
+#undef SIPG_FEB_CASE
+    default:
+      break;
+  }
+}
+
+// node passes (kind 0: gather with the task's mode and epilogue) and the
+// c-prolongation (kind 1), kBatchNodeThreads outputs per item
+template <typename T>
+__global__ void __launch_bounds__(kBatchNodeThreads) fe_nodes_batched_kernel(const FETask<T> *__restrict__ tasks,
+                                                                           const NodeItem *__restrict__ items,
+                                                                           const Seg *__restrict__ segs, int kind) {
+  const NodeItem w = items[blockIdx.x];
+  if (segs && !segs[w.p].active) return;
+  const FETask<T> &P = tasks[w.p];
+  const long i = (long)w.blk * kBatchNodeThreads + threadIdx.x;
+  if (kind == 0) {
+    if (i < (long)P.a.grid[0] * P.a.grid[1] * P.a.grid[2]) fe_gather_node<T>(P.a, i, 0);
+  } else {
+    const int n = P.a.deg + 1;
+    if (i < (long)P.a.ncells * n * n * n) c_prolongate_dof<T>(P.a, P.xc, P.xdg, i);
+  }
 }
 
 // p/h prolongation, one thread per fine node: the coarse FE function is
@@ -757,6 +840,8 @@ cudaError_t launch_fe_stencil_setup(bool curved, const FEArgs<double> &a, double
       return curved ? run_fe_stencil_setup<2, true>(a, coef, s) : run_fe_stencil_setup<2, false>(a, coef, s);
     case 2:
       return curved ? run_fe_stencil_setup<3, true>(a, coef, s) : run_fe_stencil_setup<3, false>(a, coef, s);
+    case 3:
+      return curved ? run_fe_stencil_setup<4, true>(a, coef, s) : run_fe_stencil_setup<4, false>(a, coef, s);
     default:
       return cudaErrorInvalidValue;
   }
@@ -765,13 +850,17 @@ cudaError_t launch_fe_stencil_setup(bool curved, const FEArgs<double> &a, double
 template <typename T>
 cudaError_t launch_fe_stencil_apply(const FEArgs<T> &a, const T *coef, cudaStream_t s) {
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
-  const int bs = 128;
+  const int bs = 256;
   if (total == 0) return cudaSuccess;
-  const dim3 grid((unsigned)((total + bs - 1) / bs), a.nv);
+  const long lanes = total * (a.deg == 1 ? 4 : 8);   // lanes per node (the kernel's SL)
+  if ((lanes + bs - 1) / bs > 0x7fffffffL) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((lanes + bs - 1) / bs), a.nv);
   if (a.deg == 1)
     fe_stencil_apply_kernel<T, 1><<<grid, bs, 0, s>>>(a, coef);
   else if (a.deg == 2)
     fe_stencil_apply_kernel<T, 2><<<grid, bs, 0, s>>>(a, coef);
+  else if (a.deg == 3)
+    fe_stencil_apply_kernel<T, 3><<<grid, bs, 0, s>>>(a, coef);
   else
     return cudaErrorInvalidValue;
   note_launch();
@@ -811,6 +900,38 @@ cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s) {
   fe_gather_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), a.nv), bs, 0, s>>>(a);
   note_launch();
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fe_cells_batched(bool curved, const FETask<T> *tasks, const WorkItem *items, int nitems,
+                                    size_t smem, const Seg *segs, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (curved)
+    fe_cell_batched_kernel<T, true><<<nitems, kBatchCellThreads, smem, s>>>(tasks, items, segs);
+  else
+    fe_cell_batched_kernel<T, false><<<nitems, kBatchCellThreads, smem, s>>>(tasks, items, segs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fe_nodes_batched(const FETask<T> *tasks, const NodeItem *items, int nitems, const Seg *segs,
+                                    int kind, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  fe_nodes_batched_kernel<T><<<nitems, kBatchNodeThreads, 0, s>>>(tasks, items, segs, kind);
+  note_launch();
+  return cudaGetLastError();
+}
+
+int tile_values(int n) { return cell_values(n); }
+
+template <typename T>
+cudaError_t prep_fe_cells_batched(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(fe_cell_batched_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fe_cell_batched_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
 }
 
 template <typename T>
@@ -894,6 +1015,11 @@ cudaError_t launch_dg_transfer(const XferGeom &g, const T *P1, const T *in, T *o
   template cudaError_t launch_fe_gather<T>(const FEArgs<T> &, cudaStream_t);                            \
   template cudaError_t launch_fe_stencil_apply<T>(const FEArgs<T> &, const T *, cudaStream_t);          \
   template cudaError_t launch_c_prolongate_add<T>(const FEArgs<T> &, const T *, T *, cudaStream_t, int64_t); \
+  template cudaError_t launch_fe_cells_batched<T>(bool, const FETask<T> *, const WorkItem *, int, size_t,      \
+                                                  const Seg *, cudaStream_t);                                  \
+  template cudaError_t launch_fe_nodes_batched<T>(const FETask<T> *, const NodeItem *, int, const Seg *, int, \
+                                                  cudaStream_t);                                               \
+  template cudaError_t prep_fe_cells_batched<T>(size_t);                                                       \
   template cudaError_t launch_fe_prolongate_add<T>(const XferGeom &, const T *, const T *, T *,         \
                                                    cudaStream_t);                                       \
   template cudaError_t launch_fe_restrict_nodes<T>(const XferGeom &, const T *, const T *, T *,         \

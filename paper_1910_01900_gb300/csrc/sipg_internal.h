@@ -272,6 +272,48 @@ struct Seg {
   int active;
 };
 
+// Batched FE passes (fe_kernels.cu): one task per problem, one thread block
+// per item.  Cell items cover kBatchCellThreads / n^2 cells, node items
+// kBatchNodeThreads nodes (or DG points for the c-prolongation).
+constexpr int kBatchCellThreads = 256;
+constexpr int kBatchNodeThreads = 256;
+template <typename T>
+struct FETask {
+  FEArgs<T> a;
+  const T *xc = nullptr;   // c-prolongation: FE input and DG output
+  T *xdg = nullptr;
+};
+struct NodeItem {
+  int p, blk;
+};
+template <typename T>
+cudaError_t launch_fe_cells_batched(bool curved, const FETask<T> *tasks, const WorkItem *items, int nitems,
+                                    size_t smem, const Seg *segs, cudaStream_t s);
+// kind 0: gather with each task's mode and epilogue; 1: c-prolongation
+template <typename T>
+cudaError_t launch_fe_nodes_batched(const FETask<T> *tasks, const NodeItem *items, int nitems, const Seg *segs,
+                                    int kind, cudaStream_t s);
+template <typename T>
+cudaError_t prep_fe_cells_batched(size_t smem);
+int tile_values(int n);   // shared-memory values per cell of the cell passes (sumfac.cuh)
+// batched vector steps (batch.cu); op as in vec_batched_kernel
+struct VecTask {
+  int op = 0;
+  long n = 0;
+  void *y = nullptr;
+  const void *x = nullptr, *d = nullptr;
+  double c = 0;
+};
+cudaError_t launch_vec_batched(const VecTask *tasks, const NodeItem *items, int nitems, const Seg *segs,
+                               cudaStream_t s);
+// lockstep flexible CG gated on the device (batch.cu): per-system iteration
+// count, status (1 breakdown, 2 maxit), ||r|| history [np][257] and last
+// ||r||; prm = {rtol, maxit} (device); *any = some system still iterates
+cudaError_t launch_batch_fcg_check(const double *sc, int stride, Seg *segs, int np, int *it, int *status, double *hist,
+                                   double *rn, const double *r0, const double *prm, int *any,
+                                   cudaGraphConditionalHandle next, cudaStream_t s);
+cudaError_t launch_batch_fcg_cond(const int *any, cudaGraphConditionalHandle h, cudaStream_t s);
+
 template <typename T>
 struct BatchPlan {
   std::vector<BatchProb<T>> probs;
@@ -289,13 +331,26 @@ template <typename T>
 void batch_plan_free(BatchPlan<T> &P);
 template <typename T>
 cudaError_t batch_apply(BatchPlan<T> &P, cudaStream_t s);
-constexpr int kSegBlocksHost = 32;   // blocks per system in the batched reductions (batch.cu)
-constexpr int kSegSlots = 8;   // scalar slots per problem (FCG layout of solver.cu, 4: b.b, 5: r0.r0)
-cudaError_t seg_dot(const Seg *segs, int np, int which, double *partials, unsigned *counter, double *sc,
-                    int sc_stride, int slot, cudaStream_t s);
-cudaError_t seg_update_xr(const Seg *segs, int np, double *partials, unsigned *counter, double *sc, int sc_stride,
+// one pass of the batched DG operator with the descriptors probs (device)
+template <typename T>
+cudaError_t batch_dg_pass(const BatchPlan<T> &P, const BatchProb<T> *probs, bool integrate, const Seg *segs,
                           cudaStream_t s);
-cudaError_t seg_update_p(const Seg *segs, int np, const double *sc, int sc_stride, int init, cudaStream_t s);
+constexpr int kSegSlots = 8;   // scalar slots per problem (FCG layout of solver.cu, 4: b.b, 5: r0.r0)
+// Block map of the batched vector kernels (batch.cu): g.nb[p] blocks for
+// system p, one per kSegChunk entries (at least one), its partial sums at
+// partials[2 (g.off[p] + j)]; partials hold 2 g.blocks values
+constexpr long kSegChunk = 8192;
+struct SegGrid {
+  const int2 *map = nullptr;
+  const int *off = nullptr, *nb = nullptr;
+  int blocks = 0;
+};
+cudaError_t seg_grid_build(const std::vector<long> &n, SegGrid &g, std::vector<void *> &allocs);
+cudaError_t seg_dot(const Seg *segs, const SegGrid &g, int which, double *partials, unsigned *counter, double *sc,
+                    int sc_stride, int slot, cudaStream_t s);
+cudaError_t seg_update_xr(const Seg *segs, const SegGrid &g, double *partials, unsigned *counter, double *sc,
+                          int sc_stride, cudaStream_t s);
+cudaError_t seg_update_p(const Seg *segs, const SegGrid &g, const double *sc, int sc_stride, int init, cudaStream_t s);
 
 // ---- learned smoother network (mlp.cu); bf16 buffers passed as void*
 cudaError_t mlp_gemm(const void *A, long sam, long sak, const void *B, long sbk, long sbn, int M, int N, int K,

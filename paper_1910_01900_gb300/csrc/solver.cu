@@ -89,6 +89,8 @@ struct sipg_ctx {
     double *r = nullptr, *z = nullptr, *p = nullptr, *v_ = nullptr;   // flexible-CG vectors
     std::vector<Seg> segs;
     Seg *d_segs = nullptr;
+    SegGrid sg;                                // block map of the batched vector kernels
+    std::vector<void *> sg_allocs;
     double *sc = nullptr, *partials = nullptr;
     unsigned *counters = nullptr;
     cudaGraphExec_t graph = nullptr;           // V-cycle of graph_nv vectors
@@ -339,6 +341,30 @@ void prolongate_level(sipg_ctx *c, int l, const T *xc, T *x) {
   }
 }
 
+// The steps of Algorithm 3 on level l: step 0 is x = c3 D^-1 b from x = 0
+// (xdb) or, from a given x, the first operator step with (c1, c2, c3) = (1,
+// 0, 1/theta); every later step x_new = c1 x + c2 x_prev + c3 D^-1 (b - A x).
+struct ChebStep {
+  bool xdb, has_prev;
+  double c1, c2, c3;
+};
+std::vector<ChebStep> cheb_plan(const sipg_ctx *c, int l, int ns, bool zero_start) {
+  const double lam = c->lv[l].lambda;
+  const double lhi = c->prm.cheb_hi * lam, llo = c->prm.cheb_lo * lam;
+  const double theta = 0.5 * (lhi + llo), delta = 0.5 * (lhi - llo);
+  std::vector<ChebStep> st;
+  st.push_back({zero_start, false, 1.0, 0.0, 1.0 / theta});
+  double rho_prev = delta / theta;
+  for (int j = 1; j < ns; ++j) {
+    const double rho = 1.0 / (2.0 * theta / delta - rho_prev);
+    const double sigma = rho * rho_prev, th = 2.0 * rho / delta;
+    // after x_0 = 0 the first operator step has no previous iterate
+    st.push_back({false, !(zero_start && j == 1), 1.0 + sigma, -sigma, th});
+    rho_prev = rho;
+  }
+  return st;
+}
+
 // Algorithm 3 on level l: x (in/out buffer pointer) with scratch xt; the
 // buffers are swapped as the iteration proceeds.
 template <typename T>
@@ -346,26 +372,13 @@ void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_
   constexpr int pi = pidx<T>();
   const Level &L = c->lv[l];
   const T *dinv = (const T *)L.dinv[pi];
-  const double lam = L.lambda;
-  const double lhi = c->prm.cheb_hi * lam, llo = c->prm.cheb_lo * lam;
-  const double theta = 0.5 * (lhi + llo), delta = 0.5 * (lhi - llo);
-  bool have_prev;
-  if (zero_start) {
-    CK(launch_xdb<T>(x, (T)(1.0 / theta), dinv, b, L.ndofs, c->stream, c->nv));
-    have_prev = false;   // x_0 = 0
-  } else {
-    apply_level<T>(c, l, x, xt, 1, x, nullptr, b, dinv, T(1), T(0), (T)(1.0 / theta));
+  for (const ChebStep &q : cheb_plan(c, l, ns, zero_start)) {
+    if (q.xdb) {   // x_0 = 0
+      CK(launch_xdb<T>(x, (T)q.c3, dinv, b, L.ndofs, c->stream, c->nv));
+      continue;
+    }
+    apply_level<T>(c, l, x, xt, 1, x, q.has_prev ? xt : nullptr, b, dinv, (T)q.c1, (T)q.c2, (T)q.c3);
     std::swap(x, xt);
-    have_prev = true;
-  }
-  double rho_prev = delta / theta;
-  for (int j = 1; j < ns; ++j) {
-    const double rho = 1.0 / (2.0 * theta / delta - rho_prev);
-    const double sigma = rho * rho_prev, th = 2.0 * rho / delta;
-    apply_level<T>(c, l, x, xt, 1, x, have_prev ? xt : nullptr, b, dinv, (T)(1.0 + sigma), (T)(-sigma), (T)th);
-    std::swap(x, xt);
-    have_prev = true;
-    rho_prev = rho;
   }
 }
 
@@ -910,7 +923,7 @@ void setup(sipg_ctx *c) {
   c->coarse_cg = c->lv[0].ndofs > P.coarse_dense_max;
   const int lfirst = c->coarse_cg ? 0 : 1;   // levels that need an operator beyond the V-cycle's smoothing
   // assembled stencils of the low-degree FE levels that get applied
-  if (P.fe_assemble < 0 || P.fe_assemble > 2) throw_inval("fe_assemble must be 0, 1 or 2");
+  if (P.fe_assemble < 0 || P.fe_assemble > 3) throw_inval("fe_assemble must be 0, 1, 2 or 3");
   for (int l = lfirst; l < nl; ++l) {
     Level &L = c->lv[l];
     if (L.kind != 1 || L.deg > P.fe_assemble) continue;
@@ -2236,6 +2249,45 @@ sipg_status sipg_fma_peak(int precision, void *stream, double *flops) {
 
 // ------------------------------------------------------------------ batches
 
+// One V-cycle of all problems of a batch as one captured graph: the two
+// finest levels of every problem (its DG level and the FE level of the same
+// degree, whose operators dominate the cycle) run as shared launches, each
+// Chebyshev step, residual and c-transfer one batched launch over all
+// problems' cells or nodes; below them each problem's own cycle (its
+// restriction, lower levels, coarse solve, prolongation) is a branch of the
+// graph, the branches of different problems side by side.
+struct BLaunch {
+  int kind;     // 0 vector op over DG points, 1 over FE nodes, 2 DG evaluation, 3 DG integration,
+                // 4 FE cell pass, 5 FE node pass, 6 c-prolongation, 7 the per-problem branches
+  size_t off;   // the launch's first task in its task array (one task per problem)
+};
+
+template <typename T>
+struct BatchCycle {
+  int np = 0;
+  bool curved = false;
+  BatchPlan<T> dg;                        // DG work items of the finest levels
+  WorkItem *fe_items = nullptr;           // FE cell items
+  int n_fe_items = 0;
+  size_t fe_smem = 0;
+  NodeItem *items_d = nullptr, *items_g = nullptr;   // DG points, FE nodes
+  int n_d = 0, n_g = 0;
+  VecTask *vec = nullptr;
+  BatchProb<T> *dgt = nullptr;
+  FETask<T> *fet = nullptr;
+  std::vector<BLaunch> prog;
+  std::vector<T *> br_r, br_x;            // per problem: FE residual to restrict, FE iterate to correct
+  std::vector<char> solo;                 // problems that fill the GPU alone: own cycle, beside the rest
+  cudaGraphExec_t graph = nullptr;
+  long long kernels = 0;
+  ~BatchCycle() {
+    if (graph) cudaGraphExecDestroy(graph);
+    batch_plan_free(dg);
+    for (void *q : {(void *)fe_items, (void *)items_d, (void *)items_g, (void *)vec, (void *)dgt, (void *)fet})
+      cudaFree(q);
+  }
+};
+
 struct sipg_batch {
   std::vector<sipg_ctx *> ctx;
   std::vector<cudaStream_t> streams;   // one per problem (created here)
@@ -2243,11 +2295,25 @@ struct sipg_batch {
   BatchPlan<double> plan;
   std::vector<Seg> segs;
   Seg *d_segs = nullptr;
+  SegGrid sg;                      // block map of the batched vector kernels
+  std::vector<void *> sg_allocs;
   double *sc = nullptr, *partials = nullptr;
   unsigned *counters = nullptr;
-  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_branch = nullptr;
   std::vector<cudaEvent_t> ev_done;
   std::string err;
+  // the batched cycle (state 0 not tried, 1 built, -1 not applicable)
+  int cyc_state = 0;
+  std::unique_ptr<BatchCycle<double>> cyc_d;
+  std::unique_ptr<BatchCycle<float>> cyc_f;
+  // flexible CG gated on the device: chunk graph, state and descriptors
+  cudaGraphExec_t fcg_graph = nullptr;
+  long long fcg_k0 = 0;
+  std::vector<long long> fcg_kA, fcg_kB;
+  cudaStream_t cap_stream = nullptr;
+  BatchProb<double> *d_app = nullptr;   // v = A p descriptors
+  int *d_it = nullptr, *d_status = nullptr, *d_any = nullptr;
+  double *d_hist = nullptr, *d_rn = nullptr, *d_r0 = nullptr, *d_prm = nullptr;
 };
 
 namespace {
@@ -2255,6 +2321,13 @@ namespace {
 void batch_free(sipg_batch *B) {
   if (!B) return;
   if (B->stream) cudaStreamSynchronize(B->stream);
+  B->cyc_d.reset();
+  B->cyc_f.reset();
+  if (B->fcg_graph) cudaGraphExecDestroy(B->fcg_graph);
+  if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  for (void *q : {(void *)B->d_app, (void *)B->d_it, (void *)B->d_status, (void *)B->d_any, (void *)B->d_hist,
+                  (void *)B->d_rn, (void *)B->d_r0, (void *)B->d_prm})
+    cudaFree(q);
   for (auto *c : B->ctx)
     if (c) sipg_destroy(c);
   for (auto s : B->streams) cudaStreamDestroy(s);
@@ -2262,14 +2335,26 @@ void batch_free(sipg_batch *B) {
   cudaFree(B->d_segs);
   cudaFree(B->sc);
   cudaFree(B->partials);
+  for (void *q : B->sg_allocs) cudaFree(q);
   cudaFree(B->counters);
   if (B->ev_start) cudaEventDestroy(B->ev_start);
+  if (B->ev_branch) cudaEventDestroy(B->ev_branch);
   for (auto e : B->ev_done) cudaEventDestroy(e);
   delete B;
 }
 
-// all problems' preconditioners z = M^-1 r, each on its own stream, overlapping
+template <typename T>
+BatchCycle<T> *batch_cycle(sipg_batch *B);
+
+// all problems' preconditioners z = M^-1 r: the batched cycle's graph, else
+// each problem's cycle on its own stream, overlapping
 void batch_precondition(sipg_batch *B) {
+  if (B->cyc_state == 1) {
+    const long long k = B->cyc_d ? B->cyc_d->kernels : B->cyc_f->kernels;
+    CK(cudaGraphLaunch(B->cyc_d ? B->cyc_d->graph : B->cyc_f->graph, B->stream));
+    note_kernels(k);
+    return;
+  }
   CK(cudaEventRecord(B->ev_start, B->stream));
   for (size_t p = 0; p < B->ctx.size(); ++p) {
     if (!B->segs[p].active) continue;
@@ -2301,6 +2386,7 @@ struct Lockstep {
   cudaStream_t s;
   std::vector<Seg> &segs;
   Seg *d_segs;
+  const SegGrid &g;
   double *sc, *partials;
   unsigned *counters;
   std::string &err;
@@ -2326,10 +2412,10 @@ sipg_status lockstep_fcg(Lockstep K, FR residual, FA apply, FP precondition_all,
   CK(cudaEventRecord(e0, s));
   upload_segs();
   residual();
-  CK(seg_dot(K.d_segs, np, 0, K.partials, K.counters, K.sc, st, 4, s));
+  CK(seg_dot(K.d_segs, K.g, 0, K.partials, K.counters, K.sc, st, 4, s));
   precondition_all();
-  CK(seg_dot(K.d_segs, np, 1, K.partials, K.counters, K.sc, st, 0, s));
-  CK(seg_update_p(K.d_segs, np, K.sc, st, 1, s));
+  CK(seg_dot(K.d_segs, K.g, 1, K.partials, K.counters, K.sc, st, 0, s));
+  CK(seg_update_p(K.d_segs, K.g, K.sc, st, 1, s));
   read_sc();
   std::vector<double> r0(np), rn(np);
   std::vector<int> it(np, 0);
@@ -2362,8 +2448,8 @@ sipg_status lockstep_fcg(Lockstep K, FR residual, FA apply, FP precondition_all,
     if (nact == 0) break;
     upload_segs();
     apply();
-    CK(seg_dot(K.d_segs, np, 2, K.partials, K.counters, K.sc, st, 2, s));
-    CK(seg_update_xr(K.d_segs, np, K.partials, K.counters, K.sc, st, s));
+    CK(seg_dot(K.d_segs, K.g, 2, K.partials, K.counters, K.sc, st, 2, s));
+    CK(seg_update_xr(K.d_segs, K.g, K.partials, K.counters, K.sc, st, s));
     read_sc();
     for (int p = 0; p < np; ++p) {
       if (!K.segs[p].active) continue;
@@ -2384,8 +2470,8 @@ sipg_status lockstep_fcg(Lockstep K, FR residual, FA apply, FP precondition_all,
     for (int p = 0; p < np; ++p) still += K.segs[p].active;
     if (still == 0) break;
     precondition_all();
-    CK(seg_dot(K.d_segs, np, 3, K.partials, K.counters, K.sc, st, 0, s));
-    CK(seg_update_p(K.d_segs, np, K.sc, st, 0, s));
+    CK(seg_dot(K.d_segs, K.g, 3, K.partials, K.counters, K.sc, st, 0, s));
+    CK(seg_update_p(K.d_segs, K.g, K.sc, st, 0, s));
   }
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
@@ -2410,8 +2496,504 @@ sipg_status lockstep_fcg(Lockstep K, FR residual, FA apply, FP precondition_all,
   return status;
 }
 
+// ------------------------------------------------ the batched V-cycle
+// Applicable when every problem has a DG finest level above a matrix-free FE
+// level of the same degree (the cph hierarchy's c-transfer first), one
+// vector, the batch's common precision and Chebyshev degree, and the batch
+// runs on a non-default stream (the cycle is captured).
+bool batch_cycle_applicable(const sipg_batch *B) {
+  if (!B->stream) return false;
+  const sipg_ctx *c0 = B->ctx[0];
+  for (const sipg_ctx *c : B->ctx) {
+    const int L = c->L;
+    if (c->nv != 1 || L < 2 || c->prm.precision != c0->prm.precision ||
+        c->prm.cheb_degree != c0->prm.cheb_degree)
+      return false;
+    const Level &D = c->lv[L], &F = c->lv[L - 1];
+    if (D.kind != 0 || F.kind != 1 || D.t_kind != 0 || F.deg != D.deg || D.ufn || D.curved != c0->lv[c0->L].curved ||
+        F.stencil[c->prm.precision])
+      return false;
+  }
+  return true;
+}
+
+// Issue the batched cycle's launches on s (inside a stream capture): the
+// problems that fill the GPU alone run their own cycle on their own stream,
+// beside the shared launches of the others.
+template <typename T>
+void batch_cycle_emit(sipg_batch *B, BatchCycle<T> &C, cudaStream_t s) {
+  const Seg *segs = B->d_segs;
+  bool forked = false;
+  for (int p = 0; p < C.np; ++p) {
+    if (!C.solo[p]) continue;
+    if (!forked) CK(cudaEventRecord(B->ev_start, s));
+    forked = true;
+    CK(cudaStreamWaitEvent(B->streams[p], B->ev_start, 0));
+    vcycle_body(B->ctx[p], B->ctx[p]->fr, B->ctx[p]->fz);   // on the problem's own stream
+    CK(cudaEventRecord(B->ev_done[p], B->streams[p]));
+  }
+  for (const BLaunch &r : C.prog) {
+    switch (r.kind) {
+      case 0:
+        CK(launch_vec_batched(C.vec + r.off, C.items_d, C.n_d, segs, s));
+        break;
+      case 1:
+        CK(launch_vec_batched(C.vec + r.off, C.items_g, C.n_g, segs, s));
+        break;
+      case 2:
+      case 3:
+        CK(batch_dg_pass<T>(C.dg, C.dgt + r.off, r.kind == 3, segs, s));
+        break;
+      case 4:
+        CK(launch_fe_cells_batched<T>(C.curved, C.fet + r.off, C.fe_items, C.n_fe_items, C.fe_smem, segs, s));
+        break;
+      case 5:
+        CK(launch_fe_nodes_batched<T>(C.fet + r.off, C.items_g, C.n_g, segs, 0, s));
+        break;
+      case 6:
+        CK(launch_fe_nodes_batched<T>(C.fet + r.off, C.items_d, C.n_d, segs, 1, s));
+        break;
+      default: {   // each problem's cycle below its two finest levels, side by side
+        CK(cudaEventRecord(B->ev_branch, s));
+        for (int p = 0; p < C.np; ++p) {
+          if (C.solo[p]) continue;
+          sipg_ctx *c = B->ctx[p];
+          cudaStream_t own = c->stream;
+          CK(cudaStreamWaitEvent(B->streams[p], B->ev_branch, 0));
+          c->stream = B->streams[p];
+          try {
+            const int L = c->L;
+            restrict_level<T>(c, L - 1, C.br_r[p], lvec<T>(c, L - 2, 0));
+            const T *xc = vcycle_rec<T>(c, L - 2);
+            prolongate_level<T>(c, L - 1, xc, C.br_x[p]);
+          } catch (...) {
+            c->stream = own;
+            throw;
+          }
+          c->stream = own;
+          CK(cudaEventRecord(B->ev_done[p], B->streams[p]));
+          CK(cudaStreamWaitEvent(s, B->ev_done[p], 0));
+        }
+      }
+    }
+  }
+  for (int p = 0; p < C.np; ++p)
+    if (C.solo[p]) CK(cudaStreamWaitEvent(s, B->ev_done[p], 0));
+}
+
+template <typename T>
+T *upload_vec(const std::vector<T> &h) {
+  T *d = nullptr;
+  CK(cudaMalloc(&d, std::max<size_t>(1, h.size()) * sizeof(T)));
+  if (!h.empty()) CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return d;
+}
+
+// The program of one cycle (the mirror of vcycle_rec on the two finest
+// levels, vcycle_body's conversions around it), its device arrays and its graph.
+template <typename T>
+std::unique_ptr<BatchCycle<T>> batch_cycle_build(sipg_batch *B) {
+  constexpr int pi = pidx<T>();
+  auto C = std::make_unique<BatchCycle<T>>();
+  const int np = (int)B->ctx.size();
+  C->np = np;
+  C->curved = B->ctx[0]->lv[B->ctx[0]->L].curved;
+  const int ns = B->ctx[0]->prm.cheb_degree;
+  std::vector<DGArgs<T>> a0;
+  std::vector<int> nn;
+  std::vector<WorkItem> fei;
+  std::vector<NodeItem> nd, ng;
+  // a problem of at least kSoloDofs DoF keeps its own cycle (its launches
+  // fill the GPU; in lockstep with small problems it would wait for their
+  // lower levels at every shared step)
+  constexpr int64_t kSoloDofs = int64_t(1) << 21;
+  C->solo.assign(np, 0);
+  for (int p = 0; p < np; ++p) {
+    sipg_ctx *c = B->ctx[p];
+    const Level &D = c->lv[c->L], &F = c->lv[c->L - 1];
+    a0.push_back(dg_args<T>(c, D));
+    nn.push_back(D.n);
+    if (np > 1 && D.ndofs >= kSoloDofs) {
+      C->solo[p] = 1;
+      a0.back().ncells = 0;   // no DG items
+      continue;
+    }
+    const int cb = kBatchCellThreads / (F.n * F.n);
+    C->fe_smem = std::max(C->fe_smem, (size_t)cb * tile_values(F.n) * sizeof(T));
+    for (int q = 0; q < F.ncells; q += cb) fei.push_back({p, q, (int)std::min<int64_t>(cb, F.ncells - q)});
+    for (int64_t q = 0; q * kBatchNodeThreads < D.ndofs; ++q) nd.push_back({p, (int)q});
+    for (int64_t q = 0; q * kBatchNodeThreads < F.ndofs; ++q) ng.push_back({p, (int)q});
+  }
+  CK(batch_plan_build<T>(C->dg, a0, nn));
+  C->dg.curved = C->curved;
+  CK(prep_fe_cells_batched<T>(C->fe_smem));
+  C->n_fe_items = (int)fei.size();
+  C->n_d = (int)nd.size();
+  C->n_g = (int)ng.size();
+  // the program, task by task
+  std::vector<VecTask> hv;
+  std::vector<BatchProb<T>> hd;
+  std::vector<FETask<T>> hf;
+  std::vector<T *> bL(np), xL(np), rL(np), tL(np), bF(np), xF(np), rF(np), tF(np);
+  for (int p = 0; p < np; ++p) {
+    sipg_ctx *c = B->ctx[p];
+    const int L = c->L;
+    bL[p] = lvec<T>(c, L, 0), xL[p] = lvec<T>(c, L, 1), rL[p] = lvec<T>(c, L, 2), tL[p] = lvec<T>(c, L, 3);
+    bF[p] = lvec<T>(c, L - 1, 0), xF[p] = lvec<T>(c, L - 1, 1), rF[p] = lvec<T>(c, L - 1, 2);
+    tF[p] = lvec<T>(c, L - 1, 3);
+  }
+  auto vec = [&](int kind, auto task) {
+    C->prog.push_back({kind, hv.size()});
+    for (int p = 0; p < np; ++p) hv.push_back(task(p));
+  };
+  auto dgapply = [&](auto args) {
+    C->prog.push_back({2, hd.size()});
+    C->prog.push_back({3, hd.size()});
+    for (int p = 0; p < np; ++p) {
+      BatchProb<T> q{};
+      q.a = args(p);
+      q.n = nn[p];
+      q.active = 1;
+      hd.push_back(q);
+    }
+  };
+  auto fetask = [&](int kind, auto args) {   // kind 4: cell and node pass; 5: node pass; 6: c-prolongation
+    if (kind == 4) C->prog.push_back({4, hf.size()});
+    C->prog.push_back({kind == 4 ? 5 : kind, hf.size()});
+    for (int p = 0; p < np; ++p) hf.push_back(args(p));
+  };
+  auto dga = [&](int p, const T *u, T *out, int mode, const T *x, const T *xp, const T *b, const ChebStep *q) {
+    sipg_ctx *c = B->ctx[p];
+    const Level &D = c->lv[c->L];
+    DGArgs<T> a = dg_args<T>(c, D);
+    a.u = u, a.out = out, a.mode = mode, a.x = x, a.xp = xp, a.b = b;
+    if (q) a.dinv = (const T *)D.dinv[pi], a.c1 = (T)q->c1, a.c2 = (T)q->c2, a.c3 = (T)q->c3;
+    return a;
+  };
+  auto fea = [&](int p, const T *u, T *out, int mode, const T *x, const T *xp, const T *b, const ChebStep *q) {
+    sipg_ctx *c = B->ctx[p];
+    const Level &F = c->lv[c->L - 1];
+    FETask<T> t{};
+    t.a = fe_args<T>(c, F);
+    t.a.u = u, t.a.out = out, t.a.mode = mode, t.a.x = x, t.a.xp = xp, t.a.b = b;
+    if (q) t.a.dinv = (const T *)F.dinv[pi], t.a.c1 = (T)q->c1, t.a.c2 = (T)q->c2, t.a.c3 = (T)q->c3;
+    return t;
+  };
+  // Algorithm 3 on the DG (dg) or FE level of every problem, as chebyshev()
+  auto cheb = [&](bool dg, bool zero_start) {
+    std::vector<std::vector<ChebStep>> plan(np);
+    for (int p = 0; p < np; ++p) plan[p] = cheb_plan(B->ctx[p], B->ctx[p]->L - (dg ? 0 : 1), ns, zero_start);
+    std::vector<T *> &x = dg ? xL : xF, &xt = dg ? tL : tF, &b = dg ? bL : bF;
+    for (int j = 0; j < ns; ++j) {
+      if (plan[0][j].xdb) {
+        vec(dg ? 0 : 1, [&](int p) {
+          const Level &l = B->ctx[p]->lv[B->ctx[p]->L - (dg ? 0 : 1)];
+          VecTask v;
+          v.op = pi == 1 ? 2 : 3;
+          v.n = (long)l.ndofs;
+          v.y = x[p], v.x = b[p], v.d = l.dinv[pi], v.c = (double)(T)plan[p][j].c3;
+          return v;
+        });
+        continue;
+      }
+      if (dg)
+        dgapply([&](int p) {
+          return dga(p, x[p], xt[p], 1, x[p], plan[p][j].has_prev ? xt[p] : nullptr, b[p], &plan[p][j]);
+        });
+      else
+        fetask(4, [&](int p) {
+          return fea(p, x[p], xt[p], 1, x[p], plan[p][j].has_prev ? xt[p] : nullptr, b[p], &plan[p][j]);
+        });
+      for (int p = 0; p < np; ++p) std::swap(x[p], xt[p]);
+    }
+  };
+  // r (FP64, the solver's fr) -> b of the DG level
+  vec(0, [&](int p) {
+    VecTask v;
+    v.op = pi == 1 ? 0 : 4;
+    v.n = (long)B->ctx[p]->lv[B->ctx[p]->L].ndofs;
+    v.y = bL[p], v.x = B->ctx[p]->fr;
+    return v;
+  });
+  cheb(true, true);
+  dgapply([&](int p) { return dga(p, xL[p], rL[p], 2, nullptr, nullptr, bL[p], nullptr); });
+  fetask(5, [&](int p) {   // c-restriction: the DG residual is the FE level's element buffer
+    FETask<T> t = fea(p, nullptr, bF[p], 3, nullptr, nullptr, nullptr, nullptr);
+    t.a.ebuf = rL[p];
+    return t;
+  });
+  cheb(false, true);
+  fetask(4, [&](int p) { return fea(p, xF[p], rF[p], 2, nullptr, nullptr, bF[p], nullptr); });
+  C->prog.push_back({7, 0});
+  C->br_r = rF;
+  C->br_x = xF;
+  cheb(false, false);
+  fetask(6, [&](int p) {
+    FETask<T> t = fea(p, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr);
+    t.xc = xF[p];
+    t.xdg = xL[p];
+    return t;
+  });
+  cheb(true, false);
+  vec(0, [&](int p) {   // the DG level's x -> z (FP64, the solver's fz)
+    VecTask v;
+    v.op = pi == 1 ? 1 : 4;
+    v.n = (long)B->ctx[p]->lv[B->ctx[p]->L].ndofs;
+    v.y = B->ctx[p]->fz, v.x = xL[p];
+    return v;
+  });
+  C->fe_items = upload_vec(fei);
+  C->items_d = upload_vec(nd);
+  C->items_g = upload_vec(ng);
+  C->vec = upload_vec(hv);
+  C->dgt = upload_vec(hd);
+  C->fet = upload_vec(hf);
+  // capture
+  cudaStream_t s = B->stream;
+  cudaGraph_t g = nullptr;
+  long long kernels = 0;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  try {
+    CaptureTally tally(&kernels);
+    batch_cycle_emit<T>(B, *C, s);
+  } catch (...) {
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  CK(cudaStreamEndCapture(s, &g));
+  const cudaError_t e = cudaGraphInstantiate(&C->graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  C->kernels = kernels;
+  return C;
+}
+
+// Build the batched cycle once, on the first preconditioning of a batch
+// whose problems allow it.
+void batch_cycle_prepare(sipg_batch *B) {
+  if (B->cyc_state != 0) return;
+  B->cyc_state = -1;
+  if (!batch_cycle_applicable(B)) return;
+  if (B->ctx[0]->prm.precision == 0) B->cyc_d = batch_cycle_build<double>(B);
+  else B->cyc_f = batch_cycle_build<float>(B);
+  B->cyc_state = 1;
+}
+
+// ------------------------------------ lockstep flexible CG gated on the device
+// Chunks of kFcgChunk lockstep iterations captured with conditional nodes:
+// iteration i is IF A_i { v = A p (batched), p.v, x and r update, check (per
+// system: iteration count, ||r||, leaving on convergence, breakdown or
+// maxit; sets B_i = some system active) } IF B_i { the batched cycle, r.z
+// and z.v, p update, A_{i+1} = B_i }.  The host reads the state once per chunk.
+void batch_build_fcg_chunk(sipg_batch *B) {
+  if (B->fcg_graph) return;
+  const int np = (int)B->ctx.size();
+  if (!B->cap_stream) CK(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t s = B->stream, s2 = B->cap_stream;
+  cudaGraph_t G = nullptr;
+  CK(cudaGraphCreate(&G, 0));
+  std::vector<cudaGraphConditionalHandle> hA(kFcgChunk), hB(kFcgChunk);
+  for (int i = 0; i < kFcgChunk; ++i) {
+    CK(cudaGraphConditionalHandleCreate(&hA[i], G, 0, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&hB[i], G, 0, cudaGraphCondAssignDefault));
+  }
+  B->fcg_kA.assign(kFcgChunk, 0);
+  B->fcg_kB.assign(kFcgChunk, 0);
+  B->fcg_k0 = 0;
+  auto body = [&](cudaGraph_t b, long long *tally, auto &&fn) {
+    CK(cudaStreamBeginCaptureToGraph(s2, b, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      CaptureTally t(tally);
+      fn();
+    } catch (...) {
+      cudaGraph_t o;
+      cudaStreamEndCapture(s2, &o);
+      throw;
+    }
+    cudaGraph_t o;
+    CK(cudaStreamEndCapture(s2, &o));
+  };
+  const int st = kSegSlots;
+  CK(cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  try {
+    {
+      CaptureTally t(&B->fcg_k0);
+      CK(launch_batch_fcg_cond(B->d_any, hA[0], s));
+    }
+    for (int i = 0; i < kFcgChunk; ++i) {
+      body(add_if_node(s, hA[i]), &B->fcg_kA[i], [&]() {
+        CK(batch_dg_pass<double>(B->plan, B->d_app, false, B->d_segs, s2));
+        CK(batch_dg_pass<double>(B->plan, B->d_app, true, B->d_segs, s2));
+        CK(seg_dot(B->d_segs, B->sg, 2, B->partials, B->counters, B->sc, st, 2, s2));
+        CK(seg_update_xr(B->d_segs, B->sg, B->partials, B->counters, B->sc, st, s2));
+        CK(launch_batch_fcg_check(B->sc, st, B->d_segs, np, B->d_it, B->d_status, B->d_hist, B->d_rn, B->d_r0,
+                                  B->d_prm, B->d_any, hB[i], s2));
+      });
+      body(add_if_node(s, hB[i]), &B->fcg_kB[i], [&]() {
+        if (B->cyc_d) batch_cycle_emit<double>(B, *B->cyc_d, s2);
+        else batch_cycle_emit<float>(B, *B->cyc_f, s2);
+        CK(seg_dot(B->d_segs, B->sg, 3, B->partials, B->counters, B->sc, st, 0, s2));
+        CK(seg_update_p(B->d_segs, B->sg, B->sc, st, 0, s2));
+        if (i + 1 < kFcgChunk) CK(launch_batch_fcg_cond(B->d_any, hA[i + 1], s2));
+      });
+    }
+  } catch (...) {
+    cudaGraph_t o = nullptr;
+    cudaStreamEndCapture(s, &o);
+    if (o) cudaGraphDestroy(o);
+    cudaGraphDestroy(G);
+    throw;
+  }
+  cudaGraph_t out = nullptr;
+  CK(cudaStreamEndCapture(s, &out));
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, out, 0);
+  cudaGraphDestroy(out);
+  CK(e);
+  B->fcg_graph = ex;
+}
+
+// The lockstep flexible CG with the iteration gated on the device (the
+// batched cycle is built): the host reads the state once per chunk of
+// kFcgChunk iterations instead of the scalars every iteration.  Same
+// kernels, same order and the same tests as lockstep_fcg.
+sipg_status batch_solve_device(sipg_batch *B, const double *const *b, double *const *x, double rtol, int maxit,
+                               sipg_solve_info *infos) {
+  const int np = (int)B->ctx.size();
+  const int st = kSegSlots;
+  cudaStream_t s = B->stream;
+  std::vector<const double *> xu(np);
+  std::vector<double *> rout(np);
+  for (int p = 0; p < np; ++p) {
+    sipg_ctx *c = B->ctx[p];
+    B->segs[p] = Seg{x[p], c->fr, c->fp, c->fv, c->fz, b[p], (long)c->lv[c->L].ndofs, 1};
+    xu[p] = x[p];
+    rout[p] = c->fr;
+  }
+  if (!B->d_app) {   // device state, and the v = A p descriptors (fixed per context)
+    std::vector<BatchProb<double>> app(np);
+    for (int p = 0; p < np; ++p) {
+      sipg_ctx *c = B->ctx[p];
+      app[p].a = dg_args<double>(c, c->lv[c->L]);
+      app[p].a.u = c->fp;
+      app[p].a.out = c->fv;
+      app[p].a.mode = 0;
+      app[p].n = c->lv[c->L].n;
+      app[p].active = 1;
+    }
+    B->d_app = upload_vec(app);
+    CK(cudaMalloc(&B->d_it, np * sizeof(int)));
+    CK(cudaMalloc(&B->d_status, np * sizeof(int)));
+    CK(cudaMalloc(&B->d_any, sizeof(int)));
+    CK(cudaMalloc(&B->d_hist, (size_t)np * 257 * sizeof(double)));
+    CK(cudaMalloc(&B->d_rn, np * sizeof(double)));
+    CK(cudaMalloc(&B->d_r0, np * sizeof(double)));
+    CK(cudaMalloc(&B->d_prm, 2 * sizeof(double)));
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{e0, e1};
+  CK(cudaEventRecord(e0, s));
+  CK(cudaMemcpyAsync(B->d_segs, B->segs.data(), np * sizeof(Seg), cudaMemcpyHostToDevice, s));
+  batch_set_plan(B, 2, xu.data(), rout.data());   // r = b - A x
+  CK(batch_apply(B->plan, s));
+  CK(seg_dot(B->d_segs, B->sg, 0, B->partials, B->counters, B->sc, st, 4, s));
+  batch_precondition(B);
+  CK(seg_dot(B->d_segs, B->sg, 1, B->partials, B->counters, B->sc, st, 0, s));
+  CK(seg_update_p(B->d_segs, B->sg, B->sc, st, 1, s));
+  std::vector<double> hsc((size_t)np * st);
+  CK(cudaMemcpyAsync(hsc.data(), B->sc, hsc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> r0(np);
+  int any = 0;
+  for (int p = 0; p < np; ++p) {
+    if (!std::isfinite(hsc[p * st + 4])) {
+      B->err = "a right-hand side is not finite";
+      return SIPG_ENAN;
+    }
+    r0[p] = std::sqrt(hsc[p * st + 5]);
+    if (r0[p] == 0.0) B->segs[p].active = 0;
+    any |= B->segs[p].active;
+  }
+  const double prm[2] = {rtol, (double)maxit};
+  CK(cudaMemcpyAsync(B->d_segs, B->segs.data(), np * sizeof(Seg), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(B->d_it, 0, np * sizeof(int), s));
+  CK(cudaMemsetAsync(B->d_status, 0, np * sizeof(int), s));
+  CK(cudaMemcpyAsync(B->d_r0, r0.data(), np * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(B->d_rn, r0.data(), np * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(B->d_prm, prm, sizeof(prm), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(B->d_any, &any, sizeof(int), cudaMemcpyHostToDevice, s));
+  int global_it = 0;
+  if (any) {
+    batch_build_fcg_chunk(B);
+    // every chunk that does not end the solve advances all active systems by
+    // kFcgChunk iterations, and the device ends each at maxit
+    const int max_launches = maxit / kFcgChunk + 2;
+    for (int launches = 0;; ++launches) {
+      if (launches >= max_launches) {
+        B->err = "the batched flexible CG on the device made no progress";
+        throw Fail{SIPG_ECUDA};
+      }
+      CK(cudaGraphLaunch(B->fcg_graph, s));
+      note_kernels(B->fcg_k0);
+      int h_any = 0;
+      CK(cudaMemcpyAsync(&h_any, B->d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (!h_any) break;
+    }
+  }
+  std::vector<int> it(np), status(np);
+  std::vector<double> rn(np), hist((size_t)np * 257);
+  CK(cudaMemcpyAsync(it.data(), B->d_it, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(status.data(), B->d_status, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rn.data(), B->d_rn, np * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hist.data(), B->d_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  for (int p = 0; p < np; ++p) global_it = std::max(global_it, it[p]);
+  // kernels of the bodies that ran: the first step of iterations 1..G, the
+  // second of all but the last (G = the most iterations of any system)
+  for (int j = 0; j < global_it; ++j)
+    note_kernels(B->fcg_kA[j % kFcgChunk] + (j + 1 < global_it ? B->fcg_kB[j % kFcgChunk] : 0));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  sipg_status status_all = SIPG_OK;
+  for (int p = 0; p < np; ++p) {
+    if (status[p] == 1) status_all = SIPG_EBREAKDOWN;
+    else if (status[p] == 2 && status_all == SIPG_OK) status_all = SIPG_ENOTCONV;
+  }
+  if (infos)
+    for (int p = 0; p < np; ++p) {
+      sipg_solve_info &I = infos[p];
+      std::memset(&I, 0, sizeof(I));
+      I.iterations = it[p];
+      I.r0_norm = r0[p];
+      I.r_norm = rn[p];
+      I.converged = (r0[p] == 0.0 || rn[p] <= rtol * r0[p]) ? 1 : 0;
+      I.rho = (it[p] > 0 && r0[p] > 0) ? std::pow(rn[p] / r0[p], 1.0 / it[p]) : 0.0;
+      I.n10 = (I.rho > 0 && I.rho < 1) ? -10.0 / std::log10(I.rho) : 0.0;
+      I.seconds = ms * 1e-3;
+      I.res_history[0] = r0[p];
+      const int nh = std::min(status[p] == 1 ? it[p] - 1 : it[p], 255);
+      for (int j = 1; j <= nh; ++j) I.res_history[j] = hist[(size_t)p * 257 + j];
+    }
+  if (status_all == SIPG_EBREAKDOWN) B->err = "flexible CG breakdown in one of the systems solved together";
+  if (status_all == SIPG_ENOTCONV) B->err = "a system reached maxit before the tolerance";
+  return status_all;
+}
+
 sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *const *x, double rtol, int maxit,
                              sipg_solve_info *infos) {
+  batch_cycle_prepare(B);
+  if (B->cyc_state == 1 && maxit > 0) return batch_solve_device(B, b, x, rtol, maxit, infos);
   const int np = (int)B->ctx.size();
   std::vector<const double *> xu(np), pu(np);
   std::vector<double *> rout(np), vout(np);
@@ -2423,7 +3005,7 @@ sipg_status batch_solve_impl(sipg_batch *B, const double *const *b, double *cons
     rout[p] = c->fr;
     vout[p] = c->fv;
   }
-  Lockstep K{B->stream, B->segs, B->d_segs, B->sc, B->partials, B->counters, B->err};
+  Lockstep K{B->stream, B->segs, B->d_segs, B->sg, B->sc, B->partials, B->counters, B->err};
   return lockstep_fcg(
       K,
       [&]() {   // r = b - A x
@@ -2452,6 +3034,7 @@ void ensure_multi(sipg_ctx *c, int nv) {
   M.graph_nv = 0;
   std::vector<void *> old;
   for (void *q : M.v) old.push_back(q);
+  for (void *q : M.sg_allocs) old.push_back(q);
   for (void *q : {M.grad[0], M.grad[1], M.trace[0], M.trace[1], M.ebuf[0], M.ebuf[1], (void *)M.r, (void *)M.z,
                   (void *)M.p, (void *)M.v_, (void *)M.d_segs, (void *)M.sc, (void *)M.partials,
                   (void *)M.counters})
@@ -2493,7 +3076,13 @@ void ensure_multi(sipg_ctx *c, int nv) {
   M.v_ = dalloc<double>(c, N);
   M.d_segs = (Seg *)dalloc<char>(c, (int64_t)(nv * sizeof(Seg)));
   M.sc = dalloc<double>(c, (int64_t)nv * kSegSlots);
-  M.partials = dalloc<double>(c, (int64_t)nv * kSegBlocksHost * 2);
+  {
+    std::vector<void *> al;
+    CK(seg_grid_build(std::vector<long>(nv, (long)c->lv[c->L].ndofs), M.sg, al));
+    for (void *q : al) c->allocs.push_back(q);
+    M.sg_allocs = al;
+  }
+  M.partials = dalloc<double>(c, (int64_t)M.sg.blocks * 2);
   M.counters = dalloc<unsigned>(c, nv);
   CK(cudaMemset(M.counters, 0, nv * sizeof(unsigned)));
   M.cap = nv;
@@ -2516,7 +3105,7 @@ sipg_status solve_multi_impl(sipg_ctx *c, int nrhs, const double *B, double *X, 
   for (int r = 0; r < nrhs; ++r)
     M.segs[r] = Seg{X + r * N, M.r + r * N, M.p + r * N, M.v_ + r * N, M.z + r * N, B + r * N, (long)N, 1};
   c->use_learned = 0;   // the multi-vector cycle smooths with Chebyshev
-  Lockstep K{c->stream, M.segs, M.d_segs, M.sc, M.partials, M.counters, c->err};
+  Lockstep K{c->stream, M.segs, M.d_segs, M.sg, M.sc, M.partials, M.counters, c->err};
   return lockstep_fcg(
       K, [&]() { apply_level<double>(c, c->L, X, M.r, 2, nullptr, nullptr, B); },
       [&]() { apply_level<double>(c, c->L, M.p, M.v_, 0); }, [&]() { precondition(c); }, rtol, maxit, infos);
@@ -2625,10 +3214,14 @@ sipg_status sipg_batch_create(int nprob, const sipg_mesh *meshes, const sipg_par
       B->segs.assign(nprob, Seg{});
       CK(cudaMalloc(&B->d_segs, nprob * sizeof(Seg)));
       CK(cudaMalloc(&B->sc, (size_t)nprob * kSegSlots * sizeof(double)));
-      CK(cudaMalloc(&B->partials, (size_t)nprob * kSegBlocksHost * 2 * sizeof(double)));
+      std::vector<long> sizes;
+      for (auto *c : B->ctx) sizes.push_back((long)c->lv[c->L].ndofs);
+      CK(seg_grid_build(sizes, B->sg, B->sg_allocs));
+      CK(cudaMalloc(&B->partials, (size_t)B->sg.blocks * 2 * sizeof(double)));
       CK(cudaMalloc(&B->counters, (size_t)nprob * sizeof(unsigned)));
       CK(cudaMemset(B->counters, 0, (size_t)nprob * sizeof(unsigned)));
       CK(cudaEventCreateWithFlags(&B->ev_start, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&B->ev_branch, cudaEventDisableTiming));
       B->ev_done.resize(nprob);
       for (auto &e : B->ev_done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       CK(cudaDeviceSynchronize());
@@ -2664,6 +3257,29 @@ sipg_status sipg_batch_apply(sipg_batch *B, const double *const *u, double *cons
     for (size_t p = 0; p < B->ctx.size(); ++p) B->segs[p].active = 1;
     batch_set_plan(B, 0, u, v);
     CK(batch_apply(B->plan, B->stream));
+    return SIPG_OK;
+  });
+}
+
+sipg_status sipg_batch_vcycle(sipg_batch *B, const double *const *r, double *const *z) {
+  if (!B || !r || !z) return SIPG_EINVAL;
+  for (size_t p = 0; p < B->ctx.size(); ++p)
+    if (!r[p] || !z[p]) return SIPG_EINVAL;
+  return bguarded(B, [&]() -> sipg_status {
+    batch_cycle_prepare(B);
+    cudaStream_t s = B->stream;
+    for (size_t p = 0; p < B->ctx.size(); ++p) {
+      sipg_ctx *c = B->ctx[p];
+      B->segs[p] = Seg{nullptr, c->fr, nullptr, nullptr, c->fz, nullptr, (long)c->lv[c->L].ndofs, 1};
+      CK(cudaMemcpyAsync(c->fr, r[p], c->lv[c->L].ndofs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaMemcpyAsync(B->d_segs, B->segs.data(), B->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, s));
+    batch_precondition(B);
+    for (size_t p = 0; p < B->ctx.size(); ++p) {
+      sipg_ctx *c = B->ctx[p];
+      CK(cudaMemcpyAsync(z[p], c->fz, c->lv[c->L].ndofs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
     return SIPG_OK;
   });
 }

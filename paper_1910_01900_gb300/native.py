@@ -21,7 +21,7 @@ EXPORTS = [
     "sipg_level_apply", "sipg_inverse_diagonal", "sipg_smooth", "sipg_restrict", "sipg_prolongate_add",
     "sipg_coarse_solve", "sipg_coarse_info", "sipg_coarse_amg_vcycle", "sipg_vcycle", "sipg_solve", "sipg_solve_host", "sipg_time_apply", "sipg_fma_peak",
     "sipg_operator_apply_noalloc", "sipg_launch_count", "sipg_batch_create", "sipg_batch_destroy",
-    "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_solve", "sipg_tile_shape", "sipg_set_tile_shape", "sipg_solve_multi",
+    "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_vcycle", "sipg_batch_solve", "sipg_tile_shape", "sipg_set_tile_shape", "sipg_solve_multi",
     "sipg_operator_apply_multi",
     "sipg_smoother_train", "sipg_set_smoother", "sipg_mlp_shape", "sipg_mlp_params", "sipg_mlp_forward",
     "sipg_mlp_gradients", "sipg_mlp_features", "sipg_l2_error",
@@ -127,6 +127,7 @@ def lib():
         L.sipg_batch_last_error.restype = ctypes.c_char_p
         L.sipg_batch_context.argtypes = [vp, i32, ctypes.POINTER(vp)]
         L.sipg_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.sipg_batch_vcycle.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
         L.sipg_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32, ctypes.POINTER(SolveInfo)]
         L.sipg_operator_apply_noalloc.argtypes = [ctypes.POINTER(Mesh), i32, dbl, vp, vp, vp]
         for name in EXPORTS:
@@ -542,12 +543,21 @@ class Batch:
         V = (ctypes.c_void_p * self.n)(*[_ptr(v, torch.float64, self.num_dofs(i)).value for i, v in enumerate(vs)])
         self._check(lib().sipg_batch_apply(self.h, U, V))
 
-    def solve(self, bs, xs, rtol=1e-10, maxit=200):
+    def vcycle(self, rs, zs):
+        """zs[i] = M_i^-1 rs[i]: one V-cycle of every problem (FP64 device vectors)."""
+        import torch
+        R = (ctypes.c_void_p * self.n)(*[_ptr(r, torch.float64, self.num_dofs(i)).value for i, r in enumerate(rs)])
+        Z = (ctypes.c_void_p * self.n)(*[_ptr(z, torch.float64, self.num_dofs(i)).value for i, z in enumerate(zs)])
+        self._check(lib().sipg_batch_vcycle(self.h, R, Z))
+
+    def solve(self, bs, xs, rtol=1e-10, maxit=200, allow_notconv=False):
         import torch
         B = (ctypes.c_void_p * self.n)(*[_ptr(b, torch.float64, self.num_dofs(i)).value for i, b in enumerate(bs)])
         X = (ctypes.c_void_p * self.n)(*[_ptr(x, torch.float64, self.num_dofs(i)).value for i, x in enumerate(xs)])
         infos = (SolveInfo * self.n)()
-        self._check(lib().sipg_batch_solve(self.h, B, X, float(rtol), int(maxit), infos))
+        st = lib().sipg_batch_solve(self.h, B, X, float(rtol), int(maxit), infos)
+        if not (allow_notconv and st == ENOTCONV):
+            self._check(st)
         return list(infos)
 
     def close(self):

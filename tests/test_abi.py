@@ -130,6 +130,7 @@ def test_null_handles_and_bad_arguments_are_rejected_before_device_work(lib):
         "sipg_batch_destroy": (N,),
         "sipg_batch_context": (N, 0, N),
         "sipg_batch_apply": (N, N, N),
+        "sipg_batch_vcycle": (N, N, N),
         "sipg_batch_solve": (N, N, N, 1e-10, 10, N),
         "sipg_operator_apply_noalloc": (N, 3, 1.0, N, N, N),
     }

@@ -112,20 +112,23 @@ def test_levels_diagonals_and_fe_apply(m, k, deform):
             assert close(d.cpu().numpy(), lev.dinv) <= 1e-12
 
 
+@pytest.mark.parametrize("k,fa", [(4, 2), (3, 3)])
 @pytest.mark.parametrize("deform,bc", [(1, (0, 1, 0, 0, 1, 0)), (0, (1, 1, 0, 1, 1, 1))])
-def test_assembled_low_degree_levels_match_matrix_free(deform, bc):
-    """FE levels of degree 1 (by default) and 2 (fe_assemble=2) apply an assembled stencil:
-    the same operator as the matrix-free cell and node passes and as the oracle's FE matrix,
-    with Dirichlet and Neumann sides mixed (identity rows and zero columns only on Dirichlet
-    nodes)."""
-    m, k = 6, 4   # DG4, FE4, FE2 (assembled), FE1 6^3 (assembled), FE1 3^3 (coarse)
-    ctx_a = _ctx(m, k, deform=deform, bc=bc, lambda_override=2.0, fe_assemble=2)
+def test_assembled_low_degree_levels_match_matrix_free(deform, bc, k, fa):
+    """FE levels of degree 1 (by default) and up to fa (fe_assemble=fa: 125 points at degree
+    2, 343 at degree 3) apply an assembled stencil: the same operator as the matrix-free cell
+    and node passes and as the oracle's FE matrix, with Dirichlet and Neumann sides mixed
+    (identity rows and zero columns only on Dirichlet nodes)."""
+    # k = 4: DG4, FE4, FE2 (assembled), FE1 6^3 (assembled), FE1 3^3 (coarse)
+    # k = 3: DG3, FE3 (assembled), FE1 6^3 (assembled), FE1 3^3 (coarse)
+    m = 6
+    ctx_a = _ctx(m, k, deform=deform, bc=bc, lambda_override=2.0, fe_assemble=fa)
     ctx_f = _ctx(m, k, deform=deform, bc=bc, lambda_override=2.0, fe_assemble=0)
     mg = CPHMultigrid(Mesh(m, deform=deform, bc=bc), k, lambdas=[2.0] * 16)
     checked = 0
     for l in range(1, len(mg.levels)):
         lev = mg.levels[l]
-        if lev.kind != "fe" or lev.space.p > 2:
+        if lev.kind != "fe" or lev.space.p > fa:
             continue
         u = sipg_inputs.uniform(lev.n, 500 + l)
         u[lev.space.constrained] *= -3.0
