@@ -374,7 +374,9 @@ typedef struct {
  * taken from x = 0. */
 sipg_status sipg_smoother_train(sipg_ctx *ctx, int npairs, int epochs, uint64_t seed, sipg_train_info *info);
 /* which = 0: Chebyshev (default); 1: learned (trained network required), with
- * steps_pre and steps_post network steps around the coarse correction;
+ * steps_pre and steps_post network steps around the coarse correction; 2: the
+ * same learned cycle without the Chebyshev fallback (to measure the network
+ * alone: the flexible CG still returns a correct result, or stops at maxit);
  * steps_pre = 0 keeps Chebyshev pre-smoothing (the network is trained on the
  * post-smoothing state), 1..16 network steps; steps_post 0..16, where 0
  * leaves the finest level without post-smoothing (the cycle without the

@@ -96,7 +96,7 @@ struct sipg_ctx {
     cudaGraphExec_t graph = nullptr;           // V-cycle of graph_nv vectors
     int graph_nv = 0, calls = 0;
   } mv;
-  int smoother = 0;          // 0 Chebyshev, 1 learned (finest level)
+  int smoother = 0;          // 0 Chebyshev, 1 learned (finest level), 2 learned without fallback
   int use_learned = 0;       // current cycle uses the learned smoother
   cudaGraphExec_t vgraph_l[2] = {nullptr, nullptr};   // graphs of the learned cycle
   int vcalls_l[2] = {0, 0};
@@ -1174,7 +1174,7 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
   }
   const double r0 = std::sqrt(dot(c, c->fr, c->fr, N, 3));
   std::vector<double> hist{r0};
-  c->use_learned = (c->smoother == 1 && c->net.trained) ? 1 : 0;
+  c->use_learned = (c->smoother >= 1 && c->net.trained) ? 1 : 0;
   const int learned_at_start = c->use_learned;
   precondition(c);
   CK(launch_dot2(c->fr, c->fz, nullptr, nullptr, N, c->partials, c->counter, c->scal + 0, s));
@@ -1278,7 +1278,7 @@ sipg_status solve_impl(sipg_ctx *c, const double *b, double *x, double rtol, int
     const double tr = (c->net.t_iter_cheb > 0 && c->net.t_iter_learned > 0)
                           ? c->net.t_iter_learned / c->net.t_iter_cheb
                           : 1.0;
-    if (c->use_learned && rn > std::pow(c->net.rho_cheb, tr) * rprev) {
+    if (c->use_learned && c->smoother == 1 && rn > std::pow(c->net.rho_cheb, tr) * rprev) {
       c->use_learned = 0;
       fell_back = 1;
     }
@@ -2010,7 +2010,7 @@ sipg_status sipg_coarse_amg_vcycle(sipg_ctx *c, const double *b, double *x) {
 sipg_status sipg_vcycle(sipg_ctx *c, const double *r, double *z) {
   if (!c || !r || !z || !c->solver) return SIPG_EINVAL;
   return guarded(c, [&]() -> sipg_status {
-    c->use_learned = (c->smoother == 1 && c->net.trained) ? 1 : 0;
+    c->use_learned = (c->smoother >= 1 && c->net.trained) ? 1 : 0;
     vcycle_fp64io(c, r, z);
     c->use_learned = 0;
     return SIPG_OK;
@@ -2132,9 +2132,9 @@ sipg_status sipg_smoother_train(sipg_ctx *c, int npairs, int epochs, uint64_t se
 }
 
 sipg_status sipg_set_smoother(sipg_ctx *c, int which, int steps_pre, int steps_post) {
-  if (!c || which < 0 || which > 1 || steps_pre < 0 || steps_post < 0 || steps_pre > 16 || steps_post > 16)
+  if (!c || which < 0 || which > 2 || steps_pre < 0 || steps_post < 0 || steps_pre > 16 || steps_post > 16)
     return SIPG_EINVAL;
-  if (which == 1 && !c->net.trained) {
+  if (which >= 1 && !c->net.trained) {
     c->err = "the learned smoother has not been trained (sipg_smoother_train)";
     return SIPG_EINVAL;
   }
@@ -2150,7 +2150,7 @@ sipg_status sipg_set_smoother(sipg_ctx *c, int which, int steps_pre, int steps_p
   const bool changed = c->net.steps_pre != steps_pre || c->net.steps_post != steps_post;
   c->net.steps_pre = steps_pre;
   c->net.steps_post = steps_post;
-  if (which == 1 && changed)   // the fallback test compares time per iteration
+  if (which >= 1 && changed)   // the fallback test compares time per iteration
     return guarded(c, [&]() -> sipg_status {
       c->net.t_iter_learned = iteration_ms(c, 1);
       return SIPG_OK;
