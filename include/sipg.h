@@ -121,15 +121,16 @@ typedef struct {
                               blocks leaves the fewest cell slots idle;
                               cached per (degree, geometry, cells) for the
                               process                                      */
-  int fe_assemble;         /* FE levels of degree <= fe_assemble (0, 1 or 2;
+  int fe_assemble;         /* FE levels of degree <= fe_assemble (0..3;
                               default 1) apply an assembled (2p+1)^3-point
                               stencil built at setup from the same element
                               integrals instead of the matrix-free cell and
                               node passes (27 points at degree 1: one
                               node-centric launch instead of two); 0 = all
-                              levels matrix-free.  Degree 2 (125 points) is
-                              slower than matrix-free on GB300 and is kept
-                              for comparison only                          */
+                              levels matrix-free.  Degrees 2 and 3 (125 and
+                              343 points) are slower than matrix-free on
+                              GB300 except on the smallest meshes and are
+                              kept for comparison only                     */
   int coarse_dense_max;    /* coarsest level solved by a dense inverse up to
                               this many unknowns (default 2197 = 13^3 nodes:
                               every mesh whose sizes halve down to <= 12
@@ -373,6 +374,20 @@ typedef struct {
  * c is multiplied by the omega minimising ||r - omega A d|| for the step d
  * taken from x = 0. */
 sipg_status sipg_smoother_train(sipg_ctx *ctx, int npairs, int epochs, uint64_t seed, sipg_train_info *info);
+/* Fine-tune the trained network in the energy norm (not in the paper): on
+ * the full-mesh snapshots kept by sipg_smoother_train (residual r and error e
+ * of the state the post-smoother starts from; 16 of them) minimise
+ * ||e - d||_A^2 / ||e||_A^2 for the step d = c s net(features(r)) of all cells
+ * (its gradient -2 (r - A d) / e.r: one operator application per step), Adam
+ * with learning rate lr (0: 3e-4), `epochs` passes over the snapshots; the
+ * Adam moments restart at every call, so calls accumulate passes; then damp the
+ * step by the energy-optimal omega = d.r / d.A d on the last snapshot.  info
+ * (may be NULL): loss before/after (mean over the snapshots of the first and
+ * the last pass), steps, seconds, damping.  EINVAL before training, for
+ * epochs outside 1..100000 or lr outside [0, 1]; ENAN if the loss stops being
+ * finite. */
+sipg_status sipg_smoother_finetune(sipg_ctx *ctx, int epochs, double lr, sipg_train_info *info);
+
 /* which = 0: Chebyshev (default); 1: learned (trained network required), with
  * steps_pre and steps_post network steps around the coarse correction; 2: the
  * same learned cycle without the Chebyshev fallback (to measure the network

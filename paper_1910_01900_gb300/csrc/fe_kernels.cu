@@ -49,6 +49,52 @@ __device__ __forceinline__ void fe_cell_body(const FEArgs<T> &a, const T *__rest
     sm[c * Tile<N>::CS + Tile<N>::idx(p)] = node_constrained(g, a.grid, a.bc) ? T(0) : ug[gi];
   }
   __syncthreads();
+  if constexpr (!CURVED) {
+    // An axis-aligned box cell: its matrix is the sum over d of alpha_d times
+    // the tensor product of the 1D stiffness matrix K1 in direction d and the
+    // 1D mass matrix M1 in the other two (both under the Gauss rule, as the
+    // interpolate / differentiate / weight / transpose sweeps below compute
+    // it), so y = ax K1 M1 M1 u + ay M1 K1 M1 u + az M1 M1 K1 u takes 7 1D
+    // products instead of 12: along x a = M1 u, b = K1 u; along y c = M1 a,
+    // f = ay K1 a + ax M1 b; along z y = az K1 c + M1 f.
+    T *t0 = su, *t1 = su + TT;
+    int base, stride;
+    if (act) {
+      line_of<N>(0, l, base, stride);
+      T x[N], y[N];
+      load_line<T, N>(t0, base, stride, x);
+      apply_mat<T, N, MK1>(x, y);
+      store_line<T, N>(t1, base, stride, y);
+      apply_mat<T, N, MM1>(x, y);
+      store_line<T, N>(t0, base, stride, y);
+    }
+    __syncthreads();
+    if (act) {
+      line_of<N>(1, l, base, stride);
+      T x[N], y[N], k[N];
+      load_line<T, N>(t0, base, stride, x);
+      apply_mat<T, N, MM1>(x, y);
+      store_line<T, N>(t0, base, stride, y);
+      apply_mat<T, N, MK1>(x, k);
+      load_line<T, N>(t1, base, stride, x);
+      apply_mat<T, N, MM1>(x, y);
+#pragma unroll
+      for (int q = 0; q < N; ++q) y[q] = fma(a.alpha[1], k[q], a.alpha[0] * y[q]);
+      store_line<T, N>(t1, base, stride, y);
+    }
+    __syncthreads();
+    if (!act) return;
+    line_of<N>(2, l, base, stride);
+    T x[N], y[N], k[N];
+    load_line<T, N>(t0, base, stride, x);
+    apply_mat<T, N, MK1>(x, k);
+    load_line<T, N>(t1, base, stride, x);
+    apply_mat<T, N, MM1>(x, y);
+    T *eb = ebv + (size_t)(cell0 + cl) * N3 + l;
+#pragma unroll
+    for (int q = 0; q < N; ++q) eb[q * N2] = fma(a.alpha[2], k[q], y[q]);
+    return;
+  }
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     if (act) sweep_inplace<T, N, MS>(su, d, l);

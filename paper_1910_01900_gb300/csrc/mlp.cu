@@ -664,6 +664,19 @@ __global__ void mse_grad_kernel(const float *Y, const float *Tg, long ldt, int B
   dYf[i] = d / B;
 }
 
+// output errors of the energy-norm objective: row e (a cell), column q < n3:
+// factor * c * s_e * g[e n3 + q] (the chain rule through the step
+// d_e = c s_e y_e), zero in the padding columns
+__global__ void energy_grad_kernel(const double *g, int n3, int E, const float *scale, float cs, double factor,
+                                   int ld, __nv_bfloat16 *dY, float *dYf) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)E * ld) return;
+  const int r = (int)(i / ld), q = (int)(i - (long)r * ld);
+  const float d = q < n3 ? (float)(factor * (double)cs * (double)scale[r] * g[(size_t)r * n3 + q]) : 0.f;
+  dY[i] = __float2bfloat16(d);
+  dYf[i] = d;
+}
+
 // dH = dH * (H > 0) in place (bf16)
 __global__ void relu_mask_kernel(__nv_bfloat16 *dH, const __nv_bfloat16 *H, long n) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -912,6 +925,13 @@ template cudaError_t mlp_correct<double>(double *, int, int, int, const float *,
 cudaError_t mlp_mse_grad(const float *Y, const float *Tg, long ldt, int B, int N, int ld, void *dY, float *dYf,
                          double *loss, cudaStream_t s) {
   mse_grad_kernel<<<blocks((long)B * ld), 256, 0, s>>>(Y, Tg, ldt, B, N, ld, (__nv_bfloat16 *)dY, dYf, loss);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t mlp_energy_grad(const double *g, int n3, int E, const float *scale, float cs, double factor, int ld,
+                            void *dY, float *dYf, cudaStream_t s) {
+  if (E <= 0) return cudaSuccess;
+  energy_grad_kernel<<<blocks((long)E * ld), 256, 0, s>>>(g, n3, E, scale, cs, factor, ld, (__nv_bfloat16 *)dY, dYf);
   note_launch();
   return cudaGetLastError();
 }

@@ -188,6 +188,20 @@ void build_tables(Tables<T> &t) {
     put(St, +1, t.StE[n], t.StO[n]);
     put(r.D, -1, t.DE[n], t.DO[n]);
     put(Dt, -1, t.DtE[n], t.DtO[n]);
+    std::vector<double> M1(n * n, 0.0), K1(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        for (int q = 0; q < n; ++q) {
+          M1[i * n + j] += r.wq[q] * r.S[q * n + i] * r.S[q * n + j];
+          K1[i * n + j] += r.wq[q] * r.Sd[q * n + i] * r.Sd[q * n + j];
+        }
+    if (n <= 4)
+      for (int i = 0; i < n * n; ++i) {
+        t.M1[n][i] = (T)M1[i];
+        t.K1[n][i] = (T)K1[i];
+      }
+    put(M1, +1, t.M1E[n], t.M1O[n]);
+    put(K1, +1, t.K1E[n], t.K1O[n]);
     for (int q = 0; q < n; ++q) {
       t.l0[n][q] = (T)r.l0[q];
       t.l1[n][q] = (T)r.l1[q];

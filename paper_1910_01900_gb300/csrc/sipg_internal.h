@@ -44,6 +44,11 @@ struct Tables {
   // extrapolation vectors (a face's normal-derivative test term enters the
   // integrated tile through these directly)
   T dl0[kMaxN + 1][kMaxN], dl1[kMaxN + 1][kMaxN];
+  // 1D mass and stiffness matrices of the GL basis under the Gauss rule,
+  // M1[i][j] = sum_q w_q l_i(x_q) l_j(x_q), K1[i][j] = sum_q w_q l_i'(x_q) l_j'(x_q)
+  // (both M[i][j] = M[n-1-i][n-1-j]): the factors of the Cartesian FE cell matrix
+  T M1[kMaxN + 1][16], K1[kMaxN + 1][16];
+  T M1E[kMaxN + 1][25], M1O[kMaxN + 1][20], K1E[kMaxN + 1][25], K1O[kMaxN + 1][20];
 };
 template <typename T>
 void build_tables(Tables<T> &t);
@@ -102,6 +107,7 @@ struct FEArgs {
                        //         4 diagonal (sum, constrained -> 1)
   const T *x, *xp, *b, *dinv;
   T c1, c2, c3;
+  T alpha[3];          // Cartesian: prod(h) / h_d^2, the scale of direction d's term
   // nv vectors at once: vector r of u, out, x, xp, b starts at r * vs, its
   // element buffer at r * es
   int nv = 1;
@@ -379,6 +385,9 @@ cudaError_t mlp_correct(T *x, int n3, int c0, int nc, const float *Y, int ldy, c
 cudaError_t mlp_mse_grad(const float *Y, const float *Tg, long ldt, int B, int N, int ld, void *dY, float *dYf,
                          double *loss, cudaStream_t s);
 cudaError_t mlp_relu_mask(void *dH, const void *H, long n, cudaStream_t s);
+// output errors of the energy-norm objective from g = dL/dd (DG vector) through d_e = cs s_e y_e
+cudaError_t mlp_energy_grad(const double *g, int n3, int E, const float *scale, float cs, double factor, int ld,
+                            void *dY, float *dYf, cudaStream_t s);
 cudaError_t mlp_colsum(const void *D, int bf16, int B, int N, int ld, float *g, cudaStream_t s);
 cudaError_t mlp_adam(float *p, float *m, float *v, const float *g, long n, float lr, int step, void *pb,
                      cudaStream_t s);

@@ -76,6 +76,10 @@ struct sipg_ctx {
     double omega = 1;       // damping applied to the trained output scale
     double step_reduction = 1;   // residual reduction of one damped step on that data
     int steps_pre = 0, steps_post = 1;   // Chebyshev pre-smoothing, one network post-step
+    // full-mesh snapshots of the training data (residual, error of the state
+    // the post-smoother starts from), kept for the energy-norm fine-tuning
+    int nsnap = 0;
+    double *snap_r = nullptr, *snap_e = nullptr;
   } net;
   // Several right-hand sides at once (sipg_solve_multi, sipg_operator_apply_multi):
   // nv vectors of every level's V-cycle data and of the cell-kernel scratch,
@@ -236,6 +240,7 @@ FEArgs<T> fe_args(sipg_ctx *c, const Level &L) {
   for (int d = 0; d < 3; ++d) {
     a.m[d] = L.m[d];
     a.grid[d] = L.grid[d];
+    a.alpha[d] = (T)(L.h[0] * L.h[1] * L.h[2] / (L.h[d] * L.h[d]));
   }
   for (int s = 0; s < 6; ++s) a.bc[s] = c->mesh.bc[s];
   return a;
@@ -1431,11 +1436,20 @@ void net_forward(sipg_ctx *c, const void *X, long ldx, int B, bool keep_hidden =
 }
 
 // gradients of the mean squared error over B rows (X row stride ldx, T row stride ldt) into N.G
+void net_backward(sipg_ctx *c, const void *X, long ldx, int B);
+
 void net_gradients(sipg_ctx *c, const void *X, long ldx, const float *T, long ldt, int B) {
   auto &N = c->net;
-  cudaStream_t s = c->stream;
   net_forward(c, X, ldx, B);
-  CK(mlp_mse_grad(N.Y, T, ldt, B, N.n3, N.No, N.dY, N.dYf, N.loss, s));
+  CK(mlp_mse_grad(N.Y, T, ldt, B, N.n3, N.No, N.dY, N.dYf, N.loss, c->stream));
+  net_backward(c, X, ldx, B);
+}
+
+// gradients into N.G from the output errors in N.dY (BF16) and N.dYf (FP32)
+// of the last forward pass over B rows of X
+void net_backward(sipg_ctx *c, const void *X, long ldx, int B) {
+  auto &N = c->net;
+  cudaStream_t s = c->stream;
   if (N.No <= 256) {
     // every product on the tcgen05 tensor cores: the back-propagated errors
     // dY W3^T and dH W2^T read the stored weights as K-contiguous operands;
@@ -1553,6 +1567,11 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
   c->smoother = 0;
   double *bv = dalloc<double>(c, Nd), *xv = dalloc<double>(c, Nd), *xx = dalloc<double>(c, Nd),
          *xt2 = dalloc<double>(c, Nd);
+  if (N.nsnap != S * J) {
+    N.snap_r = dalloc<double>(c, (int64_t)S * J * Nd);
+    N.snap_e = dalloc<double>(c, (int64_t)S * J * Nd);
+    N.nsnap = S * J;
+  }
   long row = 0;
   auto add_pairs = [&](const double *res, const double *err, long cnt) {
     CK(mlp_gather<double>(res, F.n, F.m, cells, (int)row, (int)cnt, bfm(Xall, row * N.Fp), N.Fp, sall + row,
@@ -1597,6 +1616,9 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
       CK(cudaMemcpyAsync(e, xv, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       CK(launch_axpy<double>(e, -1.0, x, Nd, c->stream));
       add_pairs(r, e, cnt);
+      const int64_t so = (int64_t)(sidx * J + j) * Nd;
+      CK(cudaMemcpyAsync(N.snap_r + so, r, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(N.snap_e + so, e, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       if (sidx == S - 1 && j == J - 1)   // kept for the damping below
         CK(cudaMemcpyAsync(bv, r, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -1687,6 +1709,87 @@ sipg_status train_impl(sipg_ctx *c, int npairs, int epochs, uint64_t seed, sipg_
     info->iter_ms_learned = N.t_iter_learned;
     info->damping = N.omega;
     info->step_reduction = N.step_reduction;
+  }
+  return SIPG_OK;
+}
+
+// Energy-norm fine-tuning of the trained network on the full-mesh
+// snapshots of training: for a snapshot's residual r and error e (A e = r)
+// the step of all cells is d = c s net(features(r)) and the loss
+// ||e - d||_A^2 / ||e||_A^2 = (e - d).(r - A d) / e.r; its gradient with
+// respect to d is -2 (r - A d) / e.r, one operator application per step (the
+// 2-norm training target e of one cell leaves what the step does to its
+// neighbours' residuals out; this loss sees it).  Adam (learning rate lr) over
+// all cells of one snapshot per step, `epochs` passes over the snapshots; then
+// the step is damped by the energy-optimal omega = d.r / d.A d on the last
+// snapshot.
+sipg_status finetune_impl(sipg_ctx *c, int epochs, float lr, sipg_train_info *info) {
+  auto t0 = std::chrono::steady_clock::now();
+  auto &N = c->net;
+  const Level &F = c->lv[c->L];
+  const int E = (int)F.ncells;
+  const int64_t Nd = F.ndofs;
+  net_setup(c, std::max<long>(E, 256));
+  double *d = dalloc<double>(c, Nd), *ad = dalloc<double>(c, Nd), *rp = dalloc<double>(c, Nd),
+         *ep = dalloc<double>(c, Nd);
+  double loss_first = 0, loss_last = 0;
+  int step = 0;
+  // Adam moments restart for the new objective
+  CK(cudaMemsetAsync(N.M, 0, N.np * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(N.V, 0, N.np * sizeof(float), c->stream));
+  auto take_step = [&](int k) {   // d, A d, r' = r - A d, e' = e - d for snapshot k
+    const double *r = N.snap_r + (int64_t)k * Nd;
+    CK(mlp_gather<double>(r, F.n, F.m, nullptr, 0, E, N.X, N.Fp, N.scale, c->stream));
+    net_forward(c, N.X, N.Fp, E, true);
+    CK(cudaMemsetAsync(d, 0, Nd * sizeof(double), c->stream));
+    CK(mlp_correct<double>(d, N.n3, 0, E, N.Y, N.No, N.scale, N.cscale, c->stream));
+    apply_level<double>(c, c->L, d, ad, 0);
+    CK(cudaMemcpyAsync(rp, r, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_axpy<double>(rp, -1.0, ad, Nd, c->stream));
+    CK(cudaMemcpyAsync(ep, N.snap_e + (int64_t)k * Nd, Nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_axpy<double>(ep, -1.0, d, Nd, c->stream));
+  };
+  for (int ep_i = 0; ep_i < epochs; ++ep_i) {
+    double lsum = 0;
+    for (int k = 0; k < N.nsnap; ++k) {
+      take_step(k);
+      const double er = dot(c, N.snap_e + (int64_t)k * Nd, N.snap_r + (int64_t)k * Nd, Nd, 11);
+      const double l = dot(c, ep, rp, Nd, 12) / er;
+      lsum += l;
+      CK(mlp_energy_grad(rp, N.n3, E, N.scale, N.cscale, -2.0 / er, N.No, N.dY, N.dYf, c->stream));
+      net_backward(c, N.X, N.Fp, E);
+      ++step;
+      CK(mlp_adam(N.P, N.M, N.V, N.G, N.np, lr, step, N.Pb, c->stream));
+      net_weights_updated(c);
+    }
+    lsum /= N.nsnap;
+    if (!std::isfinite(lsum)) {
+      c->err = "energy-norm fine-tuning diverged (non-finite loss) at epoch " + std::to_string(ep_i);
+      return SIPG_ENAN;
+    }
+    if (ep_i == 0) loss_first = lsum;
+    loss_last = lsum;
+  }
+  // energy-optimal damping on the last snapshot
+  take_step(N.nsnap - 1);
+  const double *r = N.snap_r + (int64_t)(N.nsnap - 1) * Nd;
+  const double dr = dot(c, d, r, Nd, 11), dad = dot(c, d, ad, Nd, 12);
+  const double omega = (dad > 0 && std::isfinite(dr / dad)) ? dr / dad : 0.0;
+  N.cscale = (float)(N.cscale * std::max(0.0, omega));
+  N.omega = omega;
+  N.t_iter_learned = iteration_ms(c, 1);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->epochs = epochs;
+    info->steps = step;
+    info->loss_first = loss_first;
+    info->loss_last = loss_last;
+    info->out_scale = N.cscale;
+    info->cheb_rate = N.rho_cheb;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->iter_ms_chebyshev = N.t_iter_cheb;
+    info->iter_ms_learned = N.t_iter_learned;
+    info->damping = omega;
   }
   return SIPG_OK;
 }
@@ -2128,6 +2231,19 @@ sipg_status sipg_smoother_train(sipg_ctx *c, int npairs, int epochs, uint64_t se
     const sipg_status st = train_impl(c, npairs, epochs, seed, info);
     const sipg_status tc = tc_check(c);
     return st != SIPG_OK ? st : tc;
+  });
+}
+
+sipg_status sipg_smoother_finetune(sipg_ctx *c, int epochs, double lr, sipg_train_info *info) {
+  if (!c || epochs < 1 || epochs > 100000 || !c->solver || !(lr >= 0.0) || lr > 1.0) return SIPG_EINVAL;
+  if (!c->net.trained || c->net.nsnap < 1) {
+    c->err = "the learned smoother has not been trained (sipg_smoother_train)";
+    return SIPG_EINVAL;
+  }
+  return guarded(c, [&]() -> sipg_status {
+    const sipg_status st = finetune_impl(c, epochs, lr > 0 ? (float)lr : 3e-4f, info);
+    if (st == SIPG_OK) return tc_check(c);
+    return st;
   });
 }
 

@@ -11,7 +11,10 @@ reports iterations, time (CUDA events on the library stream, median of 3
 after one warm-up), whether the Chebyshev rate test switched the solve back
 to Chebyshev (fell_back), and what one learned cycle leaves of the energy-
 norm error of x* = A^-1 r (as learned_gain); each learned cycle runs with
-the fallback and without it (smoother 2: the network alone, maxit 100).  Chebyshev(d, d) cycles for d =
+the fallback and without it (smoother 2: the network alone, maxit 100).
+One budget's network is then fine-tuned in the energy norm (cumulative 50,
+200, 500 and 1000 passes over the training snapshots, learning rate 3e-4)
+and measured again after each stage.  Chebyshev(d, d) cycles for d =
 1, 2, 3, 5 on the same problem give the reference: the network replaces
 smoothing steps, so it has to beat the cheaper Chebyshev cycles too.  One
 JSON line per row.
@@ -28,6 +31,9 @@ import sipg_inputs  # noqa: E402  (seeded input generators)
 
 BUDGETS = [(25000, 20), (100000, 20), (100000, 60), (300000, 20)]
 CYCLES = [(0, 1), (0, 2), (0, 3), (1, 1), (2, 2)]
+# energy-norm fine-tuning (sipg_smoother_finetune) of one budget's network,
+# passes added at each row (cumulative 50, 200, 500, 1000)
+FINETUNE_BUDGET = (100000, 20)
 
 
 def main(argv=None):
@@ -35,6 +41,8 @@ def main(argv=None):
     ap.add_argument("--m", type=int, default=32)
     ap.add_argument("--k", type=int, default=4)
     ap.add_argument("--repeats", type=int, default=3)
+    ap.add_argument("--finetune-passes", type=int, nargs="*", default=[50, 150, 300, 500])
+    ap.add_argument("--finetune-lr", type=float, default=3e-4)
     args = ap.parse_args(argv)
     import torch
 
@@ -92,17 +100,25 @@ def main(argv=None):
         with torch.cuda.stream(s):
             ctx = Context(args.m, args.k, deform=1, precision=1, stream=s)
             t = ctx.train_smoother(npairs=npairs, epochs=epochs, seed=2024)
-        for pre, post in CYCLES:
-            for which in (1, 2):   # with and without the Chebyshev fallback
-                ctx.set_smoother(which, pre, post)
-                ms, info = timed_solve(ctx, b)
-                print(json.dumps({"cycle": "learned pre %d post %d" % (pre, post), "fallback": which == 1,
-                                  "pairs": npairs, "epochs": epochs, "train_s": round(t.seconds, 2),
-                                  "loss": [round(t.loss_first, 3), round(t.loss_last, 3)],
-                                  "damping": round(t.damping, 3), "iterations": info.iterations,
-                                  "ms": round(ms, 3), "converged": bool(info.converged),
-                                  "fell_back": bool(info.fell_back),
-                                  "energy_error_left": energy_left(ctx, r, xs, e0)}), flush=True)
+        tuned = 0
+        for extra in ([0] + args.finetune_passes if (npairs, epochs) == FINETUNE_BUDGET else (0,)):
+            if extra:   # energy-norm fine-tuning on top (cumulative passes)
+                with torch.cuda.stream(s):
+                    t = ctx.finetune_smoother(epochs=extra, lr=args.finetune_lr)
+                s.synchronize()
+                tuned += extra
+            for pre, post in (CYCLES if not tuned else CYCLES[:2]):
+                for which in (1, 2):   # with and without the Chebyshev fallback
+                    ctx.set_smoother(which, pre, post)
+                    ms, info = timed_solve(ctx, b)
+                    print(json.dumps({"cycle": "learned pre %d post %d" % (pre, post), "fallback": which == 1,
+                                      "pairs": npairs, "epochs": epochs, "energy_passes": tuned,
+                                      "train_s": round(t.seconds, 2),
+                                      "loss": [round(t.loss_first, 4), round(t.loss_last, 4)],
+                                      "damping": round(t.damping, 3), "iterations": info.iterations,
+                                      "ms": round(ms, 3), "converged": bool(info.converged),
+                                      "fell_back": bool(info.fell_back),
+                                      "energy_error_left": energy_left(ctx, r, xs, e0)}), flush=True)
         ctx.close()
 
 

@@ -23,7 +23,7 @@ EXPORTS = [
     "sipg_operator_apply_noalloc", "sipg_launch_count", "sipg_batch_create", "sipg_batch_destroy",
     "sipg_batch_last_error", "sipg_batch_context", "sipg_batch_apply", "sipg_batch_vcycle", "sipg_batch_solve", "sipg_tile_shape", "sipg_set_tile_shape", "sipg_solve_multi",
     "sipg_operator_apply_multi",
-    "sipg_smoother_train", "sipg_set_smoother", "sipg_mlp_shape", "sipg_mlp_params", "sipg_mlp_forward",
+    "sipg_smoother_train", "sipg_smoother_finetune", "sipg_set_smoother", "sipg_mlp_shape", "sipg_mlp_params", "sipg_mlp_forward",
     "sipg_mlp_gradients", "sipg_mlp_features", "sipg_l2_error",
 ]
 
@@ -113,6 +113,7 @@ def lib():
         L.sipg_tile_shape.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32)]
         L.sipg_set_tile_shape.argtypes = [vp, i32, i32, i32, i32]
         L.sipg_smoother_train.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(TrainInfo)]
+        L.sipg_smoother_finetune.argtypes = [vp, i32, dbl, ctypes.POINTER(TrainInfo)]
         L.sipg_set_smoother.argtypes = [vp, i32, i32, i32]
         ip = ctypes.POINTER(i32)
         L.sipg_mlp_shape.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.POINTER(i64)]
@@ -371,6 +372,12 @@ class Context:
     def train_smoother(self, npairs=100000, epochs=20, seed=2024):
         info = TrainInfo()
         self._check(lib().sipg_smoother_train(self.h, int(npairs), int(epochs), int(seed), ctypes.byref(info)))
+        return info
+
+    def finetune_smoother(self, epochs=20, lr=0.0):
+        """Energy-norm fine-tuning of the trained network (sipg_smoother_finetune; lr 0: 3e-4)."""
+        info = TrainInfo()
+        self._check(lib().sipg_smoother_finetune(self.h, int(epochs), float(lr), ctypes.byref(info)))
         return info
 
     def set_smoother(self, which, steps_pre=0, steps_post=1):

@@ -118,6 +118,7 @@ def test_null_handles_and_bad_arguments_are_rejected_before_device_work(lib):
         "sipg_tile_shape": (N, 0, 0, 0, N),
         "sipg_set_tile_shape": (N, 0, 0, 0, 1),
         "sipg_smoother_train": (N, 100, 1, 0, N),
+        "sipg_smoother_finetune": (N, 1, 0.0, N),
         "sipg_set_smoother": (N, 0, 0, 1),
         "sipg_mlp_shape": (N, N, N, N, N, N, N),
         "sipg_mlp_params": (N, 0, N),

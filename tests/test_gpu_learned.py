@@ -139,3 +139,44 @@ def test_training_and_learned_solve():
     assert with_net < without, (with_net, without)
     ctx.set_smoother(0)
     assert ref.converged
+
+
+def test_energy_norm_finetuning():
+    """Fine-tuning in the energy norm on the training snapshots lowers that loss, the
+    energy-optimal damping is positive, a cycle with the tuned step leaves less energy-norm
+    error than the cycle without post-smoothing, and the solve still reaches 1e-10 (with and
+    without the Chebyshev fallback)."""
+    m, k = 8, 3
+    ctx = _ctx(m, k)
+    ctx.train_smoother(npairs=40000, epochs=30, seed=7)
+    info = ctx.finetune_smoother(epochs=30)
+    assert info.loss_last < info.loss_first <= 1.5, (info.loss_first, info.loss_last)
+    assert info.damping > 0
+    r = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), 71)).to(DEV)
+    xs = torch.zeros_like(r)
+    ctx.set_smoother(0)
+    assert ctx.solve(r, xs, rtol=1e-12).converged
+
+    def left(which, pre, post):
+        ctx.set_smoother(which, pre, post)
+        z, az = torch.empty_like(r), torch.empty_like(r)
+        ctx.vcycle(r, z)
+        e = xs - z
+        ctx.apply(e, az)
+        ax = torch.empty_like(r)
+        ctx.apply(xs, ax)
+        torch.cuda.synchronize()
+        return (torch.dot(e, az) / torch.dot(xs, ax)).item() ** 0.5
+    assert left(1, 0, 1) < left(1, 0, 0)
+    b = torch.as_tensor(sipg_inputs.uniform(ctx.num_dofs(), sipg_inputs.SEED_RHS)).to(DEV)
+    x0 = torch.zeros_like(b)
+    ctx.set_smoother(0)
+    ctx.solve(b, x0, rtol=1e-10)
+    for which in (1, 2):
+        ctx.set_smoother(which, 0, 1)
+        x1 = torch.zeros_like(b)
+        got = ctx.solve(b, x1, rtol=1e-10, maxit=200)
+        assert got.converged and close(x1, x0) <= 1e-8
+        if which == 2:
+            assert not got.fell_back
+    ctx.set_smoother(0)
