@@ -73,23 +73,37 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
     if (act) sweep_inplace<T, N, MS>(su, d, l);
     __syncthreads();
   }
-  if (act) {
+  // the gradient at the Gauss points (curved cells: the metric mixes its
+  // components; an axis-aligned cell needs none of it here: its normal
+  // derivatives come from the values through D^T l below, and its cell term
+  // from the values through the collocation stiffness in the integration pass)
+  if constexpr (CURVED) {
+    if (act) {
 #pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-      int base, stride;
-      line_of<N>(d, l, base, stride);
-      T x[N], y[N];
-      load_line<T, N>(su, base, stride, x);
-      apply_mat<T, N, MD>(x, y);
-      store_line<T, N>(su + (1 + d) * TT, base, stride, y);
+      for (int d = 0; d < 3; ++d) {
+        int base, stride;
+        line_of<N>(d, l, base, stride);
+        T x[N], y[N];
+        load_line<T, N>(su, base, stride, x);
+        apply_mat<T, N, MD>(x, y);
+        store_line<T, N>(su + (1 + d) * TT, base, stride, y);
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (!a.recompute) {
-    T *gg = v.grad + (size_t)cell0 * 3 * N3;
-    for (int i = tid; i < ncta * 3 * N3; i += NT) {
-      const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
-      gg[i] = sm[c * Tile<N>::CS + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)];
+    if constexpr (CURVED) {
+      T *gg = v.grad + (size_t)cell0 * 3 * N3;
+      for (int i = tid; i < ncta * 3 * N3; i += NT) {
+        const int c = i / (3 * N3), r = i - c * 3 * N3, comp = r / N3;
+        gg[i] = sm[c * Tile<N>::CS + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)];
+      }
+    } else {   // the values at the Gauss points, [cell][n^3]
+      T *gg = v.grad + (size_t)cell0 * N3;
+      for (int i = tid; i < ncta * N3; i += NT) {
+        const int c = i / N3;
+        gg[i] = sm[c * Tile<N>::CS + Tile<N>::idx(i - c * N3)];
+      }
     }
   }
   if (!act) return;
@@ -115,13 +129,12 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
     }
     T q0, q1;
     if constexpr (!CURVED) {
-      T g[N];
-      load_line<T, N>(su + (1 + d) * TT, base, stride, g);
-      T g0 = t.l0[N][0] * g[0], g1 = t.l1[N][0] * g[0];
+      // l_s . (D x) = (D^T l_s) . x: the normal derivative from the values
+      T g0 = t.dl0[N][0] * x[0], g1 = t.dl1[N][0] * x[0];
 #pragma unroll
       for (int q = 1; q < N; ++q) {
-        g0 = fma(t.l0[N][q], g[q], g0);
-        g1 = fma(t.l1[N][q], g[q], g1);
+        g0 = fma(t.dl0[N][q], x[q], g0);
+        g1 = fma(t.dl1[N][q], x[q], g1);
       }
       q0 = -a.ih[d] * g0;
       q1 = a.ih[d] * g1;
@@ -172,9 +185,35 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const bool act = cl < ncta;
   T *st = sm + cl * Tile<N>::CS;   // value accumulator, then the integrated tile
-  T *sg = st + TT;            // three gradient components
+  T *sg = st + TT;            // three gradient components (curved); the values (axis-aligned)
 
-  if (a.recompute) {
+  if constexpr (!CURVED) {
+    // An axis-aligned cell's term is sum_d alpha_d (D_d^T W D_d) applied to
+    // the values at the Gauss points; W is a tensor product, so along a line
+    // of direction d it is the collocation stiffness KG = D^T diag(w) D times
+    // the line's weight alpha_d w_t1 w_t2: one product per direction (with the
+    // face terms below) instead of a derivative and a transposed derivative.
+    if (a.recompute) {
+      const T *ug = v.u + (size_t)cell0 * N3;
+      for (int i = tid; i < ncta * N3; i += NT) {
+        const int c = i / N3;
+        sm[c * Tile<N>::CS + TT + Tile<N>::idx(i - c * N3)] = ug[i];
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int d = 0; d < 3; ++d) {
+        if (act) sweep_inplace<T, N, MS>(sg, d, l);
+        __syncthreads();
+      }
+    } else {
+      const T *gg = v.grad + (size_t)cell0 * N3;
+      for (int i = tid; i < ncta * N3; i += NT) {
+        const int c = i / N3;
+        sm[c * Tile<N>::CS + TT + Tile<N>::idx(i - c * N3)] = gg[i];
+      }
+      __syncthreads();
+    }
+  } else if (a.recompute) {
     // gradient at the Gauss points again from u: 3 interpolation and 3
     // collocation-derivative sweeps (the value slot st is free until the faces)
     const T *ug = v.u + (size_t)cell0 * N3;
@@ -206,24 +245,20 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
       sm[c * Tile<N>::CS + (1 + comp) * TT + Tile<N>::idx(r - comp * N3)] = gg[i];
     }
   }
-  __syncthreads();
-  for (int i = tid; i < ncta * N3; i += NT) {
-    const int c = i / N3, p = i - c * N3, tp = Tile<N>::idx(p);
-    T *s = sm + c * Tile<N>::CS + TT + tp;
-    const T g0 = s[0], g1 = s[TT], g2 = s[2 * TT];
-    if constexpr (!CURVED) {
-      s[0] = g0 * a.wcart[p];
-      s[TT] = g1 * a.wcart[N3 + p];
-      s[2 * TT] = g2 * a.wcart[2 * N3 + p];
-    } else {
+  if constexpr (CURVED) {
+    __syncthreads();
+    for (int i = tid; i < ncta * N3; i += NT) {
+      const int c = i / N3, p = i - c * N3, tp = Tile<N>::idx(p);
+      T *s = sm + c * Tile<N>::CS + TT + tp;
+      const T g0 = s[0], g1 = s[TT], g2 = s[2 * TT];
       const T *M = a.metric + (size_t)(cell0 + c) * 6 * N3 + p;
       const T xx = M[0], yy = M[N3], zz = M[2 * N3], xy = M[3 * N3], xz = M[4 * N3], yz = M[5 * N3];
       s[0] = xx * g0 + xy * g1 + xz * g2;
       s[TT] = xy * g0 + yy * g1 + yz * g2;
       s[2 * TT] = xz * g0 + yz * g1 + zz * g2;
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   const int cell = cell0 + cl;
   // cell coordinates and strides as scalars picked by direction (indexing a
@@ -323,7 +358,19 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
         bn0 = (d == 0 ? cvec[0][0] : (d == 1 ? cvec[0][1] : cvec[0][2])) * B[0];
         bn1 = (d == 0 ? cvec[1][0] : (d == 1 ? cvec[1][1] : cvec[1][2])) * B[1];
       }
-      if (d == 0) {
+      if constexpr (!CURVED && sizeof(T) == 4) {
+        // the cell term along this line: KG times the line's weight, with the faces
+        T x[N], y[N];
+        load_line<T, N>(sg, base, stride, x);
+        apply_mat<T, N, MKG>(x, y);
+        const T cw = a.fwcart[d * N2 + l] * a.ih[d];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          T *p = st + base + q * stride;
+          const T f = fma(t.l0[N][q], A[0], fma(t.l1[N][q], A[1], fma(t.dl0[N][q], bn0, t.dl1[N][q] * bn1)));
+          *p = fma(cw, y[q], d == 0 ? f : f + *p);
+        }
+      } else if (d == 0) {
 #pragma unroll
         for (int q = 0; q < N; ++q)
           st[base + q * stride] = fma(t.l0[N][q], A[0], fma(t.l1[N][q], A[1], fma(t.dl0[N][q], bn0, t.dl1[N][q] * bn1)));
@@ -351,18 +398,37 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
     }
     __syncthreads();
   }
+  if constexpr (CURVED) {
 #pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    if (act) {
-      int base, stride;
-      line_of<N>(d, l, base, stride);
-      T x[N], y[N];
-      load_line<T, N>(sg + d * TT, base, stride, x);
-      apply_mat<T, N, MDt>(x, y);
+    for (int d = 0; d < 3; ++d) {
+      if (act) {
+        int base, stride;
+        line_of<N>(d, l, base, stride);
+        T x[N], y[N];
+        load_line<T, N>(sg + d * TT, base, stride, x);
+        apply_mat<T, N, MDt>(x, y);
 #pragma unroll
-      for (int q = 0; q < N; ++q) st[base + q * stride] += y[q];
+        for (int q = 0; q < N; ++q) st[base + q * stride] += y[q];
+      }
+      __syncthreads();
     }
-    __syncthreads();
+  } else if constexpr (sizeof(T) == 8) {
+    // FP64: the cell term after the faces (within the face loop the sweep's
+    // registers and the face coefficients' would not fit together)
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      if (act) {
+        int base, stride;
+        line_of<N>(d, l, base, stride);
+        T x[N], y[N];
+        load_line<T, N>(sg, base, stride, x);
+        apply_mat<T, N, MKG>(x, y);
+        const T cw = a.fwcart[d * N2 + l] * a.ih[d];
+#pragma unroll
+        for (int q = 0; q < N; ++q) st[base + q * stride] = fma(cw, y[q], st[base + q * stride]);
+      }
+      __syncthreads();
+    }
   }
 #pragma unroll 1
   for (int d = 0; d < 2; ++d) {

@@ -202,6 +202,13 @@ void build_tables(Tables<T> &t) {
       }
     put(M1, +1, t.M1E[n], t.M1O[n]);
     put(K1, +1, t.K1E[n], t.K1O[n]);
+    std::vector<double> KG(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        for (int q = 0; q < n; ++q) KG[i * n + j] += r.D[q * n + i] * r.wq[q] * r.D[q * n + j];
+    if (n <= 4)
+      for (int i = 0; i < n * n; ++i) t.KG[n][i] = (T)KG[i];
+    put(KG, +1, t.KGE[n], t.KGO[n]);
     for (int q = 0; q < n; ++q) {
       t.l0[n][q] = (T)r.l0[q];
       t.l1[n][q] = (T)r.l1[q];

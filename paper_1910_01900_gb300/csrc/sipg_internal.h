@@ -49,6 +49,9 @@ struct Tables {
   // (both M[i][j] = M[n-1-i][n-1-j]): the factors of the Cartesian FE cell matrix
   T M1[kMaxN + 1][16], K1[kMaxN + 1][16];
   T M1E[kMaxN + 1][25], M1O[kMaxN + 1][20], K1E[kMaxN + 1][25], K1O[kMaxN + 1][20];
+  // the collocation stiffness at the Gauss points, KG[i][j] = sum_q D[q][i] w_q D[q][j]
+  // (KG[i][j] = KG[n-1-i][n-1-j]): the cell term of an axis-aligned DG cell along one direction
+  T KG[kMaxN + 1][16], KGE[kMaxN + 1][25], KGO[kMaxN + 1][20];
 };
 template <typename T>
 void build_tables(Tables<T> &t);

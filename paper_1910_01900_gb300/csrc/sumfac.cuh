@@ -87,7 +87,7 @@ __device__ __forceinline__ void mv(const T *__restrict__ P, const T *__restrict_
 }
 
 // Matrix selectors (compile-time n).
-enum Mat { MS = 0, MSt = 1, MD = 2, MDt = 3, MM1 = 4, MK1 = 5 };
+enum Mat { MS = 0, MSt = 1, MD = 2, MDt = 3, MM1 = 4, MK1 = 5, MKG = 6 };
 template <typename T, int N, int M>
 __device__ __forceinline__ void apply_mat(const T (&x)[N], T (&y)[N]) {
   const Tables<T> &t = tab<T>();
@@ -97,6 +97,7 @@ __device__ __forceinline__ void apply_mat(const T (&x)[N], T (&y)[N]) {
   if constexpr (M == MDt) mv<T, N, -1>(t.Dt[N], t.DtE[N], t.DtO[N], x, y);
   if constexpr (M == MM1) mv<T, N, +1>(t.M1[N], t.M1E[N], t.M1O[N], x, y);
   if constexpr (M == MK1) mv<T, N, +1>(t.K1[N], t.K1E[N], t.K1O[N], x, y);
+  if constexpr (M == MKG) mv<T, N, +1>(t.KG[N], t.KGE[N], t.KGO[N], x, y);
 }
 
 // Shared-memory layout of one cell: four tile arrays of N^3 values (x
