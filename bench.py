@@ -44,9 +44,9 @@ METRIC = "SIPG apply DoF/s & %roofline; solve s/MDoF to 1e-10 rel. res. vs plain
 
 # DRAM bytes per launch of the solve's dominant kernel, per DoF: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of dg_integrate_kernel<double,5,
-# Cartesian> on this workload's mesh (177,383,680 + 18,509,312 bytes over
+# Cartesian> on this workload's mesh (111,714,048 + 13,050,368 bytes over
 # 4,096,000 DoF in one captured launch; the command is in traffic_source).
-DOMINANT_DRAM_BYTES_PER_DOF = (177383680 + 18509312) / 4096000
+DOMINANT_DRAM_BYTES_PER_DOF = (111714048 + 13050368) / 4096000
 DOMINANT_NCU_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                         "--clock-control none -k regex:dg_integrate -s 4 -c 1 python -m "
                         "paper_1910_01900_gb300.sweep --k 4 --curved 0 --precision 0 --m 32 --repeats 2 "
