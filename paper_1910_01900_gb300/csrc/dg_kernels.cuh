@@ -43,6 +43,33 @@ __device__ __forceinline__ int face_perm(const int code, const int l) {
   return a + N * b;
 }
 
+// The interpolation of a cell's values to the Gauss points, reading u from
+// global memory: the z-lines go straight from the loads through S (thread l
+// of the cell reads its line u[l + q n^2], coalesced over the cell's
+// threads) into the tile, then the x and y sweeps in place.  One tile store
+// and one tile load per value fewer than staging u first.  Every thread of
+// the block takes part in the barriers.
+template <typename T, int N>
+__device__ __forceinline__ void interpolate_from_global(const T *__restrict__ ucell, T *tile, const bool act,
+                                                        const int l) {
+  constexpr int N2 = N * N;
+  if (act) {
+    int base, stride;
+    line_of<N>(2, l, base, stride);
+    T x[N], y[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) x[q] = ucell[l + q * N2];
+    apply_mat<T, N, MS>(x, y);
+    store_line<T, N>(tile, base, stride, y);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int d = 0; d < 2; ++d) {
+    if (act) sweep_inplace<T, N, MS>(tile, d, l);
+    __syncthreads();
+  }
+}
+
 template <typename T>
 struct VecPtrs {
   const T *u;
@@ -62,17 +89,7 @@ __device__ __forceinline__ void dg_eval_body(const DGArgs<T> &a, const VecPtrs<T
   const bool act = cl < ncta;
   T *su = sm + cl * Tile<N>::CS;
 
-  const T *ug = v.u + (size_t)cell0 * N3;
-  for (int i = tid; i < ncta * N3; i += NT) {
-    const int c = i / N3;
-    sm[c * Tile<N>::CS + Tile<N>::idx(i - c * N3)] = ug[i];
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    if (act) sweep_inplace<T, N, MS>(su, d, l);
-    __syncthreads();
-  }
+  interpolate_from_global<T, N>(v.u + (size_t)(cell0 + (act ? cl : 0)) * N3, su, act, l);
   // the gradient at the Gauss points (curved cells: the metric mixes its
   // components; an axis-aligned cell needs none of it here: its normal
   // derivatives come from the values through D^T l below, and its cell term
@@ -194,17 +211,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
     // the line's weight alpha_d w_t1 w_t2: one product per direction (with the
     // face terms below) instead of a derivative and a transposed derivative.
     if (a.recompute) {
-      const T *ug = v.u + (size_t)cell0 * N3;
-      for (int i = tid; i < ncta * N3; i += NT) {
-        const int c = i / N3;
-        sm[c * Tile<N>::CS + TT + Tile<N>::idx(i - c * N3)] = ug[i];
-      }
-      __syncthreads();
-#pragma unroll 1
-      for (int d = 0; d < 3; ++d) {
-        if (act) sweep_inplace<T, N, MS>(sg, d, l);
-        __syncthreads();
-      }
+      interpolate_from_global<T, N>(v.u + (size_t)(cell0 + (act ? cl : 0)) * N3, sg, act, l);
     } else {
       const T *gg = v.grad + (size_t)cell0 * N3;
       for (int i = tid; i < ncta * N3; i += NT) {
@@ -216,17 +223,7 @@ __device__ __forceinline__ void dg_integrate_body(const DGArgs<T> &a, const VecP
   } else if (a.recompute) {
     // gradient at the Gauss points again from u: 3 interpolation and 3
     // collocation-derivative sweeps (the value slot st is free until the faces)
-    const T *ug = v.u + (size_t)cell0 * N3;
-    for (int i = tid; i < ncta * N3; i += NT) {
-      const int c = i / N3;
-      sm[c * Tile<N>::CS + Tile<N>::idx(i - c * N3)] = ug[i];
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-      if (act) sweep_inplace<T, N, MS>(st, d, l);
-      __syncthreads();
-    }
+    interpolate_from_global<T, N>(v.u + (size_t)(cell0 + (act ? cl : 0)) * N3, st, act, l);
     if (act) {
 #pragma unroll 1
       for (int d = 0; d < 3; ++d) {
