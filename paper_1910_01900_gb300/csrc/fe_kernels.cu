@@ -23,6 +23,16 @@ void upload_tables_fe<double>(const Tables<double> &t) { upload_tables_tu(t); }
 template <>
 void upload_tables_fe<float>(const Tables<float> &t) { upload_tables_tu(t); }
 
+// (x, y, z) of point i of an nx x ny x nz grid in 32-bit arithmetic (the
+// launchers keep every grid below 2^32 points): the 64-bit divisions they
+// replace cost more than the loads of the small node passes
+__device__ __forceinline__ void grid_coords(const long i, const int nx, const int ny, int g[3]) {
+  const unsigned u = (unsigned)i, r = u / (unsigned)nx;
+  g[0] = (int)(u - r * (unsigned)nx);
+  g[1] = (int)(r % (unsigned)ny);
+  g[2] = (int)(r / (unsigned)ny);
+}
+
 __device__ __forceinline__ bool node_constrained(const int g[3], const int grid[3], const int bc[6]) {
   return (g[0] == 0 && bc[0] == 0) || (g[0] == grid[0] - 1 && bc[1] == 0) ||
          (g[1] == 0 && bc[2] == 0) || (g[1] == grid[1] - 1 && bc[3] == 0) ||
@@ -256,8 +266,8 @@ __global__ void fe_stencil_assemble_kernel(const FEArgs<double> a, const double 
   if (idx >= ng * w * w * w) return;
   const int o = (int)(idx / ng);
   const long gid = idx - (long)o * ng;
-  const int g[3] = {(int)(gid % a.grid[0]), (int)((gid / a.grid[0]) % a.grid[1]),
-                    (int)(gid / ((long)a.grid[0] * a.grid[1]))};
+  int g[3];
+  grid_coords(gid, a.grid[0], a.grid[1], g);
   const int off[3] = {o % w - p, (o / w) % w - p, o / (w * w) - p};
   if (node_constrained(g, a.grid, a.bc)) {
     coef[idx] = (off[0] == 0 && off[1] == 0 && off[2] == 0) ? 1.0 : 0.0;
@@ -316,9 +326,7 @@ __global__ void __launch_bounds__(256) fe_stencil_apply_kernel(const FEArgs<T> a
   T y = T(0);
   int g[3] = {0, 0, 0};
   if (gid < ng) {
-    g[0] = (int)(gid % a.grid[0]);
-    g[1] = (int)((gid / a.grid[0]) % a.grid[1]);
-    g[2] = (int)(gid / ((long)a.grid[0] * a.grid[1]));
+    grid_coords(gid, a.grid[0], a.grid[1], g);
   }
   if (live) {
     auto ok = [&](int d, int k) {
@@ -369,8 +377,8 @@ __device__ __forceinline__ void fe_gather_node(const FEArgs<T> &a, const long gi
   const T *__restrict__ ebuf = a.ebuf + vec * a.es;
   const int64_t vo = vec * a.vs;
   const int n = a.deg + 1, n2 = n * n, n3 = n2 * n;
-  const int g[3] = {(int)(gid % a.grid[0]), (int)((gid / a.grid[0]) % a.grid[1]),
-                    (int)(gid / ((long)a.grid[0] * a.grid[1]))};
+  int g[3];
+  grid_coords(gid, a.grid[0], a.grid[1], g);
   const bool cons = node_constrained(g, a.grid, a.bc);
   T y;
   if (cons) {
@@ -514,7 +522,8 @@ __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__
   const long total = (long)G.gf[0] * G.gf[1] * G.gf[2];
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= total) return;
-  const int g[3] = {(int)(gid % G.gf[0]), (int)((gid / G.gf[0]) % G.gf[1]), (int)(gid / ((long)G.gf[0] * G.gf[1]))};
+  int g[3];
+  grid_coords(gid, G.gf[0], G.gf[1], g);
   if (node_constrained(g, G.gf, G.bc)) return;
   xc += blockIdx.y * G.sc;   // vector blockIdx.y
   xf += blockIdx.y * G.sf;
@@ -569,7 +578,8 @@ __global__ void fe_restrict_nodes_kernel(const XferGeom G, const T *__restrict__
   if (gid >= total) return;
   rf += blockIdx.y * G.sf;   // vector blockIdx.y
   rc += blockIdx.y * G.sc;
-  const int J[3] = {(int)(gid % G.gc[0]), (int)((gid / G.gc[0]) % G.gc[1]), (int)(gid / ((long)G.gc[0] * G.gc[1]))};
+  int J[3];
+  grid_coords(gid, G.gc[0], G.gc[1], J);
   if (node_constrained(J, G.gc, G.bc)) {
     rc[gid] = T(0);
     return;
@@ -898,6 +908,7 @@ cudaError_t launch_fe_stencil_apply(const FEArgs<T> &a, const T *coef, cudaStrea
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
   const int bs = 256;
   if (total == 0) return cudaSuccess;
+  if (total >= (1L << 32)) return cudaErrorInvalidValue;   // the kernel's 32-bit grid coordinates
   const long lanes = total * (a.deg == 1 ? 4 : 8);   // lanes per node (the kernel's SL)
   if ((lanes + bs - 1) / bs > 0x7fffffffL) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((lanes + bs - 1) / bs), a.nv);
@@ -943,6 +954,7 @@ cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s) {
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
   const int bs = 256;
   if (total == 0) return cudaSuccess;
+  if (total >= (1L << 32)) return cudaErrorInvalidValue;   // the kernel's 32-bit grid coordinates
   fe_gather_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), a.nv), bs, 0, s>>>(a);
   note_launch();
   return cudaGetLastError();
@@ -996,6 +1008,7 @@ cudaError_t launch_fe_prolongate_add(const XferGeom &g, const T *P1, const T *xc
   const long total = (long)g.gf[0] * g.gf[1] * g.gf[2];
   const int bs = 256;
   if (total == 0) return cudaSuccess;
+  if (total >= (1L << 32)) return cudaErrorInvalidValue;   // the kernel's 32-bit grid coordinates
   const dim3 grid((unsigned)((total + bs - 1) / bs), g.nv);
   switch (g.pc + 1) {
     case 2:
@@ -1023,6 +1036,7 @@ cudaError_t launch_fe_restrict_nodes(const XferGeom &g, const T *P1, const T *rf
   const long total = (long)g.gc[0] * g.gc[1] * g.gc[2];
   const int bs = 128;
   if (total == 0) return cudaSuccess;
+  if (total >= (1L << 32)) return cudaErrorInvalidValue;   // the kernel's 32-bit grid coordinates
   fe_restrict_nodes_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), g.nv), bs, 0, s>>>(g, P1, rf, rc);
   note_launch();
   return cudaGetLastError();
