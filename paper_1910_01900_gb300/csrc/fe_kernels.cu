@@ -439,7 +439,9 @@ __global__ void fe_gather_kernel(const FEArgs<T> a) {
 template <typename T>
 __device__ __forceinline__ void c_prolongate_dof(const FEArgs<T> &a, const T *xc, T *xdg, const long idx) {
   const int n = a.deg + 1, n2 = n * n, n3 = n2 * n;
-  const int cell = (int)(idx / n3), p = (int)(idx - (long)cell * n3);
+  // 32-bit index arithmetic (the launchers keep the DG vector below 2^32 values)
+  const unsigned ui = (unsigned)idx, cu = ui / (unsigned)n3;
+  const int cell = (int)cu, p = (int)(ui - cu * (unsigned)n3);
   const int g[3] = {(cell % a.m[0]) * a.deg + p % n, ((cell / a.m[0]) % a.m[1]) * a.deg + (p / n) % n,
                     (cell / (a.m[0] * a.m[1])) * a.deg + p / n2};
   if (node_constrained(g, a.grid, a.bc)) return;
@@ -998,6 +1000,7 @@ cudaError_t launch_c_prolongate_add(const FEArgs<T> &a, const T *xc, T *xdg, cud
   const long total = (long)a.ncells * n * n * n;
   const int bs = 256;
   if (total == 0) return cudaSuccess;
+  if (total >= (1L << 32)) return cudaErrorInvalidValue;   // the kernel's 32-bit index arithmetic
   c_prolongate_add_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), a.nv), bs, 0, s>>>(a, xc, xdg, dg_stride);
   note_launch();
   return cudaGetLastError();
