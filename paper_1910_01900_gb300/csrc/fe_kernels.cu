@@ -372,11 +372,11 @@ __global__ void __launch_bounds__(256) fe_stencil_apply_kernel(const FEArgs<T> a
 }
 
 // Node pass: out[g] = sum over the cells sharing node g of ebuf, then the epilogue.
-template <typename T>
+template <typename T, int P>
 __device__ __forceinline__ void fe_gather_node(const FEArgs<T> &a, const long gid, const int vec) {
+  constexpr int n = P + 1, n2 = n * n, n3 = n2 * n;
   const T *__restrict__ ebuf = a.ebuf + vec * a.es;
   const int64_t vo = vec * a.vs;
-  const int n = a.deg + 1, n2 = n * n, n3 = n2 * n;
   int g[3];
   grid_coords(gid, a.grid[0], a.grid[1], g);
   const bool cons = node_constrained(g, a.grid, a.bc);
@@ -384,34 +384,41 @@ __device__ __forceinline__ void fe_gather_node(const FEArgs<T> &a, const long gi
   if (cons) {
     y = (a.mode == 3) ? T(0) : (a.mode == 4 ? T(1) : a.u[vo + gid]);
   } else {
-    // per direction the two candidate cells containing this node: the one
-    // below (when the node is on its upper face) and the one it starts
-    int cc[3][2], ll[3][2];
-    bool ok[3][2];
+    // per direction: the cell the node starts (its last cell for the last
+    // node, where it sits on the upper face) and, when the node is on that
+    // cell's lower face, the cell below, whose entry is this one's plus the
+    // fixed step D_d (local index + P, cell index - one cell)
+    int c[3], r[3];
+    bool lo[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const int c = g[d] / a.deg, r = g[d] - c * a.deg;
-      ok[d][0] = r == 0 && c > 0;
-      cc[d][0] = c - 1;
-      ll[d][0] = a.deg;
-      ok[d][1] = c < a.m[d];
-      cc[d][1] = c;
-      ll[d][1] = r;
+      c[d] = g[d] / P;
+      r[d] = g[d] - c[d] * P;
+      if (c[d] == a.m[d]) {
+        c[d] -= 1;
+        r[d] = P;
+      }
+      lo[d] = r[d] == 0 && c[d] > 0;
     }
+    const long own = (c[0] + (long)a.m[0] * (c[1] + (long)a.m[1] * c[2])) * n3 + r[0] + n * r[1] + n2 * r[2];
+    const long D0 = P - (long)n3, D1 = (long)P * n - (long)a.m[0] * n3,
+               D2 = (long)P * n2 - (long)a.m[0] * a.m[1] * n3;
     // all eight loads issued unconditionally (a missing cell reads entry 0),
-    // then summed in a fixed order over the cells that exist
+    // then summed in a fixed order over the cells that exist (the cell below
+    // before the own one in every direction)
     T e[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int x = q & 1, yy = (q >> 1) & 1, z = q >> 2;
-      const bool take = ok[0][x] && ok[1][yy] && ok[2][z];
-      const size_t cell = take ? cc[0][x] + (size_t)a.m[0] * (cc[1][yy] + (size_t)a.m[1] * cc[2][z]) : 0;
-      e[q] = ebuf[take ? cell * n3 + ll[0][x] + n * ll[1][yy] + n2 * ll[2][z] : 0];
+      const bool take = (x || lo[0]) && (yy || lo[1]) && (z || lo[2]);
+      const long addr = own + (x ? 0 : D0) + (yy ? 0 : D1) + (z ? 0 : D2);
+      e[q] = ebuf[take ? addr : 0];
     }
     y = T(0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int x = q & 1, yy = (q >> 1) & 1, z = q >> 2;
-      if (ok[0][x] && ok[1][yy] && ok[2][z]) y += e[q];
+      if ((x || lo[0]) && (yy || lo[1]) && (z || lo[2])) y += e[q];
     }
   }
   const long gv = vo + gid;
@@ -427,12 +434,27 @@ __device__ __forceinline__ void fe_gather_node(const FEArgs<T> &a, const long gi
   }
 }
 
+// the node pass for the task's degree (1..8)
 template <typename T>
+__device__ __forceinline__ void fe_gather_node_any(const FEArgs<T> &a, const long gid, const int vec) {
+  switch (a.deg) {
+    case 1: fe_gather_node<T, 1>(a, gid, vec); break;
+    case 2: fe_gather_node<T, 2>(a, gid, vec); break;
+    case 3: fe_gather_node<T, 3>(a, gid, vec); break;
+    case 4: fe_gather_node<T, 4>(a, gid, vec); break;
+    case 5: fe_gather_node<T, 5>(a, gid, vec); break;
+    case 6: fe_gather_node<T, 6>(a, gid, vec); break;
+    case 7: fe_gather_node<T, 7>(a, gid, vec); break;
+    default: fe_gather_node<T, 8>(a, gid, vec); break;
+  }
+}
+
+template <typename T, int P>
 __global__ void fe_gather_kernel(const FEArgs<T> a) {
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= total) return;
-  fe_gather_node<T>(a, gid, blockIdx.y);   // vector blockIdx.y
+  fe_gather_node<T, P>(a, gid, blockIdx.y);   // vector blockIdx.y
 }
 
 // c-transfer prolongation: x_dg[cell][i] += x_fe[node(cell, i)]  (injection).
@@ -503,7 +525,7 @@ __global__ void __launch_bounds__(kBatchNodeThreads) fe_nodes_batched_kernel(con
   const FETask<T> &P = tasks[w.p];
   const long i = (long)w.blk * kBatchNodeThreads + threadIdx.x;
   if (kind == 0) {
-    if (i < (long)P.a.grid[0] * P.a.grid[1] * P.a.grid[2]) fe_gather_node<T>(P.a, i, 0);
+    if (i < (long)P.a.grid[0] * P.a.grid[1] * P.a.grid[2]) fe_gather_node_any<T>(P.a, i, 0);
   } else {
     const int n = P.a.deg + 1;
     if (i < (long)P.a.ncells * n * n * n) c_prolongate_dof<T>(P.a, P.xc, P.xdg, i);
@@ -956,8 +978,18 @@ cudaError_t launch_fe_gather(const FEArgs<T> &a, cudaStream_t s) {
   const long total = (long)a.grid[0] * a.grid[1] * a.grid[2];
   const int bs = 256;
   if (total == 0) return cudaSuccess;
-  if (total >= (1L << 32)) return cudaErrorInvalidValue;   // the kernel's 32-bit grid coordinates
-  fe_gather_kernel<T><<<dim3((unsigned)((total + bs - 1) / bs), a.nv), bs, 0, s>>>(a);
+  if (total >= (1L << 32) || a.deg < 1 || a.deg > 8) return cudaErrorInvalidValue;   // 32-bit coordinates
+  const dim3 grid((unsigned)((total + bs - 1) / bs), a.nv);
+  switch (a.deg) {
+    case 1: fe_gather_kernel<T, 1><<<grid, bs, 0, s>>>(a); break;
+    case 2: fe_gather_kernel<T, 2><<<grid, bs, 0, s>>>(a); break;
+    case 3: fe_gather_kernel<T, 3><<<grid, bs, 0, s>>>(a); break;
+    case 4: fe_gather_kernel<T, 4><<<grid, bs, 0, s>>>(a); break;
+    case 5: fe_gather_kernel<T, 5><<<grid, bs, 0, s>>>(a); break;
+    case 6: fe_gather_kernel<T, 6><<<grid, bs, 0, s>>>(a); break;
+    case 7: fe_gather_kernel<T, 7><<<grid, bs, 0, s>>>(a); break;
+    default: fe_gather_kernel<T, 8><<<grid, bs, 0, s>>>(a); break;
+  }
   note_launch();
   return cudaGetLastError();
 }
