@@ -50,32 +50,38 @@ __device__ __forceinline__ void fe_cell_body(const FEArgs<T> &a, const T *__rest
   const int tid = threadIdx.x, cl = tid / N2, l = tid - cl * N2;
   const bool act = cl < ncta;
   T *su = sm + cl * Tile<N>::CS;
-  for (int i = tid; i < ncta * N3; i += NT) {
-    const int c = i / N3, p = i - c * N3;
-    const int cell = cell0 + c;
-    const int g[3] = {(cell % a.m[0]) * a.deg + p % N, ((cell / a.m[0]) % a.m[1]) * a.deg + (p / N) % N,
-                      (cell / (a.m[0] * a.m[1])) * a.deg + p / N2};
-    const size_t gi = g[0] + (size_t)a.grid[0] * (g[1] + (size_t)a.grid[1] * g[2]);
-    sm[c * Tile<N>::CS + Tile<N>::idx(p)] = node_constrained(g, a.grid, a.bc) ? T(0) : ug[gi];
+  // each thread gathers its z-line of the cell's nodes straight into
+  // registers (constrained Dirichlet nodes read as zero); the first sweep
+  // runs on them before anything goes to shared memory
+  T xl[N];
+  if (act) {
+    constexpr int P = N - 1;
+    const int cell = cell0 + cl;
+    const int cx = cell % a.m[0], rr = cell / a.m[0], cy = rr % a.m[1], cz = rr / a.m[1];
+    int g[3] = {cx * P + l % N, cy * P + l / N, 0};
+    const size_t b0 = g[0] + (size_t)a.grid[0] * g[1], sz = (size_t)a.grid[0] * a.grid[1];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      g[2] = cz * P + q;
+      xl[q] = node_constrained(g, a.grid, a.bc) ? T(0) : ug[b0 + sz * g[2]];
+    }
   }
-  __syncthreads();
   if constexpr (!CURVED) {
     // An axis-aligned box cell: its matrix is the sum over d of alpha_d times
     // the tensor product of the 1D stiffness matrix K1 in direction d and the
     // 1D mass matrix M1 in the other two (both under the Gauss rule, as the
-    // interpolate / differentiate / weight / transpose sweeps below compute
-    // it), so y = ax K1 M1 M1 u + ay M1 K1 M1 u + az M1 M1 K1 u takes 7 1D
-    // products instead of 12: along x a = M1 u, b = K1 u; along y c = M1 a,
-    // f = ay K1 a + ax M1 b; along z y = az K1 c + M1 f.
+    // interpolate / differentiate / weight / transpose sweeps of the general
+    // path compute it), so y = ax K1 M1 M1 u + ay M1 K1 M1 u + az M1 M1 K1 u
+    // takes 7 1D products instead of 12: along z a = M1 u, b = K1 u; along y
+    // c = M1 a, f = ay K1 a + az M1 b; along x y = ax K1 c + M1 f.
     T *t0 = su, *t1 = su + TT;
     int base, stride;
     if (act) {
-      line_of<N>(0, l, base, stride);
-      T x[N], y[N];
-      load_line<T, N>(t0, base, stride, x);
-      apply_mat<T, N, MK1>(x, y);
+      line_of<N>(2, l, base, stride);
+      T y[N];
+      apply_mat<T, N, MK1>(xl, y);
       store_line<T, N>(t1, base, stride, y);
-      apply_mat<T, N, MM1>(x, y);
+      apply_mat<T, N, MM1>(xl, y);
       store_line<T, N>(t0, base, stride, y);
     }
     __syncthreads();
@@ -89,24 +95,32 @@ __device__ __forceinline__ void fe_cell_body(const FEArgs<T> &a, const T *__rest
       load_line<T, N>(t1, base, stride, x);
       apply_mat<T, N, MM1>(x, y);
 #pragma unroll
-      for (int q = 0; q < N; ++q) y[q] = fma(a.alpha[1], k[q], a.alpha[0] * y[q]);
+      for (int q = 0; q < N; ++q) y[q] = fma(a.alpha[1], k[q], a.alpha[2] * y[q]);
       store_line<T, N>(t1, base, stride, y);
     }
     __syncthreads();
     if (!act) return;
-    line_of<N>(2, l, base, stride);
+    line_of<N>(0, l, base, stride);
     T x[N], y[N], k[N];
     load_line<T, N>(t0, base, stride, x);
     apply_mat<T, N, MK1>(x, k);
     load_line<T, N>(t1, base, stride, x);
     apply_mat<T, N, MM1>(x, y);
-    T *eb = ebv + (size_t)(cell0 + cl) * N3 + l;
+    T *eb = ebv + (size_t)(cell0 + cl) * N3 + N * l;   // the x-line of points (q, l % N, l / N)
 #pragma unroll
-    for (int q = 0; q < N; ++q) eb[q * N2] = fma(a.alpha[2], k[q], y[q]);
+    for (int q = 0; q < N; ++q) eb[q] = fma(a.alpha[0], k[q], y[q]);
     return;
   }
+  if (act) {   // interpolation along z from the registers, then x and y in place
+    int base, stride;
+    line_of<N>(2, l, base, stride);
+    T y[N];
+    apply_mat<T, N, MS>(xl, y);
+    store_line<T, N>(su, base, stride, y);
+  }
+  __syncthreads();
 #pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
+  for (int d = 0; d < 2; ++d) {
     if (act) sweep_inplace<T, N, MS>(su, d, l);
     __syncthreads();
   }
