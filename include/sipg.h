@@ -148,6 +148,15 @@ typedef struct {
   int coarse_maxit;        /* AMG-CG iterations launched per coarse solve
                               (each one skips its work once coarse_rtol is
                               met, so the solve stays capturable), 12       */
+  int fuse_tail;           /* 1 (default): the V-cycle below the assembled
+                              degree-1 levels of at most 8192 nodes (their
+                              Chebyshev steps, residuals and 2:1 transfers,
+                              Algorithms 2 and 3) and a dense coarse solve of
+                              at most 1000 unknowns run as one launch of one
+                              thread-block cluster, barriers between the
+                              steps, with the same arithmetic as the
+                              per-step launches (same results, bit for bit);
+                              0: one launch per step                        */
   void *stream;            /* cudaStream_t or NULL                             */
 } sipg_params;
 

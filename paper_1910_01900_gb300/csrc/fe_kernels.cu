@@ -554,17 +554,20 @@ __global__ void __launch_bounds__(kBatchNodeThreads) fe_nodes_batched_kernel(con
 // ([child][nf][nc]; child 0 only for the p-transfer).
 // NC: coarse points per direction at compile time (unrolled, all loads in
 // flight together), 0 = runtime
-template <typename T, int NC>
-__global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ xc,
-                                         T *__restrict__ xf) {
-  const long total = (long)G.gf[0] * G.gf[1] * G.gf[2];
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= total) return;
+// COH: xc and xf were written earlier in the same launch by other blocks of
+// a cluster (the fused tail below): read them through L2
+template <bool COH, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
+template <typename T, int NC, bool COH>
+__device__ __forceinline__ void fe_prolongate_node(const XferGeom &G, const T *__restrict__ P1, const T *xc, T *xf,
+                                                   const long gid) {
   int g[3];
   grid_coords(gid, G.gf[0], G.gf[1], g);
   if (node_constrained(g, G.gf, G.bc)) return;
-  xc += blockIdx.y * G.sc;   // vector blockIdx.y
-  xf += blockIdx.y * G.sf;
   const int nf = G.pf + 1, nc = NC > 0 ? NC : G.pc + 1;
   const T *row[3];
   int base[3];
@@ -589,12 +592,22 @@ __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__
       const size_t off = (size_t)G.gc[0] * ((base[1] + jy) + (size_t)G.gc[1] * (base[2] + jz)) + base[0];
       T sx = T(0);
 #pragma unroll
-      for (int jx = 0; jx < (NC > 0 ? NC : nc); ++jx) sx = fma(row[0][jx], xc[off + jx], sx);
+      for (int jx = 0; jx < (NC > 0 ? NC : nc); ++jx) sx = fma(row[0][jx], ldv<COH>(xc + off + jx), sx);
       sy = fma(row[1][jy], sx, sy);
     }
     sum = fma(row[2][jz], sy, sum);
   }
-  xf[gid] += sum;
+  xf[gid] = ldv<COH>(xf + gid) + sum;
+}
+
+template <typename T, int NC>
+__global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ xc,
+                                         T *__restrict__ xf) {
+  const long total = (long)G.gf[0] * G.gf[1] * G.gf[2];
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  // vector blockIdx.y
+  fe_prolongate_node<T, NC, false>(G, P1, xc + blockIdx.y * G.sc, xf + blockIdx.y * G.sf, gid);
 }
 
 // p/h restriction node by node for the two small transfers of the hierarchy
@@ -608,14 +621,9 @@ __global__ void fe_prolongate_add_kernel(const XferGeom G, const T *__restrict__
 // weights come from the prolongation's 1D tables.  27 loads per node, issued
 // unconditionally (a missing entry reads fine node 2J) and summed by
 // selection in a fixed order.
-template <typename T>
-__global__ void fe_restrict_nodes_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ rf,
-                                         T *__restrict__ rc) {
-  const long total = (long)G.gc[0] * G.gc[1] * G.gc[2];
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= total) return;
-  rf += blockIdx.y * G.sf;   // vector blockIdx.y
-  rc += blockIdx.y * G.sc;
+template <typename T, bool COH>
+__device__ __forceinline__ void fe_restrict_node(const XferGeom &G, const T *__restrict__ P1, const T *rf, T *rc,
+                                                 const long gid) {
   int J[3];
   grid_coords(gid, G.gc[0], G.gc[1], J);
   if (node_constrained(J, G.gc, G.bc)) {
@@ -654,10 +662,20 @@ __global__ void fe_restrict_nodes_kernel(const XferGeom G, const T *__restrict__
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         const T wt = w[0][x] * w[1][y] * w[2][z];
-        const T v = rf[idx[0][x] + sy * idx[1][y] + sz * idx[2][z]];
+        const T v = ldv<COH>(rf + idx[0][x] + sy * idx[1][y] + sz * idx[2][z]);
         sum = wt != T(0) ? fma(wt, v, sum) : sum;
       }
   rc[gid] = sum;
+}
+
+template <typename T>
+__global__ void fe_restrict_nodes_kernel(const XferGeom G, const T *__restrict__ P1, const T *__restrict__ rf,
+                                         T *__restrict__ rc) {
+  const long total = (long)G.gc[0] * G.gc[1] * G.gc[2];
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  // vector blockIdx.y
+  fe_restrict_node<T, false>(G, P1, rf + blockIdx.y * G.sf, rc + blockIdx.y * G.sc, gid);
 }
 
 // p/h restriction, cell part, by sum factorisation: one thread block per
@@ -1091,6 +1109,185 @@ cudaError_t launch_fe_restrict_nodes(const XferGeom &g, const T *P1, const T *rf
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- fused tail
+// Below a few thousand nodes a V-cycle step is a few microseconds of launch
+// and load latency for a few microseconds' worth of nothing; the tail runs
+// all steps of its levels in one launch of one thread-block cluster, a
+// cluster barrier (release/acquire at cluster scope) between the steps.
+// Vectors written inside the launch are read through L2 (ldv<true>); the
+// stencils, diagonals, transfer tables and the coarse inverse are read-only.
+
+// all threads of the cluster: the writes before it are seen by the reads after
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;\n" ::: "memory");
+}
+
+// One row of a 27-point stencil apply and its epilogue, one thread per node:
+// the three slab sums of fe_stencil_apply_kernel<T, 1> (slab z: its 9 offsets
+// in the same order) combined in the order of its lane shuffles, lanes 0 and
+// 2 first, then lane 1 with the idle lane 3's zero.  Written without
+// branches: every load is issued (a neighbour outside the grid or on a
+// Dirichlet plane reads the node itself) and the sums take their terms by
+// selection.
+template <typename T>
+__device__ __forceinline__ void tail_stencil_node(const TailStep<T> &s, const int gid) {
+  const int n[3] = {s.grid[0], s.grid[1], s.grid[2]};
+  const long ng = (long)n[0] * n[1] * n[2];
+  int g[3];
+  grid_coords(gid, n[0], n[1], g);
+  bool ok[3][3];   // neighbour at offset k - 1 along d exists and is free
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int h = g[d] + k - 1;
+      ok[d][k] = (h >= 0) & (h < n[d]) & !((h == 0) & (s.bc[2 * d] == 0)) & !((h == n[d] - 1) & (s.bc[2 * d + 1] == 0));
+    }
+  const long sy = n[0], sz = (long)n[0] * n[1];
+  const T *__restrict__ coef = s.coef;
+  const T *u = s.u;
+  T cf[27], uv[27];
+#pragma unroll
+  for (int z = 0; z < 3; ++z)
+#pragma unroll
+    for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const int o = x + 3 * (yy + 3 * z);
+        const bool take = ok[0][x] & ok[1][yy] & ok[2][z];
+        cf[o] = coef[(long)o * ng + gid];
+        uv[o] = ldv<true>(u + (take ? gid + (x - 1) + (yy - 1) * sy + (z - 1) * sz : gid));
+      }
+  // the epilogue's operands too, before the sums (an absent x or x_prev reads u)
+  const bool cons = node_constrained(g, n, s.bc);
+  const T ug = ldv<true>(u + gid);
+  const T bv = ldv<true>(s.b + gid);
+  const T dv = s.dinv[gid];
+  const T xv = ldv<true>((s.x ? s.x : u) + gid), xpv = ldv<true>((s.xp ? s.xp : u) + gid);
+  T part[3];
+#pragma unroll
+  for (int z = 0; z < 3; ++z) {
+    T y = T(0);
+#pragma unroll
+    for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const int o = x + 3 * (yy + 3 * z);
+        y = (ok[0][x] & ok[1][yy]) ? fma(cf[o], uv[o], y) : y;
+      }
+    part[z] = ok[2][z] ? y : T(0);
+  }
+  T y = (part[0] + part[2]) + (part[1] + T(0));
+  y = cons ? ug : y;   // identity row
+  if (s.mode == 2) {
+    s.out[gid] = bv - y;
+  } else {
+    T v = s.c3 * dv * (bv - y);
+    if (s.x) v = fma(s.c1, xv, v);
+    if (s.xp) v = fma(s.c2, xpv, v);
+    s.out[gid] = v;
+  }
+}
+
+// The program (nsteps steps) is copied to shared memory first; the grid is
+// one cluster.  A step's items go out in chunks of 32 (one warp each), chunk q
+// to block q mod C, so that a small level spreads over all the cluster's SMs
+// instead of filling the first block.
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads, 1) fe_tail_kernel(const TailStep<T> *__restrict__ prog,
+                                                                  const int nsteps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TailStep<T> *sp = reinterpret_cast<TailStep<T> *>(smem_raw);
+  {
+    const int4 *src = reinterpret_cast<const int4 *>(prog);
+    int4 *dst = reinterpret_cast<int4 *>(smem_raw);
+    const int words = nsteps * (int)(sizeof(TailStep<T>) / sizeof(int4));
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int nt = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int q0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // the thread's first chunk
+  const int first = q0 * 32 + lane;
+#pragma unroll 1
+  for (int k = 0; k < nsteps; ++k) {
+    const TailStep<T> &s = sp[k];
+    switch (s.op) {
+      case kTailXdb:   // launch_xdb
+#pragma unroll 1
+        for (int i = first; i < s.n; i += nt) s.out[i] = s.c3 * s.dinv[i] * ldv<true>(s.b + i);
+        break;
+      case kTailStencil:
+#pragma unroll 1
+        for (int i = first; i < s.n; i += nt) tail_stencil_node<T>(s, i);
+        break;
+      case kTailRestrict:
+#pragma unroll 1
+        for (int i = first; i < s.n; i += nt) fe_restrict_node<T, true>(s.g, s.P1, s.u, s.out, i);
+        break;
+      case kTailCoarse: {   // launch_dense_gemv: one warp per row
+#pragma unroll 1
+        for (int row = q0; row < s.n; row += nt >> 5) {
+          const double *ar = s.Ainv + (size_t)row * s.n;
+          double acc = 0;
+          for (int j = lane; j < s.n; j += 32) acc = fma(ar[j], (double)ldv<true>(s.b + j), acc);
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+          if (lane == 0) s.out[row] = (T)acc;
+        }
+        break;
+      }
+      default:   // kTailProlong
+#pragma unroll 1
+        for (int i = first; i < s.n; i += nt) fe_prolongate_node<T, 2, true>(s.g, s.P1, s.u, s.out, i);
+    }
+    cluster_barrier();
+  }
+}
+
+template <typename T>
+static cudaLaunchConfig_t tail_config(int nsteps, int cluster, cudaStream_t s, cudaLaunchAttribute *at) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cluster);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = (size_t)nsteps * sizeof(TailStep<T>);
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <typename T>
+int fe_tail_cluster(int nsteps) {
+  static_assert(sizeof(TailStep<T>) % sizeof(int4) == 0, "the program is copied in 16-byte words");
+  if (nsteps <= 0 || nsteps > kTailMaxSteps) return 0;
+  if (cudaFuncSetAttribute(fe_tail_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  for (const int cs : {16, 8}) {
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = tail_config<T>(kTailMaxSteps, cs, nullptr, at);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fe_tail_kernel<T>, &cfg) == cudaSuccess && n > 0) return cs;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+template <typename T>
+cudaError_t launch_fe_tail(const TailStep<T> *prog, int nsteps, int cluster, cudaStream_t s) {
+  if (nsteps <= 0 || nsteps > kTailMaxSteps || (cluster != 8 && cluster != 16)) return cudaErrorInvalidValue;
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = tail_config<T>(nsteps, cluster, s, at);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, fe_tail_kernel<T>, prog, nsteps);
+  note_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_fe_restrict_cells(const XferGeom &g, const T *P1, const T *rf, T *ebuf, cudaStream_t s) {
   const int nf = g.pf + 1, nc = g.pc + 1;
@@ -1135,7 +1332,9 @@ cudaError_t launch_dg_transfer(const XferGeom &g, const T *P1, const T *in, T *o
                                                    cudaStream_t);                                       \
   template cudaError_t launch_fe_restrict_cells<T>(const XferGeom &, const T *, const T *, T *,         \
                                                    cudaStream_t);                                       \
-  template cudaError_t launch_dg_transfer<T>(const XferGeom &, const T *, const T *, T *, bool, cudaStream_t);
+  template cudaError_t launch_dg_transfer<T>(const XferGeom &, const T *, const T *, T *, bool, cudaStream_t); \
+  template int fe_tail_cluster<T>(int);                                                                 \
+  template cudaError_t launch_fe_tail<T>(const TailStep<T> *, int, int, cudaStream_t);
 SIPG_FE_INST(double)
 SIPG_FE_INST(float)
 

@@ -218,6 +218,39 @@ inline bool fe_restrict_nodes_ok(const XferGeom &g) {
 }
 template <typename T>
 cudaError_t launch_fe_restrict_nodes(const XferGeom &g, const T *P1, const T *rf, T *rc, cudaStream_t s);
+
+// The lower end of the V-cycle (Algorithm 2 below a size bound) in one
+// launch of one thread-block cluster: the degree-1 FE levels applied by their
+// 27-point stencils, the 2:1 transfers between them and the dense coarse
+// inverse, each step a pass over the level's nodes followed by a cluster
+// barrier.  Every value is computed with the arithmetic, in the order, of the
+// per-step kernels (launch_xdb, launch_fe_stencil_apply, launch_fe_restrict_nodes,
+// launch_dense_gemv, launch_fe_prolongate_add), so both give the same bits.
+enum TailOp : int { kTailXdb = 0, kTailStencil = 1, kTailRestrict = 2, kTailCoarse = 3, kTailProlong = 4 };
+template <typename T>
+struct alignas(16) TailStep {
+  int op;                 // TailOp
+  int mode;               // kTailStencil: 1 Chebyshev step, 2 residual (as FEArgs::mode)
+  int n;                  // nodes of the step's output (kTailCoarse: unknowns of the coarse level)
+  int grid[3];            // node grid of the level (kTailStencil)
+  int bc[6];
+  const T *u;             // stencil: operand; transfers: input vector
+  const T *x, *xp, *b, *dinv, *coef;
+  T *out;                 // xdb, stencil, restriction, coarse: written; prolongation: out += P u
+  T c1, c2, c3;
+  XferGeom g;             // kTailRestrict, kTailProlong
+  const T *P1;
+  const double *Ainv;     // kTailCoarse: [n][n]
+};
+constexpr int kTailThreads = 512;     // threads per block of the cluster
+constexpr int kTailMaxNodes = 8192;   // largest level taken into the fused tail
+constexpr int kTailMaxCoarse = 1000;  // largest dense coarse level taken
+constexpr int kTailMaxSteps = 160;    // the program sits in shared memory
+// the cluster size the device runs the tail kernel with (16, else 8; 0: none)
+template <typename T>
+int fe_tail_cluster(int nsteps);
+template <typename T>
+cudaError_t launch_fe_tail(const TailStep<T> *prog, int nsteps, int cluster, cudaStream_t s);
 // DG -> DG transfers (kind 3 p, 4 h): prolong: out += P in; else out = P^T in
 template <typename T>
 cudaError_t launch_dg_transfer(const XferGeom &g, const T *P1, const T *in, T *out, bool prolong, cudaStream_t s);

@@ -117,6 +117,12 @@ struct sipg_ctx {
   std::vector<long long> fcg_kA, fcg_kB;   // kernels in each iteration's two bodies
   // kernels captured into each graph, added to the launch count per replay
   std::map<cudaGraphExec_t, long long> graph_kernels;
+  // The fused lower cycle (launch_fe_tail) in the cycle precision: for every
+  // level t = 1..tail_top the device program of vcycle_rec(t) and the buffer
+  // that holds x^(t) after it (index t; entry 0 unused)
+  int tail_top = 0, tail_cluster = 0;
+  std::vector<void *> tail_prog, tail_x;
+  std::vector<int> tail_steps;
 };
 
 static std::string g_create_err;
@@ -458,11 +464,133 @@ void coarse_cg_solve(sipg_ctx *c, const T *b_all, T *x_all) {
   c->nv = nv;
 }
 
+// The steps vcycle_rec(l) launches on the levels of the fused tail, in
+// launch order with the same buffers and coefficients, as a program of the
+// tail kernel; returns the buffer that holds x^(l) after it.
+template <typename T>
+T *tail_rec(sipg_ctx *c, int l, std::vector<TailStep<T>> &prog) {
+  constexpr int pi = pidx<T>();
+  T *b = lvec<T>(c, l, 0);
+  if (l == 0) {   // the dense coarse inverse
+    TailStep<T> s{};
+    s.op = kTailCoarse;
+    s.n = c->n0;
+    s.b = b;
+    s.out = lvec<T>(c, 0, 1);
+    s.Ainv = c->Ainv;
+    prog.push_back(s);
+    return lvec<T>(c, 0, 1);
+  }
+  const Level &L = c->lv[l];
+  T *x = lvec<T>(c, l, 1), *xt = lvec<T>(c, l, 3);
+  auto level_step = [&](int op) {
+    TailStep<T> s{};
+    s.op = op;
+    s.n = (int)L.ndofs;
+    for (int d = 0; d < 3; ++d) s.grid[d] = L.grid[d];
+    for (int k = 0; k < 6; ++k) s.bc[k] = c->mesh.bc[k];
+    s.dinv = (const T *)L.dinv[pi];
+    s.coef = (const T *)L.stencil[pi];
+    s.b = b;
+    return s;
+  };
+  auto smooth = [&](bool zero_start) {   // chebyshev()
+    for (const ChebStep &q : cheb_plan(c, l, c->prm.cheb_degree, zero_start)) {
+      TailStep<T> s = level_step(q.xdb ? kTailXdb : kTailStencil);
+      s.c3 = (T)q.c3;
+      if (q.xdb) {
+        s.out = x;
+        prog.push_back(s);
+        continue;
+      }
+      s.mode = 1;
+      s.u = x;
+      s.out = xt;
+      s.x = x;
+      s.xp = q.has_prev ? xt : nullptr;
+      s.c1 = (T)q.c1;
+      s.c2 = (T)q.c2;
+      prog.push_back(s);
+      std::swap(x, xt);
+    }
+  };
+  smooth(true);
+  TailStep<T> r = level_step(kTailStencil);   // the residual
+  r.mode = 2;
+  r.u = x;
+  r.out = lvec<T>(c, l, 2);
+  prog.push_back(r);
+  const XferGeom g = xfer(c, l);
+  TailStep<T> rs{};
+  rs.op = kTailRestrict;
+  rs.g = g;
+  rs.n = g.gc[0] * g.gc[1] * g.gc[2];
+  rs.P1 = (const T *)L.P1[pi];
+  rs.u = lvec<T>(c, l, 2);
+  rs.out = lvec<T>(c, l - 1, 0);
+  prog.push_back(rs);
+  const T *xc = tail_rec<T>(c, l - 1, prog);
+  TailStep<T> pr{};
+  pr.op = kTailProlong;
+  pr.g = g;
+  pr.n = g.gf[0] * g.gf[1] * g.gf[2];
+  pr.P1 = (const T *)L.P1[pi];
+  pr.u = xc;
+  pr.out = x;
+  prog.push_back(pr);
+  smooth(false);
+  return x;
+}
+
+// Which levels the fused tail takes: from level 1 up, every degree-1 FE level
+// below the finest applied by its stencil with a 2:1 transfer from the level
+// below and at most kTailMaxNodes nodes, over a dense coarse level; a program
+// for every top level t, so that a cycle entered at any of them (the batched
+// cycle enters below its two finest levels) runs fused.
+template <typename T>
+void build_tail(sipg_ctx *c) {
+  constexpr int pi = pidx<T>();
+  if (!c->prm.fuse_tail || c->coarse_cg || !c->Ainv || c->n0 > kTailMaxCoarse || c->n0 != c->lv[0].ndofs) return;
+  int top = 0;
+  while (top + 1 < c->L) {
+    const Level &L = c->lv[top + 1];
+    if (L.kind != 1 || L.deg != 1 || !L.stencil[pi] || L.t_kind != 2 || L.ndofs > kTailMaxNodes ||
+        !fe_restrict_nodes_ok(xfer(c, top + 1)) || !L.dinv[pi])
+      break;
+    ++top;
+  }
+  std::vector<void *> progs(top + 1, nullptr), xs(top + 1, nullptr);
+  std::vector<int> steps(top + 1, 0);
+  int built = 0;
+  for (int t = 1; t <= top; ++t) {
+    std::vector<TailStep<T>> prog;
+    xs[t] = tail_rec<T>(c, t, prog);
+    if ((int)prog.size() > kTailMaxSteps) break;
+    TailStep<T> *d = dalloc<TailStep<T>>(c, (int64_t)prog.size());
+    CK(cudaMemcpy(d, prog.data(), prog.size() * sizeof(TailStep<T>), cudaMemcpyHostToDevice));
+    progs[t] = d;
+    steps[t] = (int)prog.size();
+    built = t;
+  }
+  if (built == 0) return;
+  const int cluster = fe_tail_cluster<T>(steps[built]);
+  if (cluster == 0) return;
+  c->tail_top = built;
+  c->tail_cluster = cluster;
+  c->tail_prog = progs;
+  c->tail_x = xs;
+  c->tail_steps = steps;
+}
+
 // Algorithm 2 with x^(l) = 0 on entry: rhs in lv[l].vb; returns the buffer
 // (vx or vt of that level) that holds x^(l).  No state changes between calls,
 // so the whole cycle can be captured once and replayed.
 template <typename T>
 T *vcycle_rec(sipg_ctx *c, int l) {
+  if (l >= 1 && l <= c->tail_top && c->nv == 1 && pidx<T>() == c->prm.precision) {   // the fused tail
+    CK(launch_fe_tail<T>((const TailStep<T> *)c->tail_prog[l], c->tail_steps[l], c->tail_cluster, c->stream));
+    return (T *)c->tail_x[l];
+  }
   T *b = lvec<T>(c, l, 0);
   if (l == 0) {
     if (c->coarse_cg) coarse_cg_solve<T>(c, b, lvec<T>(c, l, 1));
@@ -993,6 +1121,8 @@ void setup(sipg_ctx *c) {
     c->Ainv = dalloc<double>(c, (int64_t)N * N);
     CK(cudaMemcpy(c->Ainv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
+  if (P.precision == 0) build_tail<double>(c);
+  else build_tail<float>(c);
   const int64_t N = c->lv[c->L].ndofs;
   c->fr = dalloc<double>(c, N);
   c->fz = dalloc<double>(c, N);
@@ -1838,6 +1968,7 @@ void sipg_default_params(sipg_params *p) {
   p->coarse_solver = 0;
   p->coarse_rtol = 1e-3;
   p->coarse_maxit = 12;
+  p->fuse_tail = 1;
   p->stream = nullptr;
 }
 
@@ -1862,6 +1993,7 @@ sipg_status sipg_create(const sipg_mesh *mesh, const sipg_params *params, sipg_c
     if (P.coarse_solver < 0 || P.coarse_solver > 1 || !(P.coarse_rtol > 0 && P.coarse_rtol < 1) ||
         P.coarse_maxit < 1 || P.coarse_maxit > 1000)
       throw_inval("coarse_solver must be 0 or 1, coarse_rtol in (0, 1) and coarse_maxit in 1..1000");
+    if (P.fuse_tail != 0 && P.fuse_tail != 1) throw_inval("fuse_tail must be 0 or 1");
     for (int s = 0; s < 6; ++s)
       if (M.bc[s] != 0 && M.bc[s] != 1) throw_inval("bc must be 0 (Dirichlet) or 1 (Neumann)");
     const double cells = (double)M.m[0] * M.m[1] * M.m[2];

@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("fe_assemble", ctypes.c_int),
                 ("coarse_dense_max", ctypes.c_int), ("coarse_iters", ctypes.c_int),
                 ("coarse_solver", ctypes.c_int), ("coarse_rtol", ctypes.c_double), ("coarse_maxit", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("fuse_tail", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -170,7 +170,8 @@ def make_mesh(m, deform=0, amp=0.1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(
 
 def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
                 operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None,
-                coarse_dense_max=None, coarse_iters=None, coarse_solver=None, coarse_rtol=None, coarse_maxit=None):
+                coarse_dense_max=None, coarse_iters=None, coarse_solver=None, coarse_rtol=None, coarse_maxit=None,
+                fuse_tail=None):
     prm = Params()
     lib().sipg_default_params(ctypes.byref(prm))
     prm.degree, prm.precision, prm.penalty_factor = int(degree), int(precision), float(penalty_factor)
@@ -191,6 +192,8 @@ def make_params(degree, precision=0, penalty_factor=1.0, cheb_degree=5, eig_iter
         prm.coarse_rtol = float(coarse_rtol)
     if coarse_maxit is not None:
         prm.coarse_maxit = int(coarse_maxit)
+    if fuse_tail is not None:
+        prm.fuse_tail = int(bool(fuse_tail))
     prm.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return prm
 
@@ -202,7 +205,7 @@ class Context:
                  precision=0, penalty_factor=1.0, cheb_degree=5, eig_iters=20, lambda_override=0.0,
                  operator_only=False, stream=None, autotune=False, p_coarsen=0, coarsening="cph", fe_assemble=None,
                  coarse_dense_max=None, coarse_iters=None, coarse_solver=None, coarse_rtol=None, coarse_maxit=None,
-                 _handle=None):
+                 fuse_tail=None, _handle=None):
         L = lib()
         mesh, mm = make_mesh(m, deform, amp, lo, hi, bc)
         self.degree, self.precision = int(degree), int(precision)
@@ -214,7 +217,7 @@ class Context:
             return
         prm = make_params(degree, precision, penalty_factor, cheb_degree, eig_iters, lambda_override,
                           operator_only, stream, autotune, p_coarsen, coarsening, fe_assemble,
-                          coarse_dense_max, coarse_iters, coarse_solver, coarse_rtol, coarse_maxit)
+                          coarse_dense_max, coarse_iters, coarse_solver, coarse_rtol, coarse_maxit, fuse_tail)
         h = ctypes.c_void_p()
         st = L.sipg_create(ctypes.byref(mesh), ctypes.byref(prm), ctypes.byref(h))
         if st != OK:

@@ -42,7 +42,7 @@ def test_default_params_and_create_rejects_bad_input(lib):
     from paper_1910_01900_gb300 import native
     p = native.Params()
     lib.sipg_default_params(ctypes.byref(p))
-    assert (p.degree, p.cheb_degree, p.eig_iters) == (3, 5, 20)
+    assert (p.degree, p.cheb_degree, p.eig_iters, p.fuse_tail) == (3, 5, 20, 1)
     assert abs(p.cheb_lo - 0.06) < 1e-15 and abs(p.cheb_hi - 1.2) < 1e-15
     mesh = native.Mesh()
     h = ctypes.c_void_p()
@@ -55,7 +55,8 @@ def test_default_params_and_create_rejects_bad_input(lib):
     for field, value, word in (("penalty_factor", -1.0, b"penalty"), ("penalty_factor", 0.0, b"penalty"),
                                ("precision", 2, b"precision"), ("cheb_degree", 0, b"smoother"),
                                ("p_coarsen", 3, b"smoother"), ("coarse_solver", 2, b"coarse_solver"),
-                               ("coarse_rtol", 0.0, b"coarse_rtol"), ("coarse_maxit", 0, b"coarse_maxit")):
+                               ("coarse_rtol", 0.0, b"coarse_rtol"), ("coarse_maxit", 0, b"coarse_maxit"),
+                               ("fuse_tail", 2, b"fuse_tail")):
         q = native.Params()
         lib.sipg_default_params(ctypes.byref(q))
         setattr(q, field, value)
