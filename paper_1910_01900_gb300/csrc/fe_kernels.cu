@@ -396,7 +396,7 @@ __device__ __forceinline__ void fe_gather_node(const FEArgs<T> &a, const long gi
   const bool cons = node_constrained(g, a.grid, a.bc);
   T y;
   if (cons) {
-    y = (a.mode == 3) ? T(0) : (a.mode == 4 ? T(1) : a.u[vo + gid]);
+    y = (a.mode == 3 || a.mode == 5) ? T(0) : (a.mode == 4 ? T(1) : a.u[vo + gid]);
   } else {
     // per direction: the cell the node starts (its last cell for the last
     // node, where it sits on the upper face) and, when the node is on that
@@ -438,6 +438,7 @@ __device__ __forceinline__ void fe_gather_node(const FEArgs<T> &a, const long gi
   const long gv = vo + gid;
   if (a.mode == 0 || a.mode >= 3) {
     a.out[gv] = y;
+    if (a.mode == 5) a.out2[gv] = a.c3 * a.dinv[gid] * y;   // launch_xdb's x = c D^-1 b
   } else if (a.mode == 2) {
     a.out[gv] = a.b[gv] - y;
   } else {

@@ -107,10 +107,12 @@ struct FEArgs {
   int ncells;
   int bc[6];
   int mode;            // gather: 0 apply, 1 chebyshev, 2 residual, 3 restrict (sum, constrained -> 0),
-                       //         4 diagonal (sum, constrained -> 1)
+                       //         4 diagonal (sum, constrained -> 1), 5 restrict and the coarse
+                       //         level's first Chebyshev step: out2 = c3 dinv out
   const T *x, *xp, *b, *dinv;
   T c1, c2, c3;
   T alpha[3];          // Cartesian: prod(h) / h_d^2, the scale of direction d's term
+  T *out2 = nullptr;   // mode 5
   // nv vectors at once: vector r of u, out, x, xp, b starts at r * vs, its
   // element buffer at r * es
   int nv = 1;
@@ -260,6 +262,9 @@ template <typename T>
 cudaError_t launch_fill(T *x, T v, int64_t n, cudaStream_t s);
 template <typename Tout, typename Tin>
 cudaError_t launch_cast(Tout *y, const Tin *x, int64_t n, cudaStream_t s);
+// b = (T) r and x = c D^-1 b (the first Chebyshev step from x = 0) in one pass
+template <typename T, typename Tin>
+cudaError_t launch_cast_xdb(T *b, T *x, T c, const T *dinv, const Tin *r, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_axpy(T *y, T a, const T *x, int64_t n, cudaStream_t s);   // y += a x
 cudaError_t launch_invert(double *d, int64_t n, cudaStream_t s);

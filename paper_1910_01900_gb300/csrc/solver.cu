@@ -312,22 +312,30 @@ XferGeom xfer(sipg_ctx *c, int l) {
   return g;
 }
 
-// rc = R r from level l to l-1
+// rc = R r from level l to l-1.  With x0: where the restriction ends in a
+// node pass, that pass also writes level l-1's first Chebyshev step from
+// x = 0, x0 = c3 D^-1 rc (the xdb step, same arithmetic); returns whether it did.
 template <typename T>
-void restrict_level(sipg_ctx *c, int l, const T *r, T *rc) {
+bool restrict_level(sipg_ctx *c, int l, const T *r, T *rc, T *x0 = nullptr, T c3 = 0) {
   constexpr int pi = pidx<T>();
   const Level &F = c->lv[l];
   if (F.t_kind >= 3) {   // DG -> DG: cell-local transpose
     CK(launch_dg_transfer<T>(xfer(c, l), (const T *)F.P1[pi], r, rc, false, c->stream));
-    return;
+    return false;
   }
   if (F.t_kind != 0 && fe_restrict_nodes_ok(xfer(c, l))) {   // small transfer: one node pass
     CK(launch_fe_restrict_nodes<T>(xfer(c, l), (const T *)F.P1[pi], r, rc, c->stream));
-    return;
+    return false;
   }
   FEArgs<T> a = fe_args<T>(c, c->lv[l - 1]);
   a.mode = 3;
   a.out = rc;
+  if (x0) {
+    a.mode = 5;
+    a.out2 = x0;
+    a.c3 = c3;
+    a.dinv = (const T *)c->lv[l - 1].dinv[pi];
+  }
   if (F.t_kind == 0) {
     a.ebuf = const_cast<T *>(r);   // the DG vector is the element buffer of the FE level
   } else {
@@ -335,6 +343,7 @@ void restrict_level(sipg_ctx *c, int l, const T *r, T *rc) {
                                    (T *)(c->nv > 1 ? c->mv.ebuf[pi] : c->ebuf[pi]), c->stream));
   }
   CK(launch_fe_gather<T>(a, c->stream));
+  return x0 != nullptr;
 }
 
 // x += P xc from level l-1 to l
@@ -378,14 +387,15 @@ std::vector<ChebStep> cheb_plan(const sipg_ctx *c, int l, int ns, bool zero_star
 
 // Algorithm 3 on level l: x (in/out buffer pointer) with scratch xt; the
 // buffers are swapped as the iteration proceeds.
+// (x0_done: the producer of b already wrote the first step, x = c3 D^-1 b)
 template <typename T>
-void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_start) {
+void chebyshev(sipg_ctx *c, int l, const T *b, T *&x, T *&xt, int ns, bool zero_start, bool x0_done = false) {
   constexpr int pi = pidx<T>();
   const Level &L = c->lv[l];
   const T *dinv = (const T *)L.dinv[pi];
   for (const ChebStep &q : cheb_plan(c, l, ns, zero_start)) {
     if (q.xdb) {   // x_0 = 0
-      CK(launch_xdb<T>(x, (T)q.c3, dinv, b, L.ndofs, c->stream, c->nv));
+      if (!x0_done) CK(launch_xdb<T>(x, (T)q.c3, dinv, b, L.ndofs, c->stream, c->nv));
       continue;
     }
     apply_level<T>(c, l, x, xt, 1, x, q.has_prev ? xt : nullptr, b, dinv, (T)q.c1, (T)q.c2, (T)q.c3);
@@ -585,9 +595,17 @@ void build_tail(sipg_ctx *c) {
 // Algorithm 2 with x^(l) = 0 on entry: rhs in lv[l].vb; returns the buffer
 // (vx or vt of that level) that holds x^(l).  No state changes between calls,
 // so the whole cycle can be captured once and replayed.
+// level l runs inside the fused tail
 template <typename T>
-T *vcycle_rec(sipg_ctx *c, int l) {
-  if (l >= 1 && l <= c->tail_top && c->nv == 1 && pidx<T>() == c->prm.precision) {   // the fused tail
+bool in_tail(const sipg_ctx *c, int l) {
+  return l >= 1 && l <= c->tail_top && c->nv == 1 && pidx<T>() == c->prm.precision;
+}
+
+// (x0_done: the restriction or the cast that wrote this level's right-hand
+// side also wrote its first Chebyshev step)
+template <typename T>
+T *vcycle_rec(sipg_ctx *c, int l, bool x0_done = false) {
+  if (in_tail<T>(c, l)) {   // the fused tail
     CK(launch_fe_tail<T>((const TailStep<T> *)c->tail_prog[l], c->tail_steps[l], c->tail_cluster, c->stream));
     return (T *)c->tail_x[l];
   }
@@ -601,10 +619,15 @@ T *vcycle_rec(sipg_ctx *c, int l) {
   const int ns = c->prm.cheb_degree;
   const bool learned = (l == c->L) && c->use_learned;
   if (learned && c->net.steps_pre > 0) learned_smooth<T>(c, b, x, c->net.steps_pre, true);
-  else chebyshev<T>(c, l, b, x, xt, ns, true);   // steps_pre = 0: Chebyshev pre-smoothing
+  else chebyshev<T>(c, l, b, x, xt, ns, true, x0_done);   // steps_pre = 0: Chebyshev pre-smoothing
   apply_level<T>(c, l, x, lvec<T>(c, l, 2), 2, nullptr, nullptr, b);
-  restrict_level<T>(c, l, lvec<T>(c, l, 2), lvec<T>(c, l - 1, 0));
-  const T *xc = vcycle_rec<T>(c, l - 1);
+  // the level below starts its Chebyshev smoothing from x = 0 unless it is the
+  // coarse level or runs in the fused tail: its first step can ride on the restriction
+  const bool x0 = c->nv == 1 && l - 1 >= 1 && !in_tail<T>(c, l - 1);
+  const bool done = restrict_level<T>(c, l, lvec<T>(c, l, 2), lvec<T>(c, l - 1, 0),
+                                      x0 ? lvec<T>(c, l - 1, 1) : nullptr,
+                                      x0 ? (T)cheb_plan(c, l - 1, ns, true)[0].c3 : T(0));
+  const T *xc = vcycle_rec<T>(c, l - 1, done);
   prolongate_level<T>(c, l, xc, x);
   if (learned) learned_smooth<T>(c, b, x, c->net.steps_post, false);
   else chebyshev<T>(c, l, b, x, xt, ns, false);
@@ -612,15 +635,28 @@ T *vcycle_rec(sipg_ctx *c, int l) {
 }
 
 // z = M^-1 r with FP64 vectors in and out
+// (one vector with Chebyshev pre-smoothing on the finest level: the copy or
+// cast of r into the level's right-hand side also writes its first step)
 void vcycle_body(sipg_ctx *c, const double *r, double *z) {
   const int64_t n = c->lv[c->L].ndofs * c->nv;
+  const bool x0 = c->nv == 1 && !(c->use_learned && c->net.steps_pre > 0);
+  const Level &F = c->lv[c->L];
+  const double c3 = x0 ? cheb_plan(c, c->L, c->prm.cheb_degree, true)[0].c3 : 0.0;
   if (c->prm.precision == 0) {
-    CK(cudaMemcpyAsync(lvec<double>(c, c->L, 0), r, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    const double *x = vcycle_rec<double>(c, c->L);
+    if (x0)
+      CK((launch_cast_xdb<double, double>(lvec<double>(c, c->L, 0), lvec<double>(c, c->L, 1), c3,
+                                          (const double *)F.dinv[0], r, n, c->stream)));
+    else
+      CK(cudaMemcpyAsync(lvec<double>(c, c->L, 0), r, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    const double *x = vcycle_rec<double>(c, c->L, x0);
     CK(cudaMemcpyAsync(z, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   } else {
-    CK((launch_cast<float, double>(lvec<float>(c, c->L, 0), r, n, c->stream)));
-    const float *x = vcycle_rec<float>(c, c->L);
+    if (x0)
+      CK((launch_cast_xdb<float, double>(lvec<float>(c, c->L, 0), lvec<float>(c, c->L, 1), (float)c3,
+                                         (const float *)F.dinv[1], r, n, c->stream)));
+    else
+      CK((launch_cast<float, double>(lvec<float>(c, c->L, 0), r, n, c->stream)));
+    const float *x = vcycle_rec<float>(c, c->L, x0);
     CK((launch_cast<double, float>(z, x, n, c->stream)));
   }
 }

@@ -24,6 +24,15 @@ __global__ void cast_kernel(Tout *y, const Tin *x, long n) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     y[i] = (Tout)x[i];
 }
+// b = (T) r and the first Chebyshev step from x = 0, x = c D^-1 b (xdb_kernel's arithmetic), in one pass
+template <typename T, typename Tin>
+__global__ void cast_xdb_kernel(T *b, T *x, T c, const T *dinv, const Tin *r, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const T v = (T)r[i];
+    b[i] = v;
+    x[i] = c * dinv[i] * v;
+  }
+}
 template <typename T>
 __global__ void axpy_kernel(T *y, T a, const T *x, long n) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -54,6 +63,17 @@ cudaError_t launch_cast(Tout *y, const Tin *x, int64_t n, cudaStream_t s) {
   note_launch();
   return cudaGetLastError();
 }
+template <typename T, typename Tin>
+cudaError_t launch_cast_xdb(T *b, T *x, T c, const T *dinv, const Tin *r, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cast_xdb_kernel<T, Tin><<<grid_for(n), 256, 0, s>>>(b, x, c, dinv, r, n);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_cast_xdb<float, double>(float *, float *, float, const float *, const double *, int64_t,
+                                                    cudaStream_t);
+template cudaError_t launch_cast_xdb<double, double>(double *, double *, double, const double *, const double *,
+                                                     int64_t, cudaStream_t);
 template <typename T>
 cudaError_t launch_axpy(T *y, T a, const T *x, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -73,8 +73,13 @@ def test_fused_tail_cycle_equals_per_step_launches(case):
     n2 = native.launch_count()
     t = _tail_levels(a)
     ns = case.get("cheb_degree", 5)
-    # per tail level: 2 ns Chebyshev steps, residual, restriction, prolongation; plus the coarse solve
-    assert (n2 - n1) - (n1 - n0) == t * (2 * ns + 3)
+    # per tail level: 2 ns Chebyshev steps, residual, restriction, prolongation; plus the coarse
+    # solve.  Without the tail, the top tail level's first step rides on the restriction into it
+    # where that ends in a node pass (from a DG level or an FE level of degree >= 3; degrees 1 and
+    # 2 restrict node by node in one launch of their own)
+    kind_above, deg_above, _ = a.level_info(t + 1)
+    folded = kind_above == 0 or deg_above >= 3
+    assert (n2 - n1) - (n1 - n0) == t * (2 * ns + 3) - (1 if folded else 0)
     # on a stream the cycle is captured as a graph and replayed: same bits
     a2, b2 = _ctx(1, s, **case), _ctx(0, s, **case)
     for _ in range(3):
